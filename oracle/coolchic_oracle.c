@@ -1,0 +1,852 @@
+/*
+ * Cool-chic 5.0 per-iteration encoder step -- plain FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call
+ * this file.  It exists so that tests, the smoke check and the CPU-baseline leg of
+ * the benchmark can compare the CUDA path against a slow, obviously correct
+ * restatement of the method.  It shares no code, header or table with the CUDA
+ * library; every constant it needs is written out here.
+ *
+ * What it computes (paper section / equation in brackets):
+ *   - latent grids  y^(k), k = 0..L-1, shape ceil(H/2^k) x ceil(W/2^k)      [Sec. III-A1, Eq. 1]
+ *   - noise relaxation  y~ = y + u, u ~ U(-1/2, 1/2) from a counter hash    [Sec. IV-C; Eq. 13 is
+ *     the paper's own proxy, replaced here by the additive uniform proxy]
+ *   - causal spatial context s_i and inter-feature context f_i = IFCE_k(r_i)  [Sec. III-A1/A2, Eqs. 4-5]
+ *   - ARM MLP + linear stabilizer -> (mu, log b)                             [Eq. 4, Eq. 9, Sec. III-C]
+ *   - Laplace interval probability and rate  -log2 p                         [Eq. 3, Eq. 11]
+ *   - upsampling cascade  z = f_up(y)                                        [Sec. III-B, Eq. 7]
+ *   - synthesis: 1x1 MLP + stabilizer, then two residual 3x3 convs           [Sec. III-B, Eq. 8, Eq. 9]
+ *   - loss  D + lambda * R / (H W)                                           [Sec. IV-A, Eq. 10]
+ *   - hand-written adjoint of all of the above (transposed forward loops)
+ *   - Adam                                                                   [Sec. IV-B]
+ *   - hard quantisation  Q = rint                                            [Sec. IV-C, Eq. 12]
+ *   - integer decode ARM and integer Laplace CDF (16-bit probabilities)       [Sec. III-A2: integer,
+ *     cross-platform decoding motivates it; the fixed-point format is this project's reading]
+ *
+ * Parity status: the spatial context pattern, the IFCE width F = 4, the upsampling filter form,
+ * the initialisation and the integer decode format are readings of a paper that leaves them open;
+ * they are pinned by invariants and by an independent float64 autograd composition in the tests,
+ * not by values printed in the paper ("parity unpinned" for those readings).
+ *
+ * Loops are plain and in the order of the definitions.  OpenMP is used only across
+ * independent rows; every reduction goes through per-row partial arrays summed serially,
+ * so results do not depend on the thread count.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ----------------------------------------------------------------------------------------
+ * Architecture (Table II read at the MOP/HOP scale chosen for this workload).
+ * ---------------------------------------------------------------------------------------- */
+#define NG 7          /* L: latent grids 1/1 .. 1/64 (Table II, small images)            */
+#define NCTX 16       /* spatial causal context size                                      */
+#define NF 4          /* IFCE output width                                                */
+#define NIFCE 3       /* grids 1/1, 1/2, 1/4 carry an IFCE (Table II)                      */
+#define AIN (NCTX + NF)
+#define AH 16         /* ARM hidden width, two hidden layers                              */
+#define NCH 3         /* image channels                                                   */
+#define SH 40         /* synthesis hidden width                                           */
+#define LOGB_MIN (-5.0)
+#define LOGB_MAX (5.0)
+#define P_MIN (1.0 / 65536.0)
+
+/* Flat parameter vector, all matrices row-major [out][in]. */
+enum {
+    O_ARM_W1 = 0, O_ARM_B1 = 320, O_ARM_W2 = 336, O_ARM_B2 = 592,
+    O_ARM_W3 = 608, O_ARM_B3 = 640, O_ARM_WS = 642, O_ARM_BS = 682,
+    O_IF0_W = 684, O_IF0_B = 708, O_IF1_W = 712, O_IF1_B = 732, O_IF2_W = 736, O_IF2_B = 752,
+    O_UP = 756,
+    O_SYN_W1 = 780, O_SYN_B1 = 1060, O_SYN_W2 = 1100, O_SYN_B2 = 1220, O_SYN_WS = 1223, O_SYN_BS = 1244,
+    O_CV1_W = 1247, O_CV1_B = 1328, O_CV2_W = 1331, O_CV2_B = 1412,
+    N_PARAMS = 1415
+};
+static const int IF_W[NIFCE] = {O_IF0_W, O_IF1_W, O_IF2_W};
+static const int IF_B[NIFCE] = {O_IF0_B, O_IF1_B, O_IF2_B};
+
+/* Causal offsets (dy, dx) of the 16 spatial context values, nearest first. */
+static const int CTX_DY[NCTX] = {0, -1, -1, -1, 0, -2, -1, -1, -2, -2, -2, -2, 0, -3, -1, -1};
+static const int CTX_DX[NCTX] = {-1, 0, -1, 1, -2, 0, -2, 2, -1, 1, -2, 2, -3, 0, -3, 3};
+
+typedef struct {
+    int H, W;
+    int h[NG], w[NG];
+    int64_t off[NG + 1];
+} geom_t;
+
+static void geom_init(geom_t* g, int H, int W) {
+    g->H = H;
+    g->W = W;
+    g->off[0] = 0;
+    for (int k = 0; k < NG; ++k) {
+        g->h[k] = (H + (1 << k) - 1) >> k; /* ceil(H / 2^k) */
+        g->w[k] = (W + (1 << k) - 1) >> k;
+        g->off[k + 1] = g->off[k] + (int64_t)g->h[k] * g->w[k];
+    }
+}
+
+int orc_param_count(void) { return N_PARAMS; }
+
+int64_t orc_latent_count(int H, int W) {
+    geom_t g;
+    geom_init(&g, H, W);
+    return g.off[NG];
+}
+
+void orc_grid_shape(int H, int W, int k, int* hk, int* wk) {
+    geom_t g;
+    geom_init(&g, H, W);
+    *hk = g.h[k];
+    *wk = g.w[k];
+}
+
+void orc_context_offsets(int* dy, int* dx) {
+    for (int n = 0; n < NCTX; ++n) {
+        dy[n] = CTX_DY[n];
+        dx[n] = CTX_DX[n];
+    }
+}
+
+/* ----------------------------------------------------------------------------------------
+ * Counter-based uniform noise.  SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014)
+ * applied to  seed XOR ((t * 2^32 + i) * golden_gamma);  the top 24 bits give u in [-1/2, 1/2).
+ * ---------------------------------------------------------------------------------------- */
+uint64_t orc_splitmix64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+double orc_noise(uint64_t seed, int64_t t, int64_t i) {
+    uint64_t ctr = ((uint64_t)t << 32) + (uint64_t)i;
+    uint64_t h = orc_splitmix64_mix(seed ^ (ctr * 0x9E3779B97F4A7C15ULL));
+    return (double)(h >> 40) * (1.0 / 16777216.0) - 0.5;
+}
+
+/* ----------------------------------------------------------------------------------------
+ * Laplace interval probability, Eq. 3:  P = F(y + 1/2) - F(y - 1/2),  F the Laplace CDF with
+ * location mu and scale b.  Evaluated on the side of mu that avoids cancellation.
+ * Also returns dP/dy and dP/d(log b).
+ * ---------------------------------------------------------------------------------------- */
+static double lap_pdf(double z, double b) { return exp(-fabs(z) / b) / (2.0 * b); }
+
+double orc_laplace_prob(double y, double mu, double b, double* dp_dy, double* dp_dlogb) {
+    double lo = y - 0.5 - mu, hi = y + 0.5 - mu;
+    double p;
+    if (lo >= 0.0)
+        p = -0.5 * exp(-lo / b) * expm1(-1.0 / b);
+    else if (hi <= 0.0)
+        p = -0.5 * exp(hi / b) * expm1(-1.0 / b);
+    else
+        p = 1.0 - 0.5 * exp(lo / b) - 0.5 * exp(-hi / b);
+    double fh = lap_pdf(hi, b), fl = lap_pdf(lo, b);
+    if (dp_dy) *dp_dy = fh - fl;
+    /* dF(z)/db = -(z/b) f(z)  =>  dP/dlogb = b dP/db = -(hi f(hi) - lo f(lo)) */
+    if (dp_dlogb) *dp_dlogb = -(hi * fh - lo * fl);
+    return p;
+}
+
+/* ----------------------------------------------------------------------------------------
+ * ARM on one context vector (Eq. 4 with the stabilizer of Eq. 9).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    double c[AIN];
+    double a1[AH], h1[AH], a2[AH], h2[AH];
+    double mu, s_raw, logb, b;
+} arm_act_t;
+
+static void arm_forward(const double* P, arm_act_t* A) {
+    for (int o = 0; o < AH; ++o) {
+        double acc = P[O_ARM_B1 + o];
+        for (int i = 0; i < AIN; ++i) acc += P[O_ARM_W1 + o * AIN + i] * A->c[i];
+        A->a1[o] = acc;
+        A->h1[o] = acc > 0.0 ? acc : 0.0;
+    }
+    for (int o = 0; o < AH; ++o) {
+        double acc = P[O_ARM_B2 + o];
+        for (int i = 0; i < AH; ++i) acc += P[O_ARM_W2 + o * AH + i] * A->h1[i];
+        A->a2[o] = acc;
+        A->h2[o] = acc > 0.0 ? acc : 0.0;
+    }
+    double out[2];
+    for (int o = 0; o < 2; ++o) {
+        double acc = P[O_ARM_B3 + o] + P[O_ARM_BS + o];
+        for (int i = 0; i < AH; ++i) acc += P[O_ARM_W3 + o * AH + i] * A->h2[i];
+        for (int i = 0; i < AIN; ++i) acc += P[O_ARM_WS + o * AIN + i] * A->c[i];
+        out[o] = acc;
+    }
+    A->mu = out[0];
+    A->s_raw = out[1];
+    A->logb = fmin(fmax(out[1], LOGB_MIN), LOGB_MAX);
+    A->b = exp(A->logb);
+}
+
+/* Adjoint of arm_forward: given dL/dmu and dL/dlogb (after the clamp), accumulate parameter
+ * gradients into G and return dL/dc. */
+static void arm_backward(const double* P, const arm_act_t* A, double dmu, double dlogb, double* G,
+                         double* dc) {
+    double ds = (A->s_raw >= LOGB_MIN && A->s_raw <= LOGB_MAX) ? dlogb : 0.0;
+    double dout[2] = {dmu, ds};
+    double dh2[AH], da2[AH], dh1[AH], da1[AH];
+    for (int i = 0; i < AIN; ++i) dc[i] = 0.0;
+    for (int i = 0; i < AH; ++i) dh2[i] = 0.0;
+    for (int o = 0; o < 2; ++o) {
+        G[O_ARM_B3 + o] += dout[o];
+        G[O_ARM_BS + o] += dout[o];
+        for (int i = 0; i < AH; ++i) {
+            G[O_ARM_W3 + o * AH + i] += dout[o] * A->h2[i];
+            dh2[i] += P[O_ARM_W3 + o * AH + i] * dout[o];
+        }
+        for (int i = 0; i < AIN; ++i) {
+            G[O_ARM_WS + o * AIN + i] += dout[o] * A->c[i];
+            dc[i] += P[O_ARM_WS + o * AIN + i] * dout[o];
+        }
+    }
+    for (int o = 0; o < AH; ++o) da2[o] = A->a2[o] > 0.0 ? dh2[o] : 0.0;
+    for (int i = 0; i < AH; ++i) dh1[i] = 0.0;
+    for (int o = 0; o < AH; ++o) {
+        G[O_ARM_B2 + o] += da2[o];
+        for (int i = 0; i < AH; ++i) {
+            G[O_ARM_W2 + o * AH + i] += da2[o] * A->h1[i];
+            dh1[i] += P[O_ARM_W2 + o * AH + i] * da2[o];
+        }
+    }
+    for (int o = 0; o < AH; ++o) da1[o] = A->a1[o] > 0.0 ? dh1[o] : 0.0;
+    for (int o = 0; o < AH; ++o) {
+        G[O_ARM_B1 + o] += da1[o];
+        for (int i = 0; i < AIN; ++i) {
+            G[O_ARM_W1 + o * AIN + i] += da1[o] * A->c[i];
+            dc[i] += P[O_ARM_W1 + o * AIN + i] * da1[o];
+        }
+    }
+}
+
+/* Number of coarser grids feeding the IFCE of grid k (0 when grid k has no IFCE). */
+static int ifce_inputs(int k) { return (k < NIFCE && k < NG - 1) ? NG - k - 1 : 0; }
+
+/* Builds c_i = concat(s_i, f_i) for latent (k, r, c) of the relaxed latents yt.  r_i holds the
+ * nearest-neighbour co-located values of the coarser grids k+1..L-1 (Sec. III-A2). */
+static void build_context(const geom_t* g, const double* P, const double* yt, int k, int r, int c,
+                          double* ctx, double* rvec) {
+    const double* yk = yt + g->off[k];
+    for (int n = 0; n < NCTX; ++n) {
+        int rr = r + CTX_DY[n], cc = c + CTX_DX[n];
+        ctx[n] = (rr >= 0 && rr < g->h[k] && cc >= 0 && cc < g->w[k]) ? yk[(int64_t)rr * g->w[k] + cc]
+                                                                      : 0.0;
+    }
+    int nin = ifce_inputs(k);
+    for (int j = 0; j < nin; ++j) {
+        int gj = k + 1 + j, sh = gj - k;
+        int rr = r >> sh, cc = c >> sh;
+        if (rr > g->h[gj] - 1) rr = g->h[gj] - 1;
+        if (cc > g->w[gj] - 1) cc = g->w[gj] - 1;
+        rvec[j] = yt[g->off[gj] + (int64_t)rr * g->w[gj] + cc];
+    }
+    for (int o = 0; o < NF; ++o) {
+        double acc = 0.0;
+        if (nin > 0) {
+            acc = P[IF_B[k] + o];
+            for (int j = 0; j < nin; ++j) acc += P[IF_W[k] + o * nin + j] * rvec[j];
+        }
+        ctx[NCTX + o] = acc;
+    }
+}
+
+/* ----------------------------------------------------------------------------------------
+ * Upsampling stage (Sec. III-B, Eq. 7): x2 separable symmetric 8-tap filter [a b c d d c b a]
+ * as a transposed convolution with replicate padding; output cropped to (th, tw).
+ * Polyphase form per axis, X indices clamped to [0, n-1]:
+ *   out[2p]   = a X[p-2] + c X[p-1] + d X[p]   + b X[p+1]
+ *   out[2p+1] = b X[p-1] + d X[p]   + c X[p+1] + a X[p+2]
+ * Rows (the W axis) first, then columns.
+ * ---------------------------------------------------------------------------------------- */
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* tap index (0=a,1=b,2=c,3=d) and input offset of the 4 taps of output position o */
+static void poly_taps(int o, int* tap, int* src) {
+    int p = o >> 1;
+    if ((o & 1) == 0) {
+        tap[0] = 0; src[0] = p - 2;
+        tap[1] = 2; src[1] = p - 1;
+        tap[2] = 3; src[2] = p;
+        tap[3] = 1; src[3] = p + 1;
+    } else {
+        tap[0] = 1; src[0] = p - 1;
+        tap[1] = 3; src[1] = p;
+        tap[2] = 2; src[2] = p + 1;
+        tap[3] = 0; src[3] = p + 2;
+    }
+}
+
+void orc_upsample(int sh, int sw, int th, int tw, const double* taps, const double* x, double* out) {
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)sh * tw);
+    for (int r = 0; r < sh; ++r)
+        for (int o = 0; o < tw; ++o) {
+            int tap[4], src[4];
+            poly_taps(o, tap, src);
+            double acc = 0.0;
+            for (int q = 0; q < 4; ++q) acc += taps[tap[q]] * x[(int64_t)r * sw + clampi(src[q], 0, sw - 1)];
+            tmp[(int64_t)r * tw + o] = acc;
+        }
+    for (int o = 0; o < th; ++o)
+        for (int c = 0; c < tw; ++c) {
+            int tap[4], src[4];
+            poly_taps(o, tap, src);
+            double acc = 0.0;
+            for (int q = 0; q < 4; ++q) acc += taps[tap[q]] * tmp[(int64_t)clampi(src[q], 0, sh - 1) * tw + c];
+            out[(int64_t)o * tw + c] = acc;
+        }
+    free(tmp);
+}
+
+/* Adjoint of orc_upsample: scatter dout back to dx and accumulate the 4 tap gradients. */
+static void upsample_adjoint(int sh, int sw, int th, int tw, const double* taps, const double* x,
+                             const double* dout, double* dx, double* dtaps) {
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)sh * tw);
+    double* dtmp = (double*)calloc((size_t)sh * tw, sizeof(double));
+    for (int r = 0; r < sh; ++r)
+        for (int o = 0; o < tw; ++o) {
+            int tap[4], src[4];
+            poly_taps(o, tap, src);
+            double acc = 0.0;
+            for (int q = 0; q < 4; ++q) acc += taps[tap[q]] * x[(int64_t)r * sw + clampi(src[q], 0, sw - 1)];
+            tmp[(int64_t)r * tw + o] = acc;
+        }
+    for (int o = 0; o < th; ++o)
+        for (int c = 0; c < tw; ++c) {
+            int tap[4], src[4];
+            poly_taps(o, tap, src);
+            double g = dout[(int64_t)o * tw + c];
+            for (int q = 0; q < 4; ++q) {
+                int64_t si = (int64_t)clampi(src[q], 0, sh - 1) * tw + c;
+                dtaps[tap[q]] += g * tmp[si];
+                dtmp[si] += g * taps[tap[q]];
+            }
+        }
+    for (int r = 0; r < sh; ++r)
+        for (int o = 0; o < tw; ++o) {
+            int tap[4], src[4];
+            poly_taps(o, tap, src);
+            double g = dtmp[(int64_t)r * tw + o];
+            for (int q = 0; q < 4; ++q) {
+                int64_t si = (int64_t)r * sw + clampi(src[q], 0, sw - 1);
+                dtaps[tap[q]] += g * x[si];
+                dx[si] += g * taps[tap[q]];
+            }
+        }
+    free(tmp);
+    free(dtmp);
+}
+
+/* ----------------------------------------------------------------------------------------
+ * 3x3 residual convolution, 3 -> 3 channels, replicate padding (cross-correlation):
+ *   out[o][y][x] = in[o][y][x] + b[o] + sum_{i,ky,kx} W[o][i][ky][kx] in[i][y+ky-1][x+kx-1]
+ * ---------------------------------------------------------------------------------------- */
+void orc_conv3x3_res(int H, int W, const double* Wt, const double* b, const double* in, double* out) {
+    int64_t HW = (int64_t)H * W;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int o = 0; o < NCH; ++o) {
+                double acc = in[o * HW + (int64_t)y * W + x] + b[o];
+                for (int i = 0; i < NCH; ++i)
+                    for (int ky = 0; ky < 3; ++ky)
+                        for (int kx = 0; kx < 3; ++kx) {
+                            int yy = clampi(y + ky - 1, 0, H - 1), xx = clampi(x + kx - 1, 0, W - 1);
+                            acc += Wt[((o * NCH + i) * 3 + ky) * 3 + kx] * in[i * HW + (int64_t)yy * W + xx];
+                        }
+                out[o * HW + (int64_t)y * W + x] = acc;
+            }
+}
+
+/* Adjoint of orc_conv3x3_res: din += dout + conv^T(dout); dW, db accumulated. */
+static void conv3x3_res_adjoint(int H, int W, const double* Wt, const double* in, const double* dout,
+                                double* din, double* dW, double* db) {
+    int64_t HW = (int64_t)H * W;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int o = 0; o < NCH; ++o) {
+                double g = dout[o * HW + (int64_t)y * W + x];
+                din[o * HW + (int64_t)y * W + x] += g;
+                db[o] += g;
+                for (int i = 0; i < NCH; ++i)
+                    for (int ky = 0; ky < 3; ++ky)
+                        for (int kx = 0; kx < 3; ++kx) {
+                            int yy = clampi(y + ky - 1, 0, H - 1), xx = clampi(x + kx - 1, 0, W - 1);
+                            int widx = ((o * NCH + i) * 3 + ky) * 3 + kx;
+                            int64_t si = i * HW + (int64_t)yy * W + xx;
+                            dW[widx] += g * in[si];
+                            din[si] += g * Wt[widx];
+                        }
+            }
+}
+
+/* ----------------------------------------------------------------------------------------
+ * Synthesis 1x1 MLP with stabilizer (Eq. 8, Eq. 9): t = W2 gelu(W1 z + b1) + b2 + Ws z + bs.
+ * GELU in its exact erf form.
+ * ---------------------------------------------------------------------------------------- */
+static double gelu(double a) { return 0.5 * a * (1.0 + erf(a / sqrt(2.0))); }
+static double gelu_grad(double a) {
+    return 0.5 * (1.0 + erf(a / sqrt(2.0))) + a * exp(-0.5 * a * a) / sqrt(2.0 * M_PI);
+}
+
+static void synth_pixel(const double* P, const double* z, double* a, double* t) {
+    for (int o = 0; o < SH; ++o) {
+        double acc = P[O_SYN_B1 + o];
+        for (int i = 0; i < NG; ++i) acc += P[O_SYN_W1 + o * NG + i] * z[i];
+        a[o] = acc;
+    }
+    for (int o = 0; o < NCH; ++o) {
+        double acc = P[O_SYN_B2 + o] + P[O_SYN_BS + o];
+        for (int i = 0; i < SH; ++i) acc += P[O_SYN_W2 + o * SH + i] * gelu(a[i]);
+        for (int i = 0; i < NG; ++i) acc += P[O_SYN_WS + o * NG + i] * z[i];
+        t[o] = acc;
+    }
+}
+
+/* ----------------------------------------------------------------------------------------
+ * Whole forward and adjoint.
+ * ---------------------------------------------------------------------------------------- */
+enum { MODE_NOISE = 0, MODE_HARD = 1, MODE_IDENTITY = 2 };
+
+typedef struct {
+    geom_t g;
+    double* yt;         /* relaxed latents, all grids                                 */
+    double* up[NG];     /* up[m]: channels for grids m+1..L-1 upsampled to grid m      */
+    double* z;          /* dense representation [L][H][W]                              */
+    double* t;          /* synthesis output before the residual convs [3][H][W]       */
+    double* x1;         /* after conv 1                                                */
+    double* xh;         /* reconstruction                                              */
+    double* mu;
+    double* logb;
+    double* bits;
+} fwd_t;
+
+static void fwd_free(fwd_t* F) {
+    free(F->yt);
+    for (int m = 0; m < NG; ++m) free(F->up[m]);
+    free(F->z);
+    free(F->t);
+    free(F->x1);
+    free(F->xh);
+    free(F->mu);
+    free(F->logb);
+    free(F->bits);
+}
+
+/* channels of S_m = [y~^(m), up[m]] are grids m..L-1; return pointer to channel j (grid m+j). */
+static const double* stage_channel(const fwd_t* F, int m, int j) {
+    if (j == 0) return F->yt + F->g.off[m];
+    return F->up[m] + (int64_t)(j - 1) * F->g.h[m] * F->g.w[m];
+}
+
+static double run_forward(int H, int W, const double* img, const double* y, const double* P, int mode,
+                          uint64_t seed, int64_t t, double lambda, fwd_t* F, double* rate_out,
+                          double* mse_out) {
+    geom_init(&F->g, H, W);
+    const geom_t* g = &F->g;
+    int64_t N = g->off[NG], HW = (int64_t)H * W;
+    F->yt = (double*)malloc(sizeof(double) * N);
+    F->mu = (double*)malloc(sizeof(double) * N);
+    F->logb = (double*)malloc(sizeof(double) * N);
+    F->bits = (double*)malloc(sizeof(double) * N);
+    for (int64_t i = 0; i < N; ++i) {
+        if (mode == MODE_NOISE)
+            F->yt[i] = y[i] + orc_noise(seed, t, i);
+        else if (mode == MODE_HARD)
+            F->yt[i] = rint(y[i]);
+        else
+            F->yt[i] = y[i];
+    }
+    /* entropy model: Eqs. 2-5, 9, 11 */
+    for (int k = 0; k < NG; ++k) {
+#pragma omp parallel for schedule(static)
+        for (int r = 0; r < g->h[k]; ++r)
+            for (int c = 0; c < g->w[k]; ++c) {
+                int64_t i = g->off[k] + (int64_t)r * g->w[k] + c;
+                arm_act_t A;
+                double rv[NG];
+                build_context(g, P, F->yt, k, r, c, A.c, rv);
+                arm_forward(P, &A);
+                double p = orc_laplace_prob(F->yt[i], A.mu, A.b, NULL, NULL);
+                F->mu[i] = A.mu;
+                F->logb[i] = A.logb;
+                F->bits[i] = -log2(fmax(p, P_MIN));
+            }
+    }
+    double rate = 0.0;
+    for (int64_t i = 0; i < N; ++i) rate += F->bits[i];
+    /* upsampling cascade: S_{L-1} = y~^(L-1); S_{m} = [y~^(m), U_{m+1}(S_{m+1})] */
+    for (int m = 0; m < NG; ++m) F->up[m] = NULL;
+    for (int m = NG - 2; m >= 0; --m) {
+        int nch = NG - m - 1; /* channels of up[m] = channels of S_{m+1} */
+        int64_t sz = (int64_t)g->h[m] * g->w[m];
+        F->up[m] = (double*)malloc(sizeof(double) * nch * sz);
+        const double* taps = P + O_UP + 4 * m; /* stage s = m + 1 */
+        for (int j = 0; j < nch; ++j)
+            orc_upsample(g->h[m + 1], g->w[m + 1], g->h[m], g->w[m], taps, stage_channel(F, m + 1, j),
+                         F->up[m] + j * sz);
+    }
+    F->z = (double*)malloc(sizeof(double) * NG * HW);
+    for (int j = 0; j < NG; ++j) memcpy(F->z + j * HW, stage_channel(F, 0, j), sizeof(double) * HW);
+    /* synthesis */
+    F->t = (double*)malloc(sizeof(double) * NCH * HW);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < HW; ++p) {
+        double z[NG], a[SH], tt[NCH];
+        for (int j = 0; j < NG; ++j) z[j] = F->z[j * HW + p];
+        synth_pixel(P, z, a, tt);
+        for (int o = 0; o < NCH; ++o) F->t[o * HW + p] = tt[o];
+    }
+    F->x1 = (double*)malloc(sizeof(double) * NCH * HW);
+    F->xh = (double*)malloc(sizeof(double) * NCH * HW);
+    orc_conv3x3_res(H, W, P + O_CV1_W, P + O_CV1_B, F->t, F->x1);
+    orc_conv3x3_res(H, W, P + O_CV2_W, P + O_CV2_B, F->x1, F->xh);
+    double se = 0.0;
+    for (int64_t q = 0; q < NCH * HW; ++q) {
+        double d = F->xh[q] - img[q];
+        se += d * d;
+    }
+    double mse = se / (double)(NCH * HW);
+    *rate_out = rate;
+    *mse_out = mse;
+    return mse + lambda * rate / (double)HW;
+}
+
+double orc_forward(int H, int W, const double* img, const double* y, const double* P, int mode,
+                   uint64_t seed, int64_t t, double lambda, double* rate_out, double* mse_out,
+                   double* mu_out, double* logb_out, double* bits_out, double* xhat_out) {
+    fwd_t F;
+    memset(&F, 0, sizeof(F));
+    double loss = run_forward(H, W, img, y, P, mode, seed, t, lambda, &F, rate_out, mse_out);
+    int64_t N = F.g.off[NG], HW = (int64_t)H * W;
+    if (mu_out) memcpy(mu_out, F.mu, sizeof(double) * N);
+    if (logb_out) memcpy(logb_out, F.logb, sizeof(double) * N);
+    if (bits_out) memcpy(bits_out, F.bits, sizeof(double) * N);
+    if (xhat_out) memcpy(xhat_out, F.xh, sizeof(double) * NCH * HW);
+    fwd_free(&F);
+    return loss;
+}
+
+/* Loss and its gradient with respect to the continuous latents y and the parameters.
+ * With the additive noise proxy, dL/dy = dL/dy~. */
+double orc_loss_grad(int H, int W, const double* img, const double* y, const double* P, int mode,
+                     uint64_t seed, int64_t t, double lambda, double* rate_out, double* mse_out,
+                     double* gy, double* gP) {
+    fwd_t F;
+    memset(&F, 0, sizeof(F));
+    double loss = run_forward(H, W, img, y, P, mode, seed, t, lambda, &F, rate_out, mse_out);
+    const geom_t* g = &F.g;
+    int64_t N = g->off[NG], HW = (int64_t)H * W;
+    double* gyt = (double*)calloc(N, sizeof(double));
+    for (int q = 0; q < N_PARAMS; ++q) gP[q] = 0.0;
+
+    /* distortion: D = mean (xh - x)^2 */
+    double* dxh = (double*)malloc(sizeof(double) * NCH * HW);
+    for (int64_t q = 0; q < NCH * HW; ++q) dxh[q] = 2.0 * (F.xh[q] - img[q]) / (double)(NCH * HW);
+    double* dx1 = (double*)calloc(NCH * HW, sizeof(double));
+    double* dt = (double*)calloc(NCH * HW, sizeof(double));
+    conv3x3_res_adjoint(H, W, P + O_CV2_W, F.x1, dxh, dx1, gP + O_CV2_W, gP + O_CV2_B);
+    conv3x3_res_adjoint(H, W, P + O_CV1_W, F.t, dx1, dt, gP + O_CV1_W, gP + O_CV1_B);
+
+    /* synthesis adjoint; per-row partial parameter gradients summed serially afterwards */
+    double* dz = (double*)calloc(NG * HW, sizeof(double));
+    double* rowg = (double*)calloc((size_t)H * N_PARAMS, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int yy = 0; yy < H; ++yy) {
+        double* Gr = rowg + (size_t)yy * N_PARAMS; /* this row's partial gradient */
+        for (int xx = 0; xx < W; ++xx) {
+            int64_t p = (int64_t)yy * W + xx;
+            double z[NG], a[SH], tt[NCH], dtt[NCH], ga[SH];
+            for (int j = 0; j < NG; ++j) z[j] = F.z[j * HW + p];
+            synth_pixel(P, z, a, tt);
+            for (int o = 0; o < NCH; ++o) dtt[o] = dt[o * HW + p];
+            double dzp[NG] = {0};
+            for (int i = 0; i < SH; ++i) ga[i] = 0.0;
+            for (int o = 0; o < NCH; ++o) {
+                Gr[O_SYN_B2 + o] += dtt[o];
+                Gr[O_SYN_BS + o] += dtt[o];
+                for (int i = 0; i < SH; ++i) {
+                    Gr[O_SYN_W2 + o * SH + i] += dtt[o] * gelu(a[i]);
+                    ga[i] += P[O_SYN_W2 + o * SH + i] * dtt[o];
+                }
+                for (int i = 0; i < NG; ++i) {
+                    Gr[O_SYN_WS + o * NG + i] += dtt[o] * z[i];
+                    dzp[i] += P[O_SYN_WS + o * NG + i] * dtt[o];
+                }
+            }
+            for (int o = 0; o < SH; ++o) {
+                double da = ga[o] * gelu_grad(a[o]);
+                Gr[O_SYN_B1 + o] += da;
+                for (int i = 0; i < NG; ++i) {
+                    Gr[O_SYN_W1 + o * NG + i] += da * z[i];
+                    dzp[i] += P[O_SYN_W1 + o * NG + i] * da;
+                }
+            }
+            for (int j = 0; j < NG; ++j) dz[j * HW + p] = dzp[j];
+        }
+    }
+    for (int yy = 0; yy < H; ++yy)
+        for (int q = O_SYN_W1; q < O_CV1_W; ++q) gP[q] += rowg[(size_t)yy * N_PARAMS + q];
+    free(rowg);
+
+    /* upsampling adjoint: dS_0 = dz; for m = 1..L-1: dS_m = U_m^T(dup[m-1]) */
+    double* dS = dz; /* channels of S_0 */
+    for (int m = 0; m < NG; ++m) {
+        int64_t sz = (int64_t)g->h[m] * g->w[m];
+        int nch = NG - m; /* channels of S_m */
+        for (int64_t q = 0; q < sz; ++q) gyt[g->off[m] + q] += dS[q];
+        if (m == NG - 1) break;
+        int64_t szn = (int64_t)g->h[m + 1] * g->w[m + 1];
+        double* dSn = (double*)calloc((size_t)(nch - 1) * szn, sizeof(double));
+        for (int j = 0; j < nch - 1; ++j)
+            upsample_adjoint(g->h[m + 1], g->w[m + 1], g->h[m], g->w[m], P + O_UP + 4 * m,
+                             stage_channel(&F, m + 1, j), dS + (int64_t)(j + 1) * sz, dSn + j * szn,
+                             gP + O_UP + 4 * m);
+        if (dS != dz) free(dS);
+        dS = dSn;
+    }
+    if (dS != dz) free(dS);
+    free(dz);
+
+    /* entropy-model adjoint: per-latent contributions computed in parallel, scattered serially */
+    double dbits = lambda / (double)HW;
+    const int NARM = O_UP; /* ARM + IFCE parameter block */
+    for (int k = 0; k < NG; ++k) {
+        int h = g->h[k], w = g->w[k];
+        double* dcs = (double*)malloc(sizeof(double) * (size_t)h * w * AIN);
+        double* rvs = (double*)malloc(sizeof(double) * (size_t)h * w * NG);
+        double* ddir = (double*)malloc(sizeof(double) * (size_t)h * w);
+        double* rowa = (double*)calloc((size_t)h * NARM, sizeof(double));
+#pragma omp parallel for schedule(static)
+        for (int r = 0; r < h; ++r) {
+            double* Gr = rowa + (size_t)r * NARM;
+            for (int c = 0; c < w; ++c) {
+                int64_t li = (int64_t)r * w + c, i = g->off[k] + li;
+                arm_act_t A;
+                double* rv = rvs + li * NG;
+                build_context(g, P, F.yt, k, r, c, A.c, rv);
+                arm_forward(P, &A);
+                double dpdy, dpdlb;
+                double p = orc_laplace_prob(F.yt[i], A.mu, A.b, &dpdy, &dpdlb);
+                double dp = (p >= P_MIN) ? -dbits / (p * log(2.0)) : 0.0;
+                ddir[li] = dp * dpdy;
+                arm_backward(P, &A, -dp * dpdy, dp * dpdlb, Gr, dcs + li * AIN);
+            }
+        }
+        for (int r = 0; r < h; ++r)
+            for (int q = 0; q < NARM; ++q) gP[q] += rowa[(size_t)r * NARM + q];
+        int nin = ifce_inputs(k);
+        for (int r = 0; r < h; ++r)
+            for (int c = 0; c < w; ++c) {
+                int64_t li = (int64_t)r * w + c;
+                const double* dc = dcs + li * AIN;
+                gyt[g->off[k] + li] += ddir[li];
+                for (int n = 0; n < NCTX; ++n) {
+                    int rr = r + CTX_DY[n], cc = c + CTX_DX[n];
+                    if (rr >= 0 && rr < h && cc >= 0 && cc < w) gyt[g->off[k] + (int64_t)rr * w + cc] += dc[n];
+                }
+                if (nin > 0) {
+                    const double* df = dc + NCTX;
+                    for (int o = 0; o < NF; ++o) {
+                        gP[IF_B[k] + o] += df[o];
+                        for (int j = 0; j < nin; ++j) gP[IF_W[k] + o * nin + j] += df[o] * rvs[li * NG + j];
+                    }
+                    for (int j = 0; j < nin; ++j) {
+                        int gj = k + 1 + j, sh = gj - k;
+                        int rr = r >> sh, cc = c >> sh;
+                        if (rr > g->h[gj] - 1) rr = g->h[gj] - 1;
+                        if (cc > g->w[gj] - 1) cc = g->w[gj] - 1;
+                        double acc = 0.0;
+                        for (int o = 0; o < NF; ++o) acc += P[IF_W[k] + o * nin + j] * df[o];
+                        gyt[g->off[gj] + (int64_t)rr * g->w[gj] + cc] += acc;
+                    }
+                }
+            }
+        free(dcs);
+        free(rvs);
+        free(ddir);
+        free(rowa);
+    }
+    /* y~ = y + u (or y): identity Jacobian; under hard rounding the gradient is zero */
+    for (int64_t i = 0; i < N; ++i) gy[i] = (mode == MODE_HARD) ? 0.0 : gyt[i];
+    free(gyt);
+    free(dxh);
+    free(dx1);
+    free(dt);
+    fwd_free(&F);
+    return loss;
+}
+
+/* ----------------------------------------------------------------------------------------
+ * Adam (Kingma & Ba), bias-corrected, no weight decay.  t_new is the 1-based step count.
+ * ---------------------------------------------------------------------------------------- */
+void orc_adam(int64_t n, double* p, const double* g, double* m, double* v, int64_t t_new, double lr,
+              double b1, double b2, double eps) {
+    double bc1 = 1.0 - pow(b1, (double)t_new), bc2 = 1.0 - pow(b2, (double)t_new);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        double mh = m[i] / bc1, vh = v[i] / bc2;
+        p[i] -= lr * mh / (sqrt(vh) + eps);
+    }
+}
+
+/* n_iters encoder iterations: loss+gradient at step t (noise keyed by t), then Adam on latents
+ * and parameters.  Per-iteration loss, rate and mse (before the update) are reported. */
+void orc_encode(int H, int W, const double* img, double* y, double* P, double* m_y, double* v_y,
+                double* m_p, double* v_p, int64_t* step, int n_iters, uint64_t seed, double lambda,
+                double lr, double b1, double b2, double eps, double* loss_out, double* rate_out,
+                double* mse_out) {
+    int64_t N = orc_latent_count(H, W);
+    double* gy = (double*)malloc(sizeof(double) * N);
+    double gP[N_PARAMS];
+    for (int it = 0; it < n_iters; ++it) {
+        double rate, mse;
+        double loss = orc_loss_grad(H, W, img, y, P, MODE_NOISE, seed, *step, lambda, &rate, &mse, gy, gP);
+        if (loss_out) loss_out[it] = loss;
+        if (rate_out) rate_out[it] = rate;
+        if (mse_out) mse_out[it] = mse;
+        *step += 1;
+        orc_adam(N, y, gy, m_y, v_y, *step, lr, b1, b2, eps);
+        orc_adam(N_PARAMS, P, gP, m_p, v_p, *step, lr, b1, b2, eps);
+    }
+    free(gy);
+}
+
+/* ----------------------------------------------------------------------------------------
+ * Integer decode-side entropy model (Sec. III-A2: integer, cross-platform decoding).
+ * Fixed point with 8 fractional bits: weights and biases w_q = rint(256 w); the spatial context
+ * enters as 256 * y^; each layer accumulates in 64-bit integers, adds the bias shifted to the
+ * product scale, shifts right by 8 (floor) and applies ReLU.  The outputs mu_q, logb_q are on a
+ * 1/256 grid; logb_q is clamped to [-1280, 1280].
+ * Integer CDF with 16-bit total mass:  C(t) = 65536 - E(s, t) for t >= 0, E(s, -t) otherwise, where
+ * E(s, u) ~ 2^15 exp(-u / (256 b_s)) = 2^15 2^(-v / 2^28) with v = u * K[s] and
+ * K[s] = rint(2^20 log2(e) exp(-s/256)).  With n = v >> 28, hi = bits 18..27 of v, lo = bits 8..17:
+ *   E = ((T_HI[hi] * T_LO[lo]) >> 15) >> n     (E = 0 once n >= 16),
+ * T_HI[j] = rint(2^15 2^(-j/2^10)), T_LO[j] = rint(2^15 2^(-j/2^20)): a coarse x fine split of the
+ * fractional exponent.  All tables are built here in FP64, independently of any other implementation.
+ * P_q16 = max(1, C(256 y^ + 128 - mu_q) - C(256 y^ - 128 - mu_q)).
+ * ---------------------------------------------------------------------------------------- */
+#define LOGBQ_MIN (-1280)
+#define LOGBQ_MAX (1280)
+static int64_t K_TAB[LOGBQ_MAX - LOGBQ_MIN + 1];
+static int64_t T_HI[1024], T_LO[1024];
+static int tabs_ready = 0;
+
+static void build_tables(void) {
+    if (tabs_ready) return;
+    for (int s = LOGBQ_MIN; s <= LOGBQ_MAX; ++s)
+        K_TAB[s - LOGBQ_MIN] = (int64_t)rint(1048576.0 * (1.0 / log(2.0)) * exp(-(double)s / 256.0));
+    for (int j = 0; j < 1024; ++j) {
+        T_HI[j] = (int64_t)rint(32768.0 * exp2(-(double)j / 1024.0));
+        T_LO[j] = (int64_t)rint(32768.0 * exp2(-(double)j / 1048576.0));
+    }
+    tabs_ready = 1;
+}
+
+int64_t orc_cdf_q16(int32_t s, int64_t t) {
+    build_tables();
+    int64_t u = t >= 0 ? t : -t;
+    int64_t v = u * K_TAB[s - LOGBQ_MIN];
+    int64_t n = v >> 28;
+    int64_t e = 0;
+    if (n < 16) e = ((T_HI[(v >> 18) & 1023] * T_LO[(v >> 8) & 1023]) >> 15) >> n;
+    return t >= 0 ? 65536 - e : e;
+}
+
+/* which = 0: K[idx] (idx = s + 1280), 1: T_HI[idx], 2: T_LO[idx] */
+int64_t orc_table_entry(int which, int idx) {
+    build_tables();
+    return which == 0 ? K_TAB[idx] : (which == 1 ? T_HI[idx] : T_LO[idx]);
+}
+
+static int64_t floor_shift8(int64_t v) { return v >> 8; } /* arithmetic shift = floor(v / 256) */
+static int64_t q8(float w) { return (int64_t)rint((double)w * 256.0); }
+
+/* Integer ARM for every latent of the hard-quantised grids q; writes mu_q, logb_q, P_q16. */
+void orc_decode_probs(int H, int W, const int32_t* q, const float* Pf, int32_t* mu_out,
+                      int32_t* logb_out, uint32_t* prob_out) {
+    build_tables();
+    geom_t g;
+    geom_init(&g, H, W);
+    for (int k = 0; k < NG; ++k) {
+        int nin = ifce_inputs(k);
+        for (int r = 0; r < g.h[k]; ++r)
+            for (int c = 0; c < g.w[k]; ++c) {
+                int64_t i = g.off[k] + (int64_t)r * g.w[k] + c;
+                int64_t ctx[AIN], h1[AH], h2[AH];
+                for (int n = 0; n < NCTX; ++n) {
+                    int rr = r + CTX_DY[n], cc = c + CTX_DX[n];
+                    int64_t v = (rr >= 0 && rr < g.h[k] && cc >= 0 && cc < g.w[k])
+                                    ? q[g.off[k] + (int64_t)rr * g.w[k] + cc]
+                                    : 0;
+                    ctx[n] = v * 256;
+                }
+                for (int o = 0; o < NF; ++o) {
+                    int64_t acc = 0;
+                    if (nin > 0) {
+                        acc = q8(Pf[IF_B[k] + o]);
+                        for (int j = 0; j < nin; ++j) {
+                            int gj = k + 1 + j, sh = gj - k;
+                            int rr = r >> sh, cc = c >> sh;
+                            if (rr > g.h[gj] - 1) rr = g.h[gj] - 1;
+                            if (cc > g.w[gj] - 1) cc = g.w[gj] - 1;
+                            acc += q8(Pf[IF_W[k] + o * nin + j]) *
+                                   (int64_t)q[g.off[gj] + (int64_t)rr * g.w[gj] + cc];
+                        }
+                    }
+                    ctx[NCTX + o] = acc;
+                }
+                for (int o = 0; o < AH; ++o) {
+                    int64_t acc = q8(Pf[O_ARM_B1 + o]) * 256;
+                    for (int n = 0; n < AIN; ++n) acc += q8(Pf[O_ARM_W1 + o * AIN + n]) * ctx[n];
+                    acc = floor_shift8(acc);
+                    h1[o] = acc > 0 ? acc : 0;
+                }
+                for (int o = 0; o < AH; ++o) {
+                    int64_t acc = q8(Pf[O_ARM_B2 + o]) * 256;
+                    for (int n = 0; n < AH; ++n) acc += q8(Pf[O_ARM_W2 + o * AH + n]) * h1[n];
+                    acc = floor_shift8(acc);
+                    h2[o] = acc > 0 ? acc : 0;
+                }
+                int64_t out[2];
+                for (int o = 0; o < 2; ++o) {
+                    int64_t acc = (q8(Pf[O_ARM_B3 + o]) + q8(Pf[O_ARM_BS + o])) * 256;
+                    for (int n = 0; n < AH; ++n) acc += q8(Pf[O_ARM_W3 + o * AH + n]) * h2[n];
+                    for (int n = 0; n < AIN; ++n) acc += q8(Pf[O_ARM_WS + o * AIN + n]) * ctx[n];
+                    out[o] = floor_shift8(acc);
+                }
+                int64_t mu = out[0];
+                int64_t s = out[1] < LOGBQ_MIN ? LOGBQ_MIN : (out[1] > LOGBQ_MAX ? LOGBQ_MAX : out[1]);
+                int64_t yq = (int64_t)q[i] * 256;
+                int64_t cp = orc_cdf_q16((int32_t)s, yq + 128 - mu);
+                int64_t cm = orc_cdf_q16((int32_t)s, yq - 128 - mu);
+                int64_t pq = cp - cm;
+                if (mu_out) mu_out[i] = (int32_t)mu;
+                if (logb_out) logb_out[i] = (int32_t)s;
+                if (prob_out) prob_out[i] = (uint32_t)(pq < 1 ? 1 : pq);
+            }
+    }
+}
+
+/* Decoder reconstruction from hard-quantised latents: upsampling + synthesis in FP64, x^ clamped
+ * to [0, 1] (Sec. III-B). */
+void orc_decode_image(int H, int W, const int32_t* q, const float* Pf, double* img_out) {
+    int64_t N = orc_latent_count(H, W);
+    double* y = (double*)malloc(sizeof(double) * N);
+    double P[N_PARAMS];
+    for (int64_t i = 0; i < N; ++i) y[i] = (double)q[i];
+    for (int j = 0; j < N_PARAMS; ++j) P[j] = (double)Pf[j];
+    double rate, mse;
+    int64_t HW = (int64_t)H * W;
+    double* zero = (double*)calloc(NCH * HW, sizeof(double));
+    fwd_t F;
+    memset(&F, 0, sizeof(F));
+    run_forward(H, W, zero, y, P, MODE_IDENTITY, 0, 0, 0.0, &F, &rate, &mse);
+    for (int64_t q2 = 0; q2 < NCH * HW; ++q2) img_out[q2] = fmin(fmax(F.xh[q2], 0.0), 1.0);
+    fwd_free(&F);
+    free(zero);
+    free(y);
+}

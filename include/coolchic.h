@@ -1,0 +1,175 @@
+/*
+ * coolchic.h -- C ABI of the GB300 (sm_103a) Cool-chic encoder-step library.
+ *
+ * The library runs the per-iteration encoder step of an overfitted image codec: forward and
+ * backward pass over every pixel and latent, then Adam (Cool-chic 5.0, Sec. IV-A, Eq. 10), plus
+ * the rate-distortion evaluation and the decoder (Sec. III).  Every step runs in hand-written CUDA
+ * kernels; the library never allocates device memory per call and never falls back to the CPU.
+ *
+ * Conventions (all entry points):
+ *   - Pointers marked [device] must point to device memory of the current CUDA device; [host]
+ *     pointers to host memory.  The caller owns every buffer.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *     stream-ordered and asynchronous unless marked "blocking".
+ *   - Return value: CC_OK (0) or a negative CC_ERR_* code.  On error, coolchic_last_error()
+ *     returns a thread-local message.  Argument checks run before any launch; a failed check
+ *     launches nothing.
+ *   - Floating point is FP32 on the device; loss reductions are finished in FP64.
+ *
+ * Architecture (fixed by this library; see cc_arch_t): C = 3 channels, L = 7 latent grids of one
+ * channel (grid k is ceil(H/2^k) x ceil(W/2^k), Sec. III-A1, Eq. 1), ARM over 16 causal
+ * neighbours + 4 inter-feature values from an IFCE on grids 0..2 (Sec. III-A2, Eq. 5), two hidden
+ * layers of 16 with ReLU and a linear stabilizer (Eq. 9), outputs (mu, log b); learned symmetric
+ * 8-tap x2 upsampling per stage (Sec. III-B, Eq. 7); synthesis 7 -> 40 (GELU) -> 3 with a 7 -> 3
+ * stabilizer, then two residual 3x3 convolutions 3 -> 3 (Eq. 8, Table II).
+ *
+ * Latent layout: one flat FP32 vector, grids concatenated k = 0..6, each row-major [h_k][w_k].
+ * Image layout: planar CHW FP32, values in [0, 1].
+ * Parameter layout: one flat FP32 vector of 1415 values; blocks in this order, matrices row-major
+ * [out][in]:  arm.w1[16][20] arm.b1[16] arm.w2[16][16] arm.b2[16] arm.w3[2][16] arm.b3[2]
+ *             arm.ws[2][20] arm.bs[2] ifce0.w[4][6] ifce0.b[4] ifce1.w[4][5] ifce1.b[4]
+ *             ifce2.w[4][4] ifce2.b[4] up.taps[6][4] syn.w1[40][7] syn.b1[40] syn.w2[3][40]
+ *             syn.b2[3] syn.ws[3][7] syn.bs[3] conv1.w[3][3][3][3] conv1.b[3] conv2.w[3][3][3][3]
+ *             conv2.b[3].   Use coolchic_param_block() to enumerate them.
+ */
+#ifndef COOLCHIC_H
+#define COOLCHIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CC_OK 0
+#define CC_ERR_ARG (-1)         /* invalid argument (shape, pointer, value)          */
+#define CC_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed       */
+#define CC_ERR_WORKSPACE (-3)   /* workspace missing, too small or misaligned        */
+#define CC_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up                */
+#define CC_ERR_UNSUPPORTED (-5) /* architecture field other than the supported one   */
+
+/* Decoder architecture.  Only H and W are free; every other field must hold the value in
+ * brackets (coolchic_arch_init fills them), otherwise calls return CC_ERR_UNSUPPORTED. */
+typedef struct {
+    int32_t C;          /* [3] image channels                                     */
+    int32_t H, W;       /* image height and width, 1 .. 16384                      */
+    int32_t L;          /* [7] latent grids                                        */
+    int32_t n_ctx;      /* [16] spatial context size                               */
+    int32_t ifce_dim;   /* [4] inter-feature context width F                       */
+    int32_t ifce_grids; /* [3] grids 0..ifce_grids-1 carry an IFCE                 */
+    int32_t arm_hidden; /* [16]                                                    */
+    int32_t arm_layers; /* [2]                                                     */
+    int32_t syn_hidden; /* [40]                                                    */
+    int32_t n_resconv;  /* [2]                                                     */
+    int32_t up_taps;    /* [8]                                                     */
+    int32_t stabilizer; /* [1]                                                     */
+} cc_arch_t;
+
+/* Encoder hyper-parameters.  lambda weighs the rate in bits per pixel (Eq. 10 with R divided by
+ * H*W); Adam (Sec. IV-B) uses lr, beta1, beta2, eps for latents and parameters alike. */
+typedef struct {
+    float lambda, lr, beta1, beta2, eps;
+    int32_t noise_mode; /* 0: y~ = y + u, u ~ U[-1/2, 1/2) from a counter hash of (seed, step, i) */
+    uint64_t seed;
+} cc_hparams_t;
+
+/* Encoder state, all [device], caller-owned: latents, params and their Adam moments (same
+ * sizes), and the step counter (one int64; the number of Adam steps already taken, which also
+ * keys the noise of the next iteration). */
+typedef struct {
+    float *latents, *params, *m_lat, *v_lat, *m_par, *v_par;
+    int64_t* step;
+} cc_state_t;
+
+/* Rate-distortion record: loss = mse + lambda * rate_bits / (H*W). */
+typedef struct {
+    double loss, rate_bits, mse;
+} cc_rd_t;
+
+/* Relaxation of the latents used by a forward pass (Sec. IV-C). */
+#define CC_RELAX_NOISE 0    /* y + u(seed, step, i)                 */
+#define CC_RELAX_HARD 1     /* rint(y), round half to even (Eq. 12) */
+#define CC_RELAX_IDENTITY 2 /* y as given                           */
+
+/* Fill *arch with the supported architecture for an H x W image.  Returns CC_ERR_ARG for a
+ * NULL pointer or a size outside 1..16384. */
+int coolchic_arch_init(cc_arch_t* arch, int32_t H, int32_t W);
+
+/* Number of latents (sum over grids of h_k * w_k) and of parameters (1415); -1 on a bad arch. */
+int64_t coolchic_latent_count(const cc_arch_t* arch);
+int64_t coolchic_param_count(const cc_arch_t* arch);
+
+/* Parameter block `index` (0-based, in storage order): its name (static string), offset and
+ * length in floats.  Returns CC_ERR_ARG past the last block. */
+int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int32_t* length);
+
+/* Bytes of device workspace one job needs.  `flags` bit 0: room for stored forward activations
+ * (coolchic_forward with store_activations = 1).  Returns 0 on a bad arch. */
+size_t coolchic_workspace_bytes(const cc_arch_t* arch, int32_t flags);
+
+/* Encoder iterations (Sec. IV-A..B): for it = 0..n_iters-1, relax the latents with the noise of
+ * step *state->step, run the forward pass and its adjoint over all latents and pixels, take one
+ * Adam step on latents and parameters, increment *state->step.
+ *   image      [device] CHW FP32, 3*H*W values.
+ *   state      [host struct of device pointers], updated in place.
+ *   rd_per_iter [device, nullable] n_iters records: loss, rate, mse measured before each update.
+ *   workspace  [device] coolchic_workspace_bytes(arch, 0) bytes, 256-byte aligned; contents are
+ *              scratch between calls.
+ * Asynchronous on `stream`; may be captured in a CUDA graph. */
+int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
+                         const cc_state_t* state, int32_t n_iters, cc_rd_t* rd_per_iter,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/* Forward pass only (Eq. 10): rate of the relaxed latents (Eq. 3, Eq. 11), reconstruction and
+ * distortion.  relax = CC_RELAX_*; `step` keys the noise for CC_RELAX_NOISE.
+ *   latents, params [device];  rd_out [device, nullable] one record;
+ *   xhat_out [device, nullable] reconstructed CHW image (not clamped);
+ *   store_activations: 1 keeps the activations the adjoint needs in the workspace (workspace
+ *   sized with flags = 1) so that coolchic_backward can skip their recomputation. */
+int coolchic_forward(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
+                     const float* latents, const float* params, int64_t step, int32_t relax,
+                     int32_t store_activations, cc_rd_t* rd_out, float* xhat_out, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
+/* Adjoint of coolchic_forward: gradients of the loss with respect to the latents and the
+ * parameters, scaled by grad_scale (dLoss/dOutput of a caller's graph).
+ *   use_stored: 1 reads the activations a preceding coolchic_forward(store_activations = 1) left
+ *   in the same workspace with the same inputs; 0 recomputes them per tile.
+ *   grad_latents [device] N floats, grad_params [device] 1415 floats, both overwritten.
+ *   Under CC_RELAX_HARD the latent gradient is zero (rounding has no derivative). */
+int coolchic_backward(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
+                      const float* latents, const float* params, int64_t step, int32_t relax,
+                      int32_t use_stored, float grad_scale, float* grad_latents,
+                      float* grad_params, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Rate-distortion of the current state (Sec. IV-A, Eq. 10), blocking: relax = CC_RELAX_HARD
+ * evaluates the quantised latents (Eq. 12), CC_RELAX_NOISE the training proxy at `step`.
+ *   rd_out [host] one record. */
+int coolchic_rate_distortion(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
+                             const float* latents, const float* params, int64_t step,
+                             int32_t relax, cc_rd_t* rd_out, void* workspace,
+                             size_t workspace_bytes, void* stream);
+
+/* Decoder (Sec. III): from integer latents q (the hard-quantised grids) and the parameters,
+ *   - the integer entropy model: a fixed-point ARM (weights rint(256 w), 8 fractional bits,
+ *     64-bit accumulation, floor shifts) and an integer Laplace CDF with 16-bit total mass,
+ *     giving prob_q16[i] = max(1, C(256 q + 128 - mu_q) - C(256 q - 128 - mu_q)), bit-exact and
+ *     platform-independent (motivated by Sec. III-A2);
+ *   - the reconstruction x^ = synthesis(upsampling(q)) in FP32, clamped to [0, 1].
+ *   q [device] N int32; params [device]; image_out [device, nullable] 3*H*W FP32;
+ *   prob_q16 [device, nullable] N uint32; mu_q, logb_q [device, nullable] N int32 each. */
+int coolchic_decode_image(const cc_arch_t* arch, const int32_t* q, const float* params,
+                          float* image_out, uint32_t* prob_q16, int32_t* mu_q, int32_t* logb_q,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* coolchic_last_error(void);
+
+/* Library version string. */
+const char* coolchic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COOLCHIC_H */

@@ -1,0 +1,420 @@
+// C ABI of the library (include/coolchic.h): argument checks, workspace layout, launch order.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/coolchic.h"
+#include "cc_kernels.h"
+
+namespace cc {
+
+namespace {
+thread_local std::string g_err;
+std::mutex g_dev_mu;
+std::vector<int> g_sms;       // SM count per device (0 = unknown)
+std::vector<int> g_attr_done; // kernel attributes set per device
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int device_setup() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(CC_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if ((int)g_sms.size() <= dev) {
+        g_sms.resize(dev + 1, 0);
+        g_attr_done.resize(dev + 1, 0);
+    }
+    if (!g_sms[dev]) {
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || n <= 0) return fail(CC_ERR_CUDA, "SM count query failed: %s", cudaGetErrorString(e));
+        g_sms[dev] = n;
+    }
+    if (!g_attr_done[dev]) {
+        arm_init_attributes();
+        synth_init_attributes();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(CC_ERR_CUDA, "kernel attribute setup: %s", cudaGetErrorString(e));
+        g_attr_done[dev] = 1;
+    }
+    return CC_OK;
+}
+
+int check_arch(const cc_arch_t* a) {
+    if (!a) return fail(CC_ERR_ARG, "arch is NULL");
+    if (a->H < 1 || a->W < 1 || a->H > 16384 || a->W > 16384)
+        return fail(CC_ERR_ARG, "image size %d x %d outside 1..16384", a->H, a->W);
+    if (a->C != kC || a->L != kL || a->n_ctx != kNCtx || a->ifce_dim != kF || a->ifce_grids != kNIfce ||
+        a->arm_hidden != kAH || a->arm_layers != 2 || a->syn_hidden != kSH || a->n_resconv != 2 || a->up_taps != 8 ||
+        a->stabilizer != 1)
+        return fail(CC_ERR_UNSUPPORTED, "only the C=3, L=7, ctx 16, F=4 (3 IFCEs), ARM 16x2, synthesis 40, "
+                                        "2 residual convs, 8-tap upsampling, stabilizer-on architecture is built");
+    return CC_OK;
+}
+
+int check_hp(const cc_hparams_t* hp) {
+    if (!hp) return fail(CC_ERR_ARG, "hparams is NULL");
+    if (!std::isfinite(hp->lambda) || hp->lambda < 0.f) return fail(CC_ERR_ARG, "lambda must be finite and >= 0");
+    if (!std::isfinite(hp->lr) || !std::isfinite(hp->eps) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) ||
+        !(hp->beta2 >= 0.f && hp->beta2 < 1.f))
+        return fail(CC_ERR_ARG, "invalid Adam hyper-parameters");
+    if (hp->noise_mode != 0) return fail(CC_ERR_UNSUPPORTED, "only noise_mode 0 (additive uniform) is built");
+    return CC_OK;
+}
+
+Hp to_hp(const cc_hparams_t* h) {
+    Hp o;
+    o.lambda = h->lambda;
+    o.lr = h->lr;
+    o.beta1 = h->beta1;
+    o.beta2 = h->beta2;
+    o.eps = h->eps;
+    o.seed = h->seed;
+    return o;
+}
+
+struct Layout {
+    size_t total = 0;
+    size_t take(size_t bytes) {
+        size_t o = total;
+        total += (bytes + 255) & ~(size_t)255;
+        return o;
+    }
+};
+
+// Carves the workspace; with base == nullptr it only measures.
+size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
+    Work W;
+    std::memset(&W, 0, sizeof(W));
+    W.g = make_geom(a->H, a->W);
+    const Geom& g = W.g;
+    W.N = g.off[kL];
+    W.HW = (int64_t)a->H * a->W;
+    const int sms = num_sms();
+    W.n_cta_arm = arm_grid(W.N);
+    {
+        int64_t rounds = (W.HW + kSynThreads - 1) / kSynThreads;
+        W.n_cta_syn = (int)(rounds < 2 * sms ? rounds : 2 * sms);
+        int64_t tiles = conv_tiles(a->H, a->W);
+        W.n_cta_conv = (int)(tiles < 2 * sms ? tiles : 2 * sms);
+    }
+    for (int st = 1; st < kL; ++st) {
+        const int nch = kL - st;
+        W.n_cta_up[st][0] = up_adj_grid((int64_t)nch * g.h[st] * g.w[st - 1]);
+        W.n_cta_up[st][1] = up_adj_grid((int64_t)nch * g.h[st] * g.w[st]);
+    }
+    Layout L;
+    const size_t F = sizeof(float);
+    size_t o_yt = L.take(W.N * F);
+    size_t o_dS = L.take(16 * W.N * F);
+    size_t o_dR[3];
+    for (int k = 0; k < kNIfce; ++k) o_dR[k] = L.take((size_t)ifce_nin(k) * g.h[k] * g.w[k] * F);
+    size_t o_dYd = L.take(W.N * F);
+    size_t o_dYsyn = L.take(W.N * F);
+    size_t o_dIf = L.take((size_t)(W.N - g.off[kNIfce] + 1) * F);
+    size_t o_up[kL] = {0}, o_dup[kL] = {0};
+    for (int m = 1; m <= kL - 2; ++m) {
+        o_up[m] = L.take((size_t)(kL - 1 - m) * g.h[m] * g.w[m] * F);
+        o_dup[m] = L.take((size_t)(kL - 1 - m) * g.h[m] * g.w[m] * F);
+    }
+    size_t o_t = L.take(3 * W.HW * F);
+    size_t o_dt = L.take(3 * W.HW * F);
+    size_t o_dz = L.take(6 * W.HW * F);
+    size_t tmp_n = 1;
+    for (int st = 1; st < kL; ++st) {
+        size_t n = (size_t)(kL - st) * g.h[st] * g.w[st - 1];
+        if (n > tmp_n) tmp_n = n;
+    }
+    size_t o_tmp = L.take(tmp_n * F);
+    size_t o_ga = L.take((size_t)W.n_cta_arm * po::arm_block * F);
+    size_t o_gs = L.take((size_t)W.n_cta_syn * po::syn_block * F);
+    size_t o_gc = L.take((size_t)W.n_cta_conv * po::conv_block * F);
+    size_t o_gu = L.take((size_t)6 * 2 * kUpMaxCta * 4 * F);
+    size_t o_rp = L.take((size_t)W.n_cta_arm * sizeof(double));
+    size_t o_sp = L.take((size_t)W.n_cta_conv * sizeof(double));
+    size_t o_gp = L.take(po::total * F);
+    size_t o_bs = L.take(4 * sizeof(int64_t));
+    size_t o_aa = 0, o_as = 0;
+    if (flags & 1) {
+        o_aa = L.take(34 * W.N * F);
+        o_as = L.take(40 * W.HW * F);
+    }
+    if (base && w) {
+        W.yt = (float*)(base + o_yt);
+        W.dS = (float*)(base + o_dS);
+        for (int k = 0; k < kNIfce; ++k) W.dR[k] = (float*)(base + o_dR[k]);
+        W.dYd = (float*)(base + o_dYd);
+        W.dYsyn = (float*)(base + o_dYsyn);
+        W.dIf = (float*)(base + o_dIf);
+        for (int m = 1; m <= kL - 2; ++m) {
+            W.up[m] = (float*)(base + o_up[m]);
+            W.dup[m] = (float*)(base + o_dup[m]);
+        }
+        W.t = (float*)(base + o_t);
+        W.dt = (float*)(base + o_dt);
+        W.dz = (float*)(base + o_dz);
+        W.tmp = (float*)(base + o_tmp);
+        W.gpart_arm = (float*)(base + o_ga);
+        W.gpart_syn = (float*)(base + o_gs);
+        W.gpart_conv = (float*)(base + o_gc);
+        W.gpart_up = (float*)(base + o_gu);
+        W.rate_part = (double*)(base + o_rp);
+        W.se_part = (double*)(base + o_sp);
+        W.grad_params = (float*)(base + o_gp);
+        W.base_step = (int64_t*)(base + o_bs);
+        if (flags & 1) {
+            W.act_arm = (float*)(base + o_aa);
+            W.act_syn = (float*)(base + o_as);
+        }
+        *w = W;
+    }
+    return L.total;
+}
+
+int prepare(const cc_arch_t* arch, int flags, void* ws, size_t ws_bytes, Work* w) {
+    int rc = check_arch(arch);
+    if (rc) return rc;
+    rc = device_setup();
+    if (rc) return rc;
+    if (!ws) return fail(CC_ERR_WORKSPACE, "workspace is NULL");
+    if (((uintptr_t)ws & 255) != 0) return fail(CC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    const size_t need = build_work(arch, flags, nullptr, nullptr);
+    if (ws_bytes < need)
+        return fail(CC_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, need);
+    build_work(arch, flags, (char*)ws, w);
+    return CC_OK;
+}
+
+int launched(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(CC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return CC_OK;
+}
+
+}  // namespace
+
+int num_sms() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(g_dev_mu);
+        if ((int)g_sms.size() > dev && g_sms[dev] > 0) return g_sms[dev];
+    }
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// Forward sequence shared by the entry points: relax, entropy model, upsampling, synthesis, convs.
+static void run_forward(const Work& w, const float* image, const float* latents, const float* params,
+                        const int64_t* step_dev, int64_t step_host, uint64_t seed, int relax, int arm_pass,
+                        int syn_pass, int conv_pass, float arm_gscale, float conv_gscale, float* xhat, cudaStream_t s) {
+    launch_relax(w, latents, step_dev, step_host, seed, relax, s);
+    launch_arm(w, params, arm_pass, arm_gscale, s);
+    launch_up_forward(w, params, s);
+    launch_syn_forward(w, params, syn_pass, s);
+    launch_conv(w, params, image, conv_pass, conv_gscale, xhat, s);
+}
+
+}  // namespace cc
+
+using namespace cc;
+
+extern "C" {
+
+int coolchic_arch_init(cc_arch_t* a, int32_t H, int32_t W) {
+    if (!a) return fail(CC_ERR_ARG, "arch is NULL");
+    if (H < 1 || W < 1 || H > 16384 || W > 16384) return fail(CC_ERR_ARG, "image size %d x %d outside 1..16384", H, W);
+    a->C = kC;
+    a->H = H;
+    a->W = W;
+    a->L = kL;
+    a->n_ctx = kNCtx;
+    a->ifce_dim = kF;
+    a->ifce_grids = kNIfce;
+    a->arm_hidden = kAH;
+    a->arm_layers = 2;
+    a->syn_hidden = kSH;
+    a->n_resconv = 2;
+    a->up_taps = 8;
+    a->stabilizer = 1;
+    return CC_OK;
+}
+
+int64_t coolchic_latent_count(const cc_arch_t* a) {
+    if (check_arch(a)) return -1;
+    return make_geom(a->H, a->W).off[kL];
+}
+
+int64_t coolchic_param_count(const cc_arch_t* a) {
+    if (check_arch(a)) return -1;
+    return po::total;
+}
+
+int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int32_t* length) {
+    static const struct {
+        const char* n;
+        int o, l;
+    } B[] = {{"arm.w1", po::arm_w1, 320},  {"arm.b1", po::arm_b1, 16},   {"arm.w2", po::arm_w2, 256},
+             {"arm.b2", po::arm_b2, 16},   {"arm.w3", po::arm_w3, 32},   {"arm.b3", po::arm_b3, 2},
+             {"arm.ws", po::arm_ws, 40},   {"arm.bs", po::arm_bs, 2},    {"ifce0.w", po::if_w0, 24},
+             {"ifce0.b", po::if_b0, 4},    {"ifce1.w", po::if_w1, 20},   {"ifce1.b", po::if_b1, 4},
+             {"ifce2.w", po::if_w2, 16},   {"ifce2.b", po::if_b2, 4},    {"up.taps", po::up, 24},
+             {"syn.w1", po::syn_w1, 280},  {"syn.b1", po::syn_b1, 40},   {"syn.w2", po::syn_w2, 120},
+             {"syn.b2", po::syn_b2, 3},    {"syn.ws", po::syn_ws, 21},   {"syn.bs", po::syn_bs, 3},
+             {"conv1.w", po::cv1_w, 81},   {"conv1.b", po::cv1_b, 3},    {"conv2.w", po::cv2_w, 81},
+             {"conv2.b", po::cv2_b, 3}};
+    const int n = (int)(sizeof(B) / sizeof(B[0]));
+    if (index < 0 || index >= n) return fail(CC_ERR_ARG, "parameter block %d out of range", index);
+    if (name) *name = B[index].n;
+    if (offset) *offset = B[index].o;
+    if (length) *length = B[index].l;
+    return CC_OK;
+}
+
+size_t coolchic_workspace_bytes(const cc_arch_t* a, int32_t flags) {
+    if (check_arch(a)) return 0;
+    if (device_setup()) return 0;
+    return build_work(a, flags, nullptr, nullptr);
+}
+
+int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image, const cc_state_t* st,
+                         int32_t n_iters, cc_rd_t* rd_per_iter, void* ws, size_t ws_bytes, void* stream) {
+    Work w;
+    int rc = prepare(arch, 0, ws, ws_bytes, &w);
+    if (rc) return rc;
+    if ((rc = check_hp(hp))) return rc;
+    if (!image || !st || !st->latents || !st->params || !st->m_lat || !st->v_lat || !st->m_par || !st->v_par || !st->step)
+        return fail(CC_ERR_ARG, "NULL image or state pointer");
+    if (n_iters < 0) return fail(CC_ERR_ARG, "n_iters must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Hp h = to_hp(hp);
+    const float arm_gs = hp->lambda / (float)w.HW;
+    const float conv_gs = 2.f / (3.f * (float)w.HW);
+    if (rd_per_iter) launch_mark_base(w, st->step, s);
+    for (int it = 0; it < n_iters; ++it) {
+        run_forward(w, image, st->latents, st->params, st->step, 0, h.seed, kRelaxNoise, PASS_FWD_BWD, PASS_FWD,
+                    PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s);
+        launch_syn_backward(w, st->params, PASS_FWD_BWD, s);
+        launch_up_adjoint(w, st->params, s);
+        launch_gather(w, st->params, kRelaxNoise, nullptr, st->latents, st->m_lat, st->v_lat, h, st->step, s);
+        launch_param_reduce(w, st->params, st->m_par, st->v_par, nullptr, 1.f, h, st->step, s);
+        launch_finish(w, h, 1, 1, (double*)rd_per_iter, st->step, 0, 1, s);
+        if ((rc = launched("encode_step"))) return rc;
+    }
+    return CC_OK;
+}
+
+int coolchic_forward(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image, const float* latents,
+                     const float* params, int64_t step, int32_t relax, int32_t store, cc_rd_t* rd_out, float* xhat,
+                     void* ws, size_t ws_bytes, void* stream) {
+    Work w;
+    int rc = prepare(arch, store ? 1 : 0, ws, ws_bytes, &w);
+    if (rc) return rc;
+    if ((rc = check_hp(hp))) return rc;
+    if (!image || !latents || !params) return fail(CC_ERR_ARG, "NULL image, latents or params");
+    if (relax < 0 || relax > 2) return fail(CC_ERR_ARG, "relax must be 0, 1 or 2");
+    if (step < 0 || step > 0x7fffffffLL) return fail(CC_ERR_ARG, "step outside 0..2^31-1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Hp h = to_hp(hp);
+    const int ap = store ? PASS_FWD_STORE : PASS_FWD;
+    run_forward(w, image, latents, params, nullptr, step, h.seed, relax, ap, ap, PASS_FWD, 0.f, 0.f, xhat, s);
+    launch_finish(w, h, 1, 1, (double*)rd_out, nullptr, 0, 0, s);
+    return launched("forward");
+}
+
+int coolchic_backward(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image, const float* latents,
+                      const float* params, int64_t step, int32_t relax, int32_t use_stored, float grad_scale,
+                      float* grad_latents, float* grad_params, void* ws, size_t ws_bytes, void* stream) {
+    Work w;
+    int rc = prepare(arch, use_stored ? 1 : 0, ws, ws_bytes, &w);
+    if (rc) return rc;
+    if ((rc = check_hp(hp))) return rc;
+    if (!image || !latents || !params || !grad_latents || !grad_params)
+        return fail(CC_ERR_ARG, "NULL image, latents, params or gradient pointer");
+    if (relax < 0 || relax > 2) return fail(CC_ERR_ARG, "relax must be 0, 1 or 2");
+    if (step < 0 || step > 0x7fffffffLL) return fail(CC_ERR_ARG, "step outside 0..2^31-1");
+    if (!std::isfinite(grad_scale)) return fail(CC_ERR_ARG, "grad_scale must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Hp h = to_hp(hp);
+    const float arm_gs = hp->lambda / (float)w.HW * grad_scale;
+    const float conv_gs = 2.f / (3.f * (float)w.HW) * grad_scale;
+    if (use_stored) {
+        // y~, upsampled grids and t are still in the workspace from coolchic_forward
+        launch_arm(w, params, PASS_BWD_LOAD, arm_gs, s);
+        launch_conv(w, params, image, PASS_FWD_BWD, conv_gs, nullptr, s);
+        launch_syn_backward(w, params, PASS_BWD_LOAD, s);
+    } else {
+        run_forward(w, image, latents, params, nullptr, step, h.seed, relax, PASS_FWD_BWD, PASS_FWD, PASS_FWD_BWD,
+                    arm_gs, conv_gs, nullptr, s);
+        launch_syn_backward(w, params, PASS_FWD_BWD, s);
+    }
+    launch_up_adjoint(w, params, s);
+    launch_gather(w, params, relax, grad_latents, nullptr, nullptr, nullptr, h, nullptr, s);
+    launch_param_reduce(w, nullptr, nullptr, nullptr, grad_params, 1.f, h, nullptr, s);
+    return launched("backward");
+}
+
+int coolchic_rate_distortion(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image, const float* latents,
+                             const float* params, int64_t step, int32_t relax, cc_rd_t* rd_out, void* ws,
+                             size_t ws_bytes, void* stream) {
+    Work w;
+    int rc = prepare(arch, 0, ws, ws_bytes, &w);
+    if (rc) return rc;
+    if ((rc = check_hp(hp))) return rc;
+    if (!image || !latents || !params || !rd_out) return fail(CC_ERR_ARG, "NULL image, latents, params or rd_out");
+    if (relax < 0 || relax > 2) return fail(CC_ERR_ARG, "relax must be 0, 1 or 2");
+    if (step < 0 || step > 0x7fffffffLL) return fail(CC_ERR_ARG, "step outside 0..2^31-1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Hp h = to_hp(hp);
+    double* rd_dev = (double*)w.grad_params;  // 3 doubles of scratch
+    run_forward(w, image, latents, params, nullptr, step, h.seed, relax, PASS_FWD, PASS_FWD, PASS_FWD, 0.f, 0.f,
+                nullptr, s);
+    launch_finish(w, h, 1, 1, rd_dev, nullptr, 0, 0, s);
+    if ((rc = launched("rate_distortion"))) return rc;
+    cudaError_t e = cudaMemcpyAsync(rd_out, rd_dev, sizeof(cc_rd_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(CC_ERR_CUDA, "rate_distortion readback: %s", cudaGetErrorString(e));
+    return CC_OK;
+}
+
+int coolchic_decode_image(const cc_arch_t* arch, const int32_t* q, const float* params, float* image_out,
+                          uint32_t* prob_q16, int32_t* mu_q, int32_t* logb_q, void* ws, size_t ws_bytes,
+                          void* stream) {
+    Work w;
+    int rc = prepare(arch, 0, ws, ws_bytes, &w);
+    if (rc) return rc;
+    if (!q || !params) return fail(CC_ERR_ARG, "NULL latents or params");
+    decode_init_tables();
+    if ((rc = launched("decode table setup"))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_decode(w.g, q, params, w.yt, prob_q16, mu_q, logb_q, s);
+    if (image_out) {
+        launch_up_forward(w, params, s);
+        launch_syn_forward(w, params, PASS_FWD, s);
+        // the residual convs of the forward pass against a dummy target; only xhat is kept
+        launch_conv(w, params, w.dt, PASS_FWD, 0.f, image_out, s);
+        launch_clamp01(image_out, 3 * w.HW, s);
+    }
+    return launched("decode_image");
+}
+
+const char* coolchic_last_error(void) { return g_err.c_str(); }
+
+const char* coolchic_version(void) { return "coolchic-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

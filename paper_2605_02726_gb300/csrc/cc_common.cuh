@@ -1,0 +1,174 @@
+// Shared device-side definitions of the encoder-step kernels: geometry, parameter layout,
+// counter noise, Laplace mass, block reductions.  Included by every .cu of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cc {
+
+constexpr int kL = 7;        // latent grids (Sec. III-A1, Eq. 1; Table II 1/1..1/64)
+constexpr int kNCtx = 16;    // spatial context values
+constexpr int kF = 4;        // IFCE output width
+constexpr int kNIfce = 3;    // grids 0..2 carry an IFCE (Table II)
+constexpr int kAIn = kNCtx + kF;
+constexpr int kAH = 16;      // ARM hidden width
+constexpr int kC = 3;        // image channels
+constexpr int kSH = 40;      // synthesis hidden width
+constexpr float kLogbMin = -5.f, kLogbMax = 5.f;
+constexpr float kPMin = 1.f / 65536.f;
+
+// Flat parameter vector (row-major [out][in] matrices); the interface documented in coolchic.h.
+namespace po {
+constexpr int arm_w1 = 0, arm_b1 = 320, arm_w2 = 336, arm_b2 = 592, arm_w3 = 608, arm_b3 = 640,
+              arm_ws = 642, arm_bs = 682;
+constexpr int if_w0 = 684, if_b0 = 708, if_w1 = 712, if_b1 = 732, if_w2 = 736, if_b2 = 752;
+constexpr int up = 756;
+constexpr int syn_w1 = 780, syn_b1 = 1060, syn_w2 = 1100, syn_b2 = 1220, syn_ws = 1223, syn_bs = 1244;
+constexpr int cv1_w = 1247, cv1_b = 1328, cv2_w = 1331, cv2_b = 1412;
+constexpr int total = 1415;
+constexpr int arm_block = up;                 // ARM + IFCE parameters: [0, 756)
+constexpr int syn_block = cv1_w - syn_w1;     // 467
+constexpr int conv_block = total - cv1_w;     // 168
+}  // namespace po
+
+__host__ __device__ constexpr int ifce_w_off(int k) { return k == 0 ? po::if_w0 : (k == 1 ? po::if_w1 : po::if_w2); }
+__host__ __device__ constexpr int ifce_b_off(int k) { return k == 0 ? po::if_b0 : (k == 1 ? po::if_b1 : po::if_b2); }
+__host__ __device__ constexpr int ifce_nin(int k) { return k < kNIfce ? kL - k - 1 : 0; }
+
+// Causal context offsets (dy, dx), nearest first; 3 rows up, 3 columns either side.
+__host__ __device__ constexpr int ctx_dy(int n) {
+    constexpr int t[kNCtx] = {0, -1, -1, -1, 0, -2, -1, -1, -2, -2, -2, -2, 0, -3, -1, -1};
+    return t[n];
+}
+__host__ __device__ constexpr int ctx_dx(int n) {
+    constexpr int t[kNCtx] = {-1, 0, -1, 1, -2, 0, -2, 2, -1, 1, -2, 2, -3, 0, -3, 3};
+    return t[n];
+}
+
+struct Geom {
+    int H, W;
+    int h[kL], w[kL];
+    int64_t off[kL + 1];
+};
+
+inline Geom make_geom(int H, int W) {
+    Geom g;
+    g.H = H;
+    g.W = W;
+    g.off[0] = 0;
+    for (int k = 0; k < kL; ++k) {
+        g.h[k] = (H + (1 << k) - 1) >> k;
+        g.w[k] = (W + (1 << k) - 1) >> k;
+        g.off[k + 1] = g.off[k] + (int64_t)g.h[k] * g.w[k];
+    }
+    return g;
+}
+
+__device__ __forceinline__ int grid_of(const Geom& g, int64_t i) {
+    int k = 0;
+#pragma unroll
+    for (int j = 1; j < kL; ++j) k += (i >= g.off[j]) ? 1 : 0;
+    return k;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// ---------------------------------------------------------------------------------------------
+// Counter noise: SplitMix64 output function (Steele, Lea, Flood 2014) of
+// seed ^ ((step << 32) + i) * 0x9E3779B97F4A7C15; top 24 bits -> u in [-1/2, 1/2), exact in FP32.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float counter_uniform(uint64_t seed, int64_t step, int64_t i) {
+    uint64_t z = seed ^ ((((uint64_t)step << 32) + (uint64_t)i) * 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (float)(uint32_t)(z >> 40) * (1.f / 16777216.f) - 0.5f;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Laplace mass of [y - 1/2, y + 1/2] (Eq. 3), location mu, scale b = exp(logb), evaluated on the
+// side of mu where it does not cancel; derivatives with respect to y and log b.
+//   dP/dy = f(hi) - f(lo),  dP/dlogb = -(hi f(hi) - lo f(lo)),  f(z) = exp(-|z|/b) / (2b).
+// ---------------------------------------------------------------------------------------------
+struct LapOut {
+    float p, dp_dy, dp_dlogb;
+};
+
+__device__ __forceinline__ LapOut laplace_mass(float y, float mu, float logb) {
+    float b = expf(logb);
+    float inv_b = __frcp_rn(b);
+    float lo = y - 0.5f - mu, hi = y + 0.5f - mu;
+    float el = expf(-fabsf(lo) * inv_b), eh = expf(-fabsf(hi) * inv_b);
+    float p;
+    if (lo >= 0.f)
+        p = -0.5f * el * expm1f(-inv_b);
+    else if (hi <= 0.f)
+        p = -0.5f * eh * expm1f(-inv_b);
+    else
+        p = 1.f - 0.5f * el - 0.5f * eh;
+    float fh = 0.5f * inv_b * eh, fl = 0.5f * inv_b * el;
+    LapOut o;
+    o.p = p;
+    o.dp_dy = fh - fl;
+    o.dp_dlogb = -(hi * fh - lo * fl);
+    return o;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of NV values per thread, fixed order; result valid in thread 0.  `scratch`
+// holds NV * (blockDim.x / 32) floats.
+template <int NV>
+__device__ __forceinline__ void block_sum(float (&v)[NV], float* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) scratch[j * nw + wid] = v[j];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            float s = 0.f;
+            for (int q = 0; q < nw; ++q) s += scratch[j * nw + q];
+            v[j] = s;
+        }
+    __syncthreads();
+}
+
+// GELU, exact erf form, and its derivative.
+__device__ __forceinline__ float gelu_f(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float a) {
+    return 0.5f * (1.f + erff(a * 0.70710678118654752f)) + a * 0.39894228040143268f * expf(-0.5f * a * a);
+}
+
+// Polyphase taps of the x2 upsampler (Sec. III-B): output position o reads 4 inputs at
+// p-2..p+1 (even o) or p-1..p+2 (odd o), p = o >> 1, with tap order
+//   even: a c d b      odd: b d c a       (a, b, c, d = taps[0..3])
+__device__ __forceinline__ void poly(int o, int& first, int (&tap)[4]) {
+    int p = o >> 1;
+    if ((o & 1) == 0) {
+        first = p - 2;
+        tap[0] = 0; tap[1] = 2; tap[2] = 3; tap[3] = 1;
+    } else {
+        first = p - 1;
+        tap[0] = 1; tap[1] = 3; tap[2] = 2; tap[3] = 0;
+    }
+}
+
+}  // namespace cc

@@ -1,0 +1,792 @@
+// Reconstruction side of the encoder step: upsampling cascade (Sec. III-B, Eq. 7), synthesis
+// 1x1 MLP with stabilizer (Eq. 8, Eq. 9), two residual 3x3 convolutions, distortion (Eq. 10) and
+// the adjoint of each.  Every parameter-gradient sum is reduced per CTA in a fixed order.
+#include "cc_kernels.h"
+
+namespace cc {
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Upsampling stage s (grid s -> grid s-1), forward, stages 6..2.  Output up[m], m = s-1, holds
+// the channels of grids m+1..6: channel 0 comes from y~^(m+1), channel j >= 1 from up[m+1][j-1].
+// Separable 4x4 polyphase taps with replicate (clamped) indices, cropped to the grid size.
+// ---------------------------------------------------------------------------------------------
+struct UpFwdArgs {
+    const float* src0;   // y~ of grid m+1
+    const float* srcup;  // up[m+1] (channels 1..), may be null when nch == 1
+    float* dst;          // up[m]
+    int hs, ws, ht, wt, nch;
+    const float* taps;   // 4 taps of this stage (device)
+};
+
+__global__ void k_up_fwd(UpFwdArgs a) {
+    const int64_t total = (int64_t)a.nch * a.ht * a.wt;
+    const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / ((int64_t)a.ht * a.wt));
+        const int rem = (int)(e - (int64_t)j * a.ht * a.wt);
+        const int y = rem / a.wt, x = rem - y * a.wt;
+        const float* S = j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws;
+        int fy, fx, ty[4], tx[4];
+        poly(y, fy, ty);
+        poly(x, fx, tx);
+        float acc = 0.f;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const float* row = S + clampi(fy + p, 0, a.hs - 1) * a.ws;
+            float rs = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) rs = fmaf(tp[tx[q]], __ldg(row + clampi(fx + q, 0, a.ws - 1)), rs);
+            acc = fmaf(tp[ty[p]], rs, acc);
+        }
+        a.dst[e] = acc;
+    }
+}
+
+// Stage-1 upsampling of S_1 = [y~^(1), up[1]] at full-resolution pixel (y, x): z[1..6].
+__device__ __forceinline__ void dense_latents(const Geom& g, const float* yt, const float* up1,
+                                              const float (&tp)[4], int y, int x, float (&z)[kL]) {
+    const int hs = g.h[1], ws = g.w[1];
+    z[0] = __ldg(yt + (int64_t)y * g.W + x);
+    int fy, fx, ty[4], tx[4];
+    poly(y, fy, ty);
+    poly(x, fx, tx);
+    int ro[4], co[4];
+    float wy[4], wx[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        ro[p] = clampi(fy + p, 0, hs - 1) * ws;
+        co[p] = clampi(fx + p, 0, ws - 1);
+        wy[p] = tp[ty[p]];
+        wx[p] = tp[tx[p]];
+    }
+    const int64_t n1 = (int64_t)hs * ws;
+#pragma unroll
+    for (int j = 1; j < kL; ++j) {
+        const float* S = j == 1 ? yt + g.off[1] : up1 + (int64_t)(j - 2) * n1;
+        float acc = 0.f;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            float rs = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) rs = fmaf(wx[q], __ldg(S + ro[p] + co[q]), rs);
+            acc = fmaf(wy[p], rs, acc);
+        }
+        z[j] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Synthesis MLP forward: t = W2 gelu(W1 z + b1) + b2 + Ws z + bs.  One thread per pixel.
+// ---------------------------------------------------------------------------------------------
+struct SynArgs {
+    Geom g;
+    int64_t HW;
+    const float* yt;
+    const float* up1;
+    const float* params;
+    float* t;        // [3][HW]
+    const float* dt; // [3][HW]
+    float* act;      // [40][HW]
+    float* dYsyn0;   // grid-0 part of dYsyn [HW]
+    float* dz;       // [6][HW]
+    float* gpart;    // [gridDim.x][467]
+};
+
+// shared weight layout of the synthesis kernels
+constexpr int ss_w1 = 0;      // [40][8] (7 used, 8th = bias b1)
+constexpr int ss_w2 = 320;    // [3][40]
+constexpr int ss_ws = 440;    // [3][8]  (7 used, 8th = b2 + bs)
+constexpr int ss_total = 464;
+
+__device__ __forceinline__ void load_syn_weights(const float* P, float* sW) {
+    for (int j = threadIdx.x; j < ss_total; j += blockDim.x) {
+        float v;
+        if (j < ss_w2) {
+            const int o = j >> 3, i = j & 7;
+            v = i < 7 ? P[po::syn_w1 + o * 7 + i] : P[po::syn_b1 + o];
+        } else if (j < ss_ws) {
+            v = P[po::syn_w2 + (j - ss_w2)];
+        } else {
+            const int o = (j - ss_ws) >> 3, i = (j - ss_ws) & 7;
+            v = i < 7 ? P[po::syn_ws + o * 7 + i] : P[po::syn_b2 + o] + P[po::syn_bs + o];
+        }
+        sW[j] = v;
+    }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kSynThreads) k_syn_fwd(SynArgs a) {
+    __shared__ __align__(16) float sW[ss_total];
+    load_syn_weights(a.params, sW);
+    const float tp[4] = {a.params[po::up], a.params[po::up + 1], a.params[po::up + 2], a.params[po::up + 3]};
+    __syncthreads();
+    const Geom& g = a.g;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.HW; p += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(p / g.W), x = (int)(p - (int64_t)y * g.W);
+        float z[kL];
+        dense_latents(g, a.yt, a.up1, tp, y, x, z);
+        float t0 = sW[ss_ws + 7], t1 = sW[ss_ws + 15], t2 = sW[ss_ws + 23];
+#pragma unroll
+        for (int i = 0; i < kL; ++i) {
+            t0 = fmaf(sW[ss_ws + i], z[i], t0);
+            t1 = fmaf(sW[ss_ws + 8 + i], z[i], t1);
+            t2 = fmaf(sW[ss_ws + 16 + i], z[i], t2);
+        }
+#pragma unroll 4
+        for (int o = 0; o < kSH; ++o) {
+            const float4 w0 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8);
+            const float4 w1 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8 + 4);
+            float acc = w1.w;
+            acc = fmaf(w0.x, z[0], acc);
+            acc = fmaf(w0.y, z[1], acc);
+            acc = fmaf(w0.z, z[2], acc);
+            acc = fmaf(w0.w, z[3], acc);
+            acc = fmaf(w1.x, z[4], acc);
+            acc = fmaf(w1.y, z[5], acc);
+            acc = fmaf(w1.z, z[6], acc);
+            if (PASS == PASS_FWD_STORE) a.act[(int64_t)o * a.HW + p] = acc;
+            const float h = gelu_f(acc);
+            t0 = fmaf(sW[ss_w2 + o], h, t0);
+            t1 = fmaf(sW[ss_w2 + kSH + o], h, t1);
+            t2 = fmaf(sW[ss_w2 + 2 * kSH + o], h, t2);
+        }
+        a.t[p] = t0;
+        a.t[a.HW + p] = t1;
+        a.t[2 * a.HW + p] = t2;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Synthesis MLP adjoint, one thread per pixel, rounds of 128 pixels.  dz = W1^T da + Ws^T dt,
+// da = (W2^T dt) * gelu'(a).  Parameter gradients as staged outer products:
+//   U rows: da 0-39, dt 40-42, zero 43-47;   V rows: z 0-6, one 7, g 8-47.
+//   blocks (U0, V0): da x [z, 1] -> (0..32 step 8, 0);  dt x [z, 1] -> (40, 0);  dt x g -> (40, 8..40).
+// ---------------------------------------------------------------------------------------------
+constexpr int kSLd = kSynThreads + 4;
+constexpr int kSBlocks = 11;
+constexpr int kSChunks = 11;
+constexpr int kSTasks = kSBlocks * kSChunks;  // 121
+__constant__ unsigned char c_sblk_u[kSBlocks] = {0, 8, 16, 24, 32, 40, 40, 40, 40, 40, 40};
+__constant__ unsigned char c_sblk_v[kSBlocks] = {0, 0, 0, 0, 0, 0, 8, 16, 24, 32, 40};
+__constant__ unsigned char c_schunk[kSChunks + 1] = {0, 12, 24, 36, 48, 60, 72, 84, 96, 108, 120, 128};
+
+__device__ int syn_grad_index(int u, int v) {  // index relative to po::syn_w1, or -1
+    if (u < 40) {
+        if (v < 7) return (po::syn_w1 - po::syn_w1) + u * 7 + v;
+        if (v == 7) return (po::syn_b1 - po::syn_w1) + u;
+        return -1;
+    }
+    if (u < 43) {
+        const int o = u - 40;
+        if (v < 7) return (po::syn_ws - po::syn_w1) + o * 7 + v;
+        if (v == 7) return (po::syn_bs - po::syn_w1) + o;  // b2 takes the same sum
+        if (v < 48) return (po::syn_w2 - po::syn_w1) + o * kSH + (v - 8);
+    }
+    return -1;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd(SynArgs a) {
+    extern __shared__ float4 smem4[];
+    float* sW = reinterpret_cast<float*>(smem4);
+    float* sU = sW + ss_total;
+    float* sV = sU + 48 * kSLd;
+    float* sAcc = sV + 48 * kSLd;
+    load_syn_weights(a.params, sW);
+    const float tp[4] = {a.params[po::up], a.params[po::up + 1], a.params[po::up + 2], a.params[po::up + 3]};
+    const int tid = threadIdx.x;
+    for (int j = tid; j < kSTasks * 64; j += kSynThreads) sAcc[j] = 0.f;
+    for (int j = tid; j < kSLd; j += kSynThreads) {
+        for (int r = 43; r < 48; ++r) sU[r * kSLd + j] = 0.f;
+        sV[7 * kSLd + j] = 1.f;
+    }
+    __syncthreads();
+    const Geom& g = a.g;
+    const int64_t HW = a.HW;
+    const int64_t n_rounds = (HW + kSynThreads - 1) / kSynThreads;
+    for (int64_t rd = blockIdx.x; rd < n_rounds; rd += gridDim.x) {
+        const int64_t p = rd * kSynThreads + tid;
+        const bool valid = p < HW;
+        const int64_t pc = valid ? p : HW - 1;
+        const int y = (int)(pc / g.W), x = (int)(pc - (int64_t)y * g.W);
+        float z[kL];
+        dense_latents(g, a.yt, a.up1, tp, y, x, z);
+        const float m = valid ? 1.f : 0.f;
+        const float dt0 = a.dt[pc] * m, dt1 = a.dt[HW + pc] * m, dt2 = a.dt[2 * HW + pc] * m;
+        float dz[kL];
+#pragma unroll
+        for (int i = 0; i < kL; ++i)
+            dz[i] = sW[ss_ws + i] * dt0 + sW[ss_ws + 8 + i] * dt1 + sW[ss_ws + 16 + i] * dt2;
+#pragma unroll 4
+        for (int o = 0; o < kSH; ++o) {
+            const float4 w0 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8);
+            const float4 w1 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8 + 4);
+            float acc;
+            if (PASS == PASS_BWD_LOAD) {
+                acc = a.act[(int64_t)o * HW + pc];
+            } else {
+                acc = w1.w;
+                acc = fmaf(w0.x, z[0], acc);
+                acc = fmaf(w0.y, z[1], acc);
+                acc = fmaf(w0.z, z[2], acc);
+                acc = fmaf(w0.w, z[3], acc);
+                acc = fmaf(w1.x, z[4], acc);
+                acc = fmaf(w1.y, z[5], acc);
+                acc = fmaf(w1.z, z[6], acc);
+            }
+            const float dg = sW[ss_w2 + o] * dt0 + sW[ss_w2 + kSH + o] * dt1 + sW[ss_w2 + 2 * kSH + o] * dt2;
+            const float da = dg * gelu_grad_f(acc);
+            sU[o * kSLd + tid] = da;
+            sV[(8 + o) * kSLd + tid] = gelu_f(acc) * m;
+            dz[0] = fmaf(w0.x, da, dz[0]);
+            dz[1] = fmaf(w0.y, da, dz[1]);
+            dz[2] = fmaf(w0.z, da, dz[2]);
+            dz[3] = fmaf(w0.w, da, dz[3]);
+            dz[4] = fmaf(w1.x, da, dz[4]);
+            dz[5] = fmaf(w1.y, da, dz[5]);
+            dz[6] = fmaf(w1.z, da, dz[6]);
+        }
+        sU[40 * kSLd + tid] = dt0;
+        sU[41 * kSLd + tid] = dt1;
+        sU[42 * kSLd + tid] = dt2;
+#pragma unroll
+        for (int i = 0; i < kL; ++i) sV[i * kSLd + tid] = z[i] * m;
+        if (valid) {
+            a.dYsyn0[p] = dz[0];
+#pragma unroll
+            for (int j = 1; j < kL; ++j) a.dz[(int64_t)(j - 1) * HW + p] = dz[j];
+        }
+        __syncthreads();
+        if (tid < kSTasks) {
+            const int blk = tid / kSChunks, ch = tid - blk * kSChunks;
+            const float* U = sU + c_sblk_u[blk] * kSLd;
+            const float* V = sV + c_sblk_v[blk] * kSLd;
+            float acc[8][8];
+            float* A = sAcc + tid * 64;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = A[i * 8 + j];
+            for (int l = c_schunk[ch]; l < c_schunk[ch + 1]; l += 4) {
+                float4 u[8], v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) u[i] = *reinterpret_cast<const float4*>(U + i * kSLd + l);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = *reinterpret_cast<const float4*>(V + j * kSLd + l);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float s = acc[i][j];
+                        s = fmaf(u[i].x, v[j].x, s);
+                        s = fmaf(u[i].y, v[j].y, s);
+                        s = fmaf(u[i].z, v[j].z, s);
+                        s = fmaf(u[i].w, v[j].w, s);
+                        acc[i][j] = s;
+                    }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) A[i * 8 + j] = acc[i][j];
+        }
+        __syncthreads();
+    }
+    float* gp = a.gpart + (int64_t)blockIdx.x * po::syn_block;
+    for (int e = tid; e < kSBlocks * 64; e += kSynThreads) {
+        const int blk = e >> 6, pq = e & 63;
+        const int u = c_sblk_u[blk] + (pq >> 3), v = c_sblk_v[blk] + (pq & 7);
+        const int idx = syn_grad_index(u, v);
+        if (idx < 0) continue;
+        float sum = 0.f;
+        for (int ch = 0; ch < kSChunks; ++ch) sum += sAcc[(blk * kSChunks + ch) * 64 + pq];
+        gp[idx] = sum;
+        if (u >= 40 && u < 43 && v == 7) gp[po::syn_b2 - po::syn_w1 + (u - 40)] = sum;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Residual 3x3 convolutions, distortion and adjoint on 16x32 pixel tiles with recomputed halos.
+//   x1 = t + b1 + conv1(t),  xh = x1 + b2 + conv2(x1)  (replicate padding),  D = mean (xh - x)^2.
+//   dxh = 2 (xh - x) / (3HW);  dx1 = dxh + conv2^T(dxh);  dt = dx1 + conv1^T(dx1).
+// The transposed convolution gathers, per axis, the 3 (source, tap) pairs whose clamped index
+// lands on the target: interior q <- (q+1, 0), (q, 1), (q-1, 2); q = 0 <- (0,0), (0,1), (1,0);
+// q = n-1 <- (n-1,1), (n-1,2), (n-2,2); n = 1 <- (0,0), (0,1), (0,2).
+// ---------------------------------------------------------------------------------------------
+constexpr int kTH = kConvTH, kTW = kConvTW;
+constexpr int kConvThreads = 256;
+constexpr int R4H = kTH + 8, R4W = kTW + 8;  // t region (halo 4)
+constexpr int R3H = kTH + 6, R3W = kTW + 6;  // x1
+constexpr int R2H = kTH + 4, R2W = kTW + 4;  // xh / dxh
+constexpr int R1H = kTH + 2, R1W = kTW + 2;  // dx1
+
+struct ConvArgs {
+    int H, W;
+    int64_t HW;
+    const float* t;
+    const float* img;
+    const float* params;
+    float gscale;      // 2 / (3 HW) times the caller's outer scale
+    float* dt;
+    float* xhat;       // optional
+    float* gpart;      // [gridDim.x][168]
+    double* se_part;   // [gridDim.x]
+    int tiles_x, n_tiles;
+};
+
+__device__ __forceinline__ void conv_pairs(int q, int n, int (&src)[3], int (&tap)[3]) {
+    if (n == 1) {
+        src[0] = 0; tap[0] = 0; src[1] = 0; tap[1] = 1; src[2] = 0; tap[2] = 2;
+    } else if (q == 0) {
+        src[0] = 0; tap[0] = 0; src[1] = 0; tap[1] = 1; src[2] = 1; tap[2] = 0;
+    } else if (q == n - 1) {
+        src[0] = n - 1; tap[0] = 1; src[1] = n - 1; tap[1] = 2; src[2] = n - 2; tap[2] = 2;
+    } else {
+        src[0] = q + 1; tap[0] = 0; src[1] = q; tap[1] = 1; src[2] = q - 1; tap[2] = 2;
+    }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kConvThreads) k_conv(ConvArgs a) {
+    constexpr bool BWD = pass_bwd(PASS);
+    __shared__ float sWc[2][84];
+    __shared__ float sT[3][R4H][R4W];
+    __shared__ float sX1[3][R3H][R3W];
+    __shared__ float sD[3][R2H][R2W];   // xh, then dxh in place
+    __shared__ float sD1[3][R1H][R1W];
+    __shared__ double sSe[kConvThreads / 32];
+    const int tid = threadIdx.x;
+    for (int j = tid; j < 84; j += kConvThreads) {
+        sWc[0][j] = j < 81 ? a.params[po::cv1_w + j] : a.params[po::cv1_b + j - 81];
+        sWc[1][j] = j < 81 ? a.params[po::cv2_w + j] : a.params[po::cv2_b + j - 81];
+    }
+    // weight-gradient task of this thread: conv c, out o, in i, row tap ky, row group rg
+    // tasks 0..215: (c, o, i, ky, rg) ; tasks 216..239: bias (c, o, rg)
+    float gacc[3] = {0.f, 0.f, 0.f};
+    double se = 0.0;
+    const int H = a.H, W = a.W;
+    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        const int ty0 = (tile / a.tiles_x) * kTH, tx0 = (tile % a.tiles_x) * kTW;
+        __syncthreads();
+        // t on the halo-4 region (clamped reads; positions outside the image are never used)
+        for (int e = tid; e < 3 * R4H * R4W; e += kConvThreads) {
+            const int c = e / (R4H * R4W), rem = e % (R4H * R4W);
+            const int ry = rem / R4W, rx = rem % R4W;
+            const int gy = clampi(ty0 - 4 + ry, 0, H - 1), gx = clampi(tx0 - 4 + rx, 0, W - 1);
+            sT[c][ry][rx] = a.t[(int64_t)c * a.HW + (int64_t)gy * W + gx];
+        }
+        __syncthreads();
+        // x1 on the halo-3 region
+        for (int e = tid; e < R3H * R3W; e += kConvThreads) {
+            const int ry = e / R3W, rx = e % R3W;
+            const int gy = ty0 - 3 + ry, gx = tx0 - 3 + rx;
+            if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
+            float in[3][3][3];
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int sy = clampi(gy + ky - 1, 0, H - 1) - (ty0 - 4);
+                    const int sx = clampi(gx + kx - 1, 0, W - 1) - (tx0 - 4);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) in[i][ky][kx] = sT[i][sy][sx];
+                }
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                float acc = sT[o][ry + 1][rx + 1] + sWc[0][81 + o];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx) acc = fmaf(sWc[0][((o * 3 + i) * 3 + ky) * 3 + kx], in[i][ky][kx], acc);
+                sX1[o][ry][rx] = acc;
+            }
+        }
+        __syncthreads();
+        // xh, distortion and dxh on the halo-2 region
+        for (int e = tid; e < R2H * R2W; e += kConvThreads) {
+            const int ry = e / R2W, rx = e % R2W;
+            const int gy = ty0 - 2 + ry, gx = tx0 - 2 + rx;
+            if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
+            const bool core = ry >= 2 && ry < 2 + kTH && rx >= 2 && rx < 2 + kTW;
+            float in[3][3][3];
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int sy = clampi(gy + ky - 1, 0, H - 1) - (ty0 - 3);
+                    const int sx = clampi(gx + kx - 1, 0, W - 1) - (tx0 - 3);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) in[i][ky][kx] = sX1[i][sy][sx];
+                }
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                float acc = sX1[o][ry + 1][rx + 1] + sWc[1][81 + o];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx) acc = fmaf(sWc[1][((o * 3 + i) * 3 + ky) * 3 + kx], in[i][ky][kx], acc);
+                const int64_t gi = (int64_t)o * a.HW + (int64_t)gy * W + gx;
+                const float diff = acc - __ldg(a.img + gi);
+                if (core) {
+                    se += (double)diff * diff;
+                    if (a.xhat) a.xhat[gi] = acc;
+                }
+                sD[o][ry][rx] = diff * a.gscale;
+            }
+        }
+        if (!BWD) continue;
+        __syncthreads();
+        // dx1 on the halo-1 region: dxh + conv2^T(dxh)
+        for (int e = tid; e < R1H * R1W; e += kConvThreads) {
+            const int ry = e / R1W, rx = e % R1W;
+            const int gy = ty0 - 1 + ry, gx = tx0 - 1 + rx;
+            if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
+            int sy[3], ky[3], sx[3], kx[3];
+            conv_pairs(gy, H, sy, ky);
+            conv_pairs(gx, W, sx, kx);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float acc = sD[i][ry + 1][rx + 1];
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int o = 0; o < 3; ++o)
+                            acc = fmaf(sWc[1][((o * 3 + i) * 3 + ky[p]) * 3 + kx[q]],
+                                       sD[o][sy[p] - (ty0 - 2)][sx[q] - (tx0 - 2)], acc);
+                sD1[i][ry][rx] = acc;
+            }
+        }
+        __syncthreads();
+        // dt on the core: dx1 + conv1^T(dx1)
+        for (int e = tid; e < kTH * kTW; e += kConvThreads) {
+            const int ry = e / kTW, rx = e % kTW;
+            const int gy = ty0 + ry, gx = tx0 + rx;
+            if (gy >= H || gx >= W) continue;
+            int sy[3], ky[3], sx[3], kx[3];
+            conv_pairs(gy, H, sy, ky);
+            conv_pairs(gx, W, sx, kx);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float acc = sD1[i][ry + 1][rx + 1];
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int o = 0; o < 3; ++o)
+                            acc = fmaf(sWc[0][((o * 3 + i) * 3 + ky[p]) * 3 + kx[q]],
+                                       sD1[o][sy[p] - (ty0 - 1)][sx[q] - (tx0 - 1)], acc);
+                a.dt[(int64_t)i * a.HW + (int64_t)gy * W + gx] = acc;
+            }
+        }
+        // parameter gradients over the core pixels (sums in a fixed order per thread)
+        if (tid < 216) {
+            const int rg = tid & 3, task = tid >> 2;          // task 0..53
+            const int c = task / 27, r27 = task % 27;
+            const int o = r27 / 9, i = (r27 / 3) % 3, ky = r27 % 3;
+            // conv c: gradient dU (sD for conv2, sD1 for conv1) times its input (sX1 / sT)
+            for (int ry = rg * 4; ry < rg * 4 + 4; ++ry) {
+                const int gy = ty0 + ry;
+                if (gy >= H) break;
+                const int iy = clampi(gy + ky - 1, 0, H - 1);
+                for (int rx = 0; rx < kTW; ++rx) {
+                    const int gx = tx0 + rx;
+                    if (gx >= W) break;
+                    float gval, v0, v1, v2;
+                    const int x0 = clampi(gx - 1, 0, W - 1), x2 = clampi(gx + 1, 0, W - 1);
+                    if (c == 1) {  // conv2 (second residual layer)
+                        gval = sD[o][ry + 2][rx + 2];
+                        v0 = sX1[i][iy - (ty0 - 3)][x0 - (tx0 - 3)];
+                        v1 = sX1[i][iy - (ty0 - 3)][gx - (tx0 - 3)];
+                        v2 = sX1[i][iy - (ty0 - 3)][x2 - (tx0 - 3)];
+                    } else {
+                        gval = sD1[o][ry + 1][rx + 1];
+                        v0 = sT[i][iy - (ty0 - 4)][x0 - (tx0 - 4)];
+                        v1 = sT[i][iy - (ty0 - 4)][gx - (tx0 - 4)];
+                        v2 = sT[i][iy - (ty0 - 4)][x2 - (tx0 - 4)];
+                    }
+                    gacc[0] = fmaf(gval, v0, gacc[0]);
+                    gacc[1] = fmaf(gval, v1, gacc[1]);
+                    gacc[2] = fmaf(gval, v2, gacc[2]);
+                }
+            }
+        } else if (tid < 240) {
+            const int rg = tid & 3, task = (tid - 216) >> 2;  // 0..5: conv c, out o
+            const int c = task / 3, o = task % 3;
+            for (int ry = rg * 4; ry < rg * 4 + 4; ++ry) {
+                const int gy = ty0 + ry;
+                if (gy >= H) break;
+                for (int rx = 0; rx < kTW; ++rx) {
+                    if (tx0 + rx >= W) break;
+                    gacc[0] += c == 1 ? sD[o][ry + 2][rx + 2] : sD1[o][ry + 1][rx + 1];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // distortion partial
+    {
+        double v = warp_sum_d(se);
+        if ((tid & 31) == 0) sSe[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int q = 0; q < kConvThreads / 32; ++q) s += sSe[q];
+            a.se_part[blockIdx.x] = s;
+        }
+    }
+    if (!BWD) return;
+    // reduce the 4 row groups of each task in a fixed order and write this CTA's partial
+    __shared__ float sG[240][3];
+    if (tid < 240) {
+        sG[tid][0] = gacc[0];
+        sG[tid][1] = gacc[1];
+        sG[tid][2] = gacc[2];
+    }
+    __syncthreads();
+    float* gp = a.gpart + (int64_t)blockIdx.x * po::conv_block;
+    if (tid < 54) {
+        const int c = tid / 27, r27 = tid % 27;
+        const int o = r27 / 9, i = (r27 / 3) % 3, ky = r27 % 3;
+        const int base = c == 0 ? 0 : 84;  // conv1 block first, then conv2
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            float s = 0.f;
+            for (int rg = 0; rg < 4; ++rg) s += sG[tid * 4 + rg][kx];
+            gp[base + ((o * 3 + i) * 3 + ky) * 3 + kx] = s;
+        }
+    } else if (tid < 60) {
+        const int task = tid - 54, c = task / 3, o = task % 3;
+        float s = 0.f;
+        for (int rg = 0; rg < 4; ++rg) s += sG[216 + task * 4 + rg][0];
+        gp[(c == 0 ? 81 : 84 + 81) + o] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Upsampling adjoint, stage s: D = d up[s-1] (7-s channels at grid s-1) -> dS_s at grid s.
+// Pass A (columns): T[j][py][ox] = sum_tau h_tau G_tau, G_tau = sum of D[j][oy][ox] over the
+//   output rows oy that read input row py through tap tau; dh_tau += G_tau * R[j][py][ox] with R
+//   the forward row-pass value.
+// Pass B (rows): dS[j][py][px] = sum_tau h_tau G'_tau over T; dh_tau += G'_tau * S[j][py][px].
+// ---------------------------------------------------------------------------------------------
+struct UpAdjArgs {
+    const float* D;      // [nch][ht][wt]
+    const float* src0;   // S_s channel 0 = y~ of grid s
+    const float* srcup;  // S_s channels 1.. = up[s]
+    float* T;            // [nch][hs][wt]
+    float* out0;         // dYsyn of grid s
+    float* outup;        // dup[s]
+    float* gpart;        // [gridDim.x][4]
+    int hs, ws, ht, wt, nch;
+    const float* taps;
+};
+
+// G[tau] for input index p along an axis with n_in inputs and n_out (cropped) outputs, reading
+// the output-side values through `get(o)`.
+template <typename F>
+__device__ __forceinline__ void gather_taps(int p, int n_in, int n_out, F get, float (&G)[4]) {
+    G[0] = G[1] = G[2] = G[3] = 0.f;
+    if (p >= 2 && p <= n_in - 3) {
+        const int o0 = 2 * p - 3;  // outputs 2p-3 .. 2p+4 use taps a b c d d c b a
+        const int tt[8] = {0, 1, 2, 3, 3, 2, 1, 0};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int o = o0 + q;
+            if (o < n_out) G[tt[q]] += get(o);
+        }
+    } else {
+        const int lo = max(0, 2 * p - 7), hi = min(n_out - 1, 2 * p + 8);
+        for (int o = lo; o <= hi; ++o) {
+            int f, tap[4];
+            poly(o, f, tap);
+            const float v = get(o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (clampi(f + q, 0, n_in - 1) == p) G[tap[q]] += v;
+        }
+    }
+}
+
+__global__ void k_up_adj_cols(UpAdjArgs a) {
+    const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
+    float dh[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t total = (int64_t)a.nch * a.hs * a.wt;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / ((int64_t)a.hs * a.wt));
+        const int rem = (int)(e - (int64_t)j * a.hs * a.wt);
+        const int py = rem / a.wt, ox = rem - py * a.wt;
+        const float* Dj = a.D + (int64_t)j * a.ht * a.wt;
+        float G[4];
+        gather_taps(py, a.hs, a.ht, [&](int oy) { return __ldg(Dj + (int64_t)oy * a.wt + ox); }, G);
+        a.T[e] = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
+        // forward row-pass value R[j][py][ox]
+        const float* S = (j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws) + (int64_t)py * a.ws;
+        int fx, tx[4];
+        poly(ox, fx, tx);
+        float R = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) R = fmaf(tp[tx[q]], __ldg(S + clampi(fx + q, 0, a.ws - 1)), R);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], R, dh[q]);
+    }
+    __shared__ float scratch[4 * (kUpThreads / 32)];
+    block_sum<4>(dh, scratch);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 4; ++q) a.gpart[blockIdx.x * 4 + q] = dh[q];
+}
+
+__global__ void k_up_adj_rows(UpAdjArgs a) {
+    const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
+    float dh[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t total = (int64_t)a.nch * a.hs * a.ws;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / ((int64_t)a.hs * a.ws));
+        const int rem = (int)(e - (int64_t)j * a.hs * a.ws);
+        const int py = rem / a.ws, px = rem - py * a.ws;
+        const float* Tr = a.T + (int64_t)j * a.hs * a.wt + (int64_t)py * a.wt;
+        float G[4];
+        gather_taps(px, a.ws, a.wt, [&](int ox) { return Tr[ox]; }, G);
+        const float d = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
+        const int64_t si = (int64_t)py * a.ws + px;
+        const float sv = j == 0 ? __ldg(a.src0 + si) : __ldg(a.srcup + (int64_t)(j - 1) * a.hs * a.ws + si);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], sv, dh[q]);
+        if (j == 0)
+            a.out0[si] = d;
+        else
+            a.outup[(int64_t)(j - 1) * a.hs * a.ws + si] = d;
+    }
+    __shared__ float scratch[4 * (kUpThreads / 32)];
+    block_sum<4>(dh, scratch);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 4; ++q) a.gpart[blockIdx.x * 4 + q] = dh[q];
+}
+
+int up_grid(int64_t total) {
+    int64_t b = (total + kUpThreads - 1) / kUpThreads;
+    if (b < 1) b = 1;
+    return (int)(b < kUpMaxCta ? b : kUpMaxCta);
+}
+
+}  // namespace
+
+int up_adj_grid(int64_t total) { return up_grid(total); }
+
+size_t syn_bwd_smem_bytes() { return (size_t)(ss_total + 2 * 48 * kSLd + kSTasks * 64) * sizeof(float); }
+
+int conv_tiles(int H, int W) { return ((H + kTH - 1) / kTH) * ((W + kTW - 1) / kTW); }
+
+void synth_init_attributes() {
+    const int sm = (int)syn_bwd_smem_bytes();
+    cudaFuncSetAttribute(k_syn_bwd<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_syn_bwd<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+void launch_up_forward(const Work& w, const float* params, cudaStream_t s) {
+    const Geom& g = w.g;
+    for (int m = kL - 2; m >= 1; --m) {  // stage s = m + 1
+        UpFwdArgs a;
+        a.src0 = w.yt + g.off[m + 1];
+        a.srcup = w.up[m + 1];
+        a.dst = w.up[m];
+        a.hs = g.h[m + 1];
+        a.ws = g.w[m + 1];
+        a.ht = g.h[m];
+        a.wt = g.w[m];
+        a.nch = kL - 1 - m;
+        a.taps = params + po::up + 4 * m;
+        const int64_t total = (int64_t)a.nch * a.ht * a.wt;
+        k_up_fwd<<<up_grid(total), kUpThreads, 0, s>>>(a);
+    }
+}
+
+static SynArgs syn_args(const Work& w, const float* params) {
+    SynArgs a;
+    a.g = w.g;
+    a.HW = w.HW;
+    a.yt = w.yt;
+    a.up1 = w.up[1];
+    a.params = params;
+    a.t = w.t;
+    a.dt = w.dt;
+    a.act = w.act_syn;
+    a.dYsyn0 = w.dYsyn;
+    a.dz = w.dz;
+    a.gpart = w.gpart_syn;
+    return a;
+}
+
+void launch_syn_forward(const Work& w, const float* params, int pass, cudaStream_t s) {
+    SynArgs a = syn_args(w, params);
+    int64_t blocks = (w.HW + kSynThreads - 1) / kSynThreads;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    if (pass == PASS_FWD_STORE)
+        k_syn_fwd<PASS_FWD_STORE><<<(int)blocks, kSynThreads, 0, s>>>(a);
+    else
+        k_syn_fwd<PASS_FWD><<<(int)blocks, kSynThreads, 0, s>>>(a);
+}
+
+void launch_syn_backward(const Work& w, const float* params, int pass, cudaStream_t s) {
+    SynArgs a = syn_args(w, params);
+    const size_t sm = syn_bwd_smem_bytes();
+    if (pass == PASS_BWD_LOAD)
+        k_syn_bwd<PASS_BWD_LOAD><<<w.n_cta_syn, kSynThreads, sm, s>>>(a);
+    else
+        k_syn_bwd<PASS_FWD_BWD><<<w.n_cta_syn, kSynThreads, sm, s>>>(a);
+}
+
+void launch_conv(const Work& w, const float* params, const float* image, int pass, float grad_scale,
+                 float* xhat_out, cudaStream_t s) {
+    ConvArgs a;
+    a.H = w.g.H;
+    a.W = w.g.W;
+    a.HW = w.HW;
+    a.t = w.t;
+    a.img = image;
+    a.params = params;
+    a.gscale = grad_scale;
+    a.dt = w.dt;
+    a.xhat = xhat_out;
+    a.gpart = w.gpart_conv;
+    a.se_part = w.se_part;
+    a.tiles_x = (w.g.W + kTW - 1) / kTW;
+    a.n_tiles = conv_tiles(w.g.H, w.g.W);
+    if (pass_bwd(pass))
+        k_conv<PASS_FWD_BWD><<<w.n_cta_conv, kConvThreads, 0, s>>>(a);
+    else
+        k_conv<PASS_FWD><<<w.n_cta_conv, kConvThreads, 0, s>>>(a);
+}
+
+void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
+    const Geom& g = w.g;
+    for (int st = 1; st < kL; ++st) {  // stage st: grid st -> grid st-1
+        UpAdjArgs a;
+        a.D = st == 1 ? w.dz : w.dup[st - 1];
+        a.src0 = w.yt + g.off[st];
+        a.srcup = w.up[st];
+        a.T = w.tmp;
+        a.out0 = w.dYsyn + g.off[st];
+        a.outup = w.dup[st];
+        a.hs = g.h[st];
+        a.ws = g.w[st];
+        a.ht = g.h[st - 1];
+        a.wt = g.w[st - 1];
+        a.nch = kL - st;
+        a.taps = params + po::up + 4 * (st - 1);
+        a.gpart = w.gpart_up + ((st - 1) * 2 + 0) * kUpMaxCta * 4;
+        k_up_adj_cols<<<w.n_cta_up[st][0], kUpThreads, 0, s>>>(a);
+        a.gpart = w.gpart_up + ((st - 1) * 2 + 1) * kUpMaxCta * 4;
+        k_up_adj_rows<<<w.n_cta_up[st][1], kUpThreads, 0, s>>>(a);
+    }
+}
+
+}  // namespace cc

@@ -1,0 +1,205 @@
+"""Thin ctypes binding of libcoolchic.so (include/coolchic.h).
+
+Argument marshalling only: torch tensors supply device memory and streams, every computation
+runs in the library's CUDA kernels.  There is no CPU fallback; if the library cannot be loaded
+the import fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcoolchic.so")
+
+CC_OK = 0
+CC_RELAX_NOISE, CC_RELAX_HARD, CC_RELAX_IDENTITY = 0, 1, 2
+N_GRIDS = 7
+N_PARAMS = 1415
+
+
+class Arch(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("C", "H", "W", "L", "n_ctx", "ifce_dim", "ifce_grids",
+                                              "arm_hidden", "arm_layers", "syn_hidden", "n_resconv",
+                                              "up_taps", "stabilizer")]
+
+
+class HParams(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_float), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("noise_mode", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("latents", ctypes.c_void_p), ("params", ctypes.c_void_p), ("m_lat", ctypes.c_void_p),
+                ("v_lat", ctypes.c_void_p), ("m_par", ctypes.c_void_p), ("v_par", ctypes.c_void_p),
+                ("step", ctypes.c_void_p)]
+
+
+class RD(ctypes.Structure):
+    _fields_ = [("loss", ctypes.c_double), ("rate_bits", ctypes.c_double), ("mse", ctypes.c_double)]
+
+
+class CoolChicError(RuntimeError):
+    pass
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2605_02726_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp, i32, i64, sz, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_float
+    sig = {
+        "coolchic_arch_init": (i32, [P(Arch), i32, i32]),
+        "coolchic_latent_count": (i64, [P(Arch)]),
+        "coolchic_param_count": (i64, [P(Arch)]),
+        "coolchic_param_block": (i32, [i32, P(ctypes.c_char_p), P(i32), P(i32)]),
+        "coolchic_workspace_bytes": (sz, [P(Arch), i32]),
+        "coolchic_encode_step": (i32, [P(Arch), P(HParams), vp, P(State), i32, vp, vp, sz, vp]),
+        "coolchic_forward": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, i32, vp, vp, vp, sz, vp]),
+        "coolchic_backward": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, i32, f32, vp, vp, vp, sz, vp]),
+        "coolchic_rate_distortion": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, P(RD), vp, sz, vp]),
+        "coolchic_decode_image": (i32, [P(Arch), vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "coolchic_last_error": (ctypes.c_char_p, []),
+        "coolchic_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count", "coolchic_param_block",
+            "coolchic_workspace_bytes", "coolchic_encode_step", "coolchic_forward", "coolchic_backward",
+            "coolchic_rate_distortion", "coolchic_decode_image", "coolchic_last_error", "coolchic_version"]
+
+
+def raw():
+    """The ctypes library handle (for tests of the C ABI itself)."""
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != CC_OK:
+        raise CoolChicError(f"{what} failed ({rc}): {_lib.coolchic_last_error().decode()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def arch(H: int, W: int) -> Arch:
+    a = Arch()
+    _check(_lib.coolchic_arch_init(ctypes.byref(a), H, W), "arch_init")
+    return a
+
+
+def hparams(lam=1e-3, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, seed=0) -> HParams:
+    return HParams(lam, lr, beta1, beta2, eps, 0, seed)
+
+
+def latent_count(H: int, W: int) -> int:
+    return int(_lib.coolchic_latent_count(ctypes.byref(arch(H, W))))
+
+
+def param_blocks():
+    out = []
+    i = 0
+    while True:
+        name = ctypes.c_char_p()
+        off, ln = ctypes.c_int32(), ctypes.c_int32()
+        if _lib.coolchic_param_block(i, ctypes.byref(name), ctypes.byref(off), ctypes.byref(ln)) != CC_OK:
+            break
+        out.append((name.value.decode(), off.value, ln.value))
+        i += 1
+    return out
+
+
+def workspace(H: int, W: int, store_activations: bool = False, device=None) -> torch.Tensor:
+    """Device workspace for one job (256-byte aligned byte tensor)."""
+    n = int(_lib.coolchic_workspace_bytes(ctypes.byref(arch(H, W)), 1 if store_activations else 0))
+    if n == 0:
+        raise CoolChicError(_lib.coolchic_last_error().decode())
+    buf = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + n]
+
+
+class EncoderState:
+    """Device-resident encoder state: latents, parameters, Adam moments, step counter."""
+
+    def __init__(self, latents: torch.Tensor, params: torch.Tensor, step: int = 0):
+        dev = latents.device
+        self.latents = latents.detach().clone().float().contiguous()
+        self.params = params.detach().clone().float().contiguous()
+        self.m_lat = torch.zeros_like(self.latents)
+        self.v_lat = torch.zeros_like(self.latents)
+        self.m_par = torch.zeros_like(self.params)
+        self.v_par = torch.zeros_like(self.params)
+        self.step = torch.full((1,), int(step), dtype=torch.int64, device=dev)
+
+    def c_state(self) -> State:
+        return State(self.latents.data_ptr(), self.params.data_ptr(), self.m_lat.data_ptr(), self.v_lat.data_ptr(),
+                     self.m_par.data_ptr(), self.v_par.data_ptr(), self.step.data_ptr())
+
+    def clone(self) -> "EncoderState":
+        s = EncoderState.__new__(EncoderState)
+        for k in ("latents", "params", "m_lat", "v_lat", "m_par", "v_par", "step"):
+            setattr(s, k, getattr(self, k).clone())
+        return s
+
+
+def encode_step(image, state: EncoderState, n_iters: int, *, H, W, hp: HParams, ws, rd=None, stream=None):
+    """n_iters encoder iterations in place; rd (optional, float64 [n_iters, 3]) gets loss/rate/mse."""
+    a = arch(H, W)
+    cs = state.c_state()
+    _check(_lib.coolchic_encode_step(ctypes.byref(a), ctypes.byref(hp), _ptr(image), ctypes.byref(cs), n_iters,
+                                     _ptr(rd), _ptr(ws), ws.numel(), _stream(stream)), "encode_step")
+
+
+def forward(image, latents, params, *, H, W, hp: HParams, step=0, relax=CC_RELAX_NOISE, ws, store=False,
+            rd=None, xhat=None, stream=None):
+    a = arch(H, W)
+    _check(_lib.coolchic_forward(ctypes.byref(a), ctypes.byref(hp), _ptr(image), _ptr(latents), _ptr(params),
+                                 int(step), relax, 1 if store else 0, _ptr(rd), _ptr(xhat), _ptr(ws), ws.numel(),
+                                 _stream(stream)), "forward")
+
+
+def backward(image, latents, params, grad_latents, grad_params, *, H, W, hp: HParams, step=0,
+             relax=CC_RELAX_NOISE, ws, use_stored=False, grad_scale=1.0, stream=None):
+    a = arch(H, W)
+    _check(_lib.coolchic_backward(ctypes.byref(a), ctypes.byref(hp), _ptr(image), _ptr(latents), _ptr(params),
+                                  int(step), relax, 1 if use_stored else 0, float(grad_scale), _ptr(grad_latents),
+                                  _ptr(grad_params), _ptr(ws), ws.numel(), _stream(stream)), "backward")
+
+
+def rate_distortion(image, latents, params, *, H, W, hp: HParams, step=0, relax=CC_RELAX_HARD, ws, stream=None):
+    a = arch(H, W)
+    out = RD()
+    _check(_lib.coolchic_rate_distortion(ctypes.byref(a), ctypes.byref(hp), _ptr(image), _ptr(latents),
+                                         _ptr(params), int(step), relax, ctypes.byref(out), _ptr(ws), ws.numel(),
+                                         _stream(stream)), "rate_distortion")
+    return dict(loss=out.loss, rate_bits=out.rate_bits, mse=out.mse)
+
+
+def decode_image(q_latents, params, *, H, W, ws, image_out=None, prob=None, mu_q=None, logb_q=None, stream=None):
+    a = arch(H, W)
+    _check(_lib.coolchic_decode_image(ctypes.byref(a), _ptr(q_latents), _ptr(params), _ptr(image_out), _ptr(prob),
+                                      _ptr(mu_q), _ptr(logb_q), _ptr(ws), ws.numel(), _stream(stream)),
+           "decode_image")

@@ -163,6 +163,21 @@ int coolchic_decode_image(const cc_arch_t* arch, const int32_t* q, const float* 
                           float* image_out, uint32_t* prob_q16, int32_t* mu_q, int32_t* logb_q,
                           void* workspace, size_t workspace_bytes, void* stream);
 
+/* Measurement hooks (no counterpart in the paper; used by benchmarks).  While enabled, every
+ * launch of the kernel `kernel_id` (CC_KERNEL_*) made by this library is bracketed by two CUDA
+ * events recorded on the launch stream, up to `max_launches` launches (the events are created
+ * here, on the current device).  Not for use under stream capture.  coolchic_timing_collect()
+ * synchronises on the recorded events and returns the summed duration in milliseconds and the
+ * number of timed launches; coolchic_timing_disable() destroys the events.  Returns CC_ERR_ARG
+ * for an unknown id, CC_ERR_CUDA if event creation fails. */
+#define CC_KERNEL_ARM 0      /* entropy model forward + adjoint */
+#define CC_KERNEL_SYN_BWD 1  /* synthesis adjoint               */
+#define CC_KERNEL_CONV 2     /* residual convs + distortion     */
+#define CC_KERNEL_SYN_FWD 3  /* synthesis forward               */
+int coolchic_timing_enable(int32_t kernel_id, int32_t max_launches);
+int coolchic_timing_collect(double* total_ms, int64_t* launches);
+int coolchic_timing_disable(void);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* coolchic_last_error(void);
 

@@ -114,8 +114,7 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     }
     for (int st = 1; st < kL; ++st) {
         const int nch = kL - st;
-        W.n_cta_up[st][0] = up_adj_grid((int64_t)nch * g.h[st] * g.w[st - 1]);
-        W.n_cta_up[st][1] = up_adj_grid((int64_t)nch * g.h[st] * g.w[st]);
+        W.n_cta_up[st] = up_adj_grid((int64_t)nch * g.h[st]);
     }
     Layout L;
     const size_t F = sizeof(float);
@@ -125,7 +124,7 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     for (int k = 0; k < kNIfce; ++k) o_dR[k] = L.take((size_t)ifce_nin(k) * g.h[k] * g.w[k] * F);
     size_t o_dYd = L.take(W.N * F);
     size_t o_dYsyn = L.take(W.N * F);
-    size_t o_dIf = L.take((size_t)(W.N - g.off[kNIfce] + 1) * F);
+    size_t o_dIf = L.take((size_t)4 * g.h[kNIfce] * g.w[kNIfce] * F);
     size_t o_up[kL] = {0}, o_dup[kL] = {0};
     for (int m = 1; m <= kL - 2; ++m) {
         o_up[m] = L.take((size_t)(kL - 1 - m) * g.h[m] * g.w[m] * F);
@@ -134,16 +133,11 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     size_t o_t = L.take(3 * W.HW * F);
     size_t o_dt = L.take(3 * W.HW * F);
     size_t o_dz = L.take(6 * W.HW * F);
-    size_t tmp_n = 1;
-    for (int st = 1; st < kL; ++st) {
-        size_t n = (size_t)(kL - st) * g.h[st] * g.w[st - 1];
-        if (n > tmp_n) tmp_n = n;
-    }
-    size_t o_tmp = L.take(tmp_n * F);
+    size_t o_tmp = L.take(F);
     size_t o_ga = L.take((size_t)W.n_cta_arm * po::arm_block * F);
     size_t o_gs = L.take((size_t)W.n_cta_syn * po::syn_block * F);
     size_t o_gc = L.take((size_t)W.n_cta_conv * po::conv_block * F);
-    size_t o_gu = L.take((size_t)6 * 2 * kUpMaxCta * 4 * F);
+    size_t o_gu = L.take((size_t)6 * kUpMaxCta * 4 * F);
     size_t o_rp = L.take((size_t)W.n_cta_arm * sizeof(double));
     size_t o_sp = L.take((size_t)W.n_cta_conv * sizeof(double));
     size_t o_gp = L.take(po::total * F);
@@ -205,6 +199,26 @@ int launched(const char* what) {
     return CC_OK;
 }
 
+// Measurement hooks: event pairs around the launches of one kernel.
+struct Timing {
+    int kernel = -1, cap = 0, used = 0;
+    std::vector<cudaEvent_t> ev;
+};
+std::mutex g_tm_mu;
+Timing g_tm;
+
+void tbeg(int id, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    if (g_tm.kernel == id && g_tm.used < g_tm.cap) cudaEventRecord(g_tm.ev[2 * g_tm.used], s);
+}
+void tend(int id, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    if (g_tm.kernel == id && g_tm.used < g_tm.cap) {
+        cudaEventRecord(g_tm.ev[2 * g_tm.used + 1], s);
+        ++g_tm.used;
+    }
+}
+
 }  // namespace
 
 int num_sms() {
@@ -224,10 +238,22 @@ static void run_forward(const Work& w, const float* image, const float* latents,
                         const int64_t* step_dev, int64_t step_host, uint64_t seed, int relax, int arm_pass,
                         int syn_pass, int conv_pass, float arm_gscale, float conv_gscale, float* xhat, cudaStream_t s) {
     launch_relax(w, latents, step_dev, step_host, seed, relax, s);
+    tbeg(CC_KERNEL_ARM, s);
     launch_arm(w, params, arm_pass, arm_gscale, s);
+    tend(CC_KERNEL_ARM, s);
     launch_up_forward(w, params, s);
+    tbeg(CC_KERNEL_SYN_FWD, s);
     launch_syn_forward(w, params, syn_pass, s);
+    tend(CC_KERNEL_SYN_FWD, s);
+    tbeg(CC_KERNEL_CONV, s);
     launch_conv(w, params, image, conv_pass, conv_gscale, xhat, s);
+    tend(CC_KERNEL_CONV, s);
+}
+
+static void syn_backward_timed(const Work& w, const float* params, int pass, cudaStream_t s) {
+    tbeg(CC_KERNEL_SYN_BWD, s);
+    launch_syn_backward(w, params, pass, s);
+    tend(CC_KERNEL_SYN_BWD, s);
 }
 
 }  // namespace cc
@@ -309,7 +335,7 @@ int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const fl
     for (int it = 0; it < n_iters; ++it) {
         run_forward(w, image, st->latents, st->params, st->step, 0, h.seed, kRelaxNoise, PASS_FWD_BWD, PASS_FWD,
                     PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s);
-        launch_syn_backward(w, st->params, PASS_FWD_BWD, s);
+        syn_backward_timed(w, st->params, PASS_FWD_BWD, s);
         launch_up_adjoint(w, st->params, s);
         launch_gather(w, st->params, kRelaxNoise, nullptr, st->latents, st->m_lat, st->v_lat, h, st->step, s);
         launch_param_reduce(w, st->params, st->m_par, st->v_par, nullptr, 1.f, h, st->step, s);
@@ -355,13 +381,17 @@ int coolchic_backward(const cc_arch_t* arch, const cc_hparams_t* hp, const float
     const float conv_gs = 2.f / (3.f * (float)w.HW) * grad_scale;
     if (use_stored) {
         // y~, upsampled grids and t are still in the workspace from coolchic_forward
+        tbeg(CC_KERNEL_ARM, s);
         launch_arm(w, params, PASS_BWD_LOAD, arm_gs, s);
+        tend(CC_KERNEL_ARM, s);
+        tbeg(CC_KERNEL_CONV, s);
         launch_conv(w, params, image, PASS_FWD_BWD, conv_gs, nullptr, s);
-        launch_syn_backward(w, params, PASS_BWD_LOAD, s);
+        tend(CC_KERNEL_CONV, s);
+        syn_backward_timed(w, params, PASS_BWD_LOAD, s);
     } else {
         run_forward(w, image, latents, params, nullptr, step, h.seed, relax, PASS_FWD_BWD, PASS_FWD, PASS_FWD_BWD,
                     arm_gs, conv_gs, nullptr, s);
-        launch_syn_backward(w, params, PASS_FWD_BWD, s);
+        syn_backward_timed(w, params, PASS_FWD_BWD, s);
     }
     launch_up_adjoint(w, params, s);
     launch_gather(w, params, relax, grad_latents, nullptr, nullptr, nullptr, h, nullptr, s);
@@ -411,6 +441,52 @@ int coolchic_decode_image(const cc_arch_t* arch, const int32_t* q, const float* 
         launch_clamp01(image_out, 3 * w.HW, s);
     }
     return launched("decode_image");
+}
+
+int coolchic_timing_enable(int32_t kernel_id, int32_t max_launches) {
+    if (kernel_id < CC_KERNEL_ARM || kernel_id > CC_KERNEL_SYN_FWD) return fail(CC_ERR_ARG, "unknown kernel id %d", kernel_id);
+    if (max_launches < 1 || max_launches > (1 << 20)) return fail(CC_ERR_ARG, "max_launches outside 1..2^20");
+    coolchic_timing_disable();
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    g_tm.ev.assign(2 * (size_t)max_launches, nullptr);
+    for (auto& e : g_tm.ev) {
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) {
+            for (auto& x : g_tm.ev)
+                if (x) cudaEventDestroy(x);
+            g_tm.ev.clear();
+            return fail(CC_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(r));
+        }
+    }
+    g_tm.kernel = kernel_id;
+    g_tm.cap = max_launches;
+    g_tm.used = 0;
+    return CC_OK;
+}
+
+int coolchic_timing_collect(double* total_ms, int64_t* launches) {
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    double tot = 0.0;
+    for (int i = 0; i < g_tm.used; ++i) {
+        cudaError_t r = cudaEventSynchronize(g_tm.ev[2 * i + 1]);
+        float ms = 0.f;
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, g_tm.ev[2 * i], g_tm.ev[2 * i + 1]);
+        if (r != cudaSuccess) return fail(CC_ERR_CUDA, "timing collect: %s", cudaGetErrorString(r));
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = g_tm.used;
+    return CC_OK;
+}
+
+int coolchic_timing_disable(void) {
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    for (auto& e : g_tm.ev)
+        if (e) cudaEventDestroy(e);
+    g_tm.ev.clear();
+    g_tm.kernel = -1;
+    g_tm.cap = g_tm.used = 0;
+    return CC_OK;
 }
 
 const char* coolchic_last_error(void) { return g_err.c_str(); }

@@ -37,13 +37,17 @@ __host__ __device__ constexpr int ifce_b_off(int k) { return k == 0 ? po::if_b0 
 __host__ __device__ constexpr int ifce_nin(int k) { return k < kNIfce ? kL - k - 1 : 0; }
 
 // Causal context offsets (dy, dx), nearest first; 3 rows up, 3 columns either side.
+// (written as selects so that no lookup table is ever materialised in local memory)
+//   n : 0  1  2  3  4  5  6  7  8  9 10 11 12 13 14 15
+//   dy: 0 -1 -1 -1  0 -2 -1 -1 -2 -2 -2 -2  0 -3 -1 -1
+//   dx:-1  0 -1  1 -2  0 -2  2 -1  1 -2  2 -3  0 -3  3
 __host__ __device__ constexpr int ctx_dy(int n) {
-    constexpr int t[kNCtx] = {0, -1, -1, -1, 0, -2, -1, -1, -2, -2, -2, -2, 0, -3, -1, -1};
-    return t[n];
+    return (n == 0 || n == 4 || n == 12) ? 0 : (n == 5 || (n >= 8 && n <= 11)) ? -2 : (n == 13) ? -3 : -1;
 }
 __host__ __device__ constexpr int ctx_dx(int n) {
-    constexpr int t[kNCtx] = {-1, 0, -1, 1, -2, 0, -2, 2, -1, 1, -2, 2, -3, 0, -3, 3};
-    return t[n];
+    return n == 0 ? -1 : n == 1 ? 0 : n == 2 ? -1 : n == 3 ? 1 : n == 4 ? -2 : n == 5 ? 0 : n == 6 ? -2
+         : n == 7 ? 2 : n == 8 ? -1 : n == 9 ? 1 : n == 10 ? -2 : n == 11 ? 2 : n == 12 ? -3 : n == 13 ? 0
+         : n == 14 ? -3 : 3;
 }
 
 struct Geom {
@@ -151,6 +155,14 @@ __device__ __forceinline__ void block_sum(float (&v)[NV], float* scratch) {
     __syncthreads();
 }
 
+// Asynchronous 4-byte global -> shared copy (no register staging, latencies overlap);
+// cp_async_wait_all() waits for all of this thread's copies.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // GELU, exact erf form, and its derivative.
 __device__ __forceinline__ float gelu_f(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float a) {
@@ -160,15 +172,18 @@ __device__ __forceinline__ float gelu_grad_f(float a) {
 // Polyphase taps of the x2 upsampler (Sec. III-B): output position o reads 4 inputs at
 // p-2..p+1 (even o) or p-1..p+2 (odd o), p = o >> 1, with tap order
 //   even: a c d b      odd: b d c a       (a, b, c, d = taps[0..3])
-__device__ __forceinline__ void poly(int o, int& first, int (&tap)[4]) {
-    int p = o >> 1;
-    if ((o & 1) == 0) {
-        first = p - 2;
-        tap[0] = 0; tap[1] = 2; tap[2] = 3; tap[3] = 1;
-    } else {
-        first = p - 1;
-        tap[0] = 1; tap[1] = 3; tap[2] = 2; tap[3] = 0;
-    }
+// Written with selects on constant indices so that nothing is indexed dynamically.
+__device__ __forceinline__ int poly_first(int o) { return (o >> 1) - 2 + (o & 1); }
+__device__ __forceinline__ int poly_tap(int o, int q) {  // tap index (0..3) of the q-th input
+    const bool odd = o & 1;
+    return q == 0 ? (odd ? 1 : 0) : q == 1 ? (odd ? 3 : 2) : q == 2 ? (odd ? 2 : 3) : (odd ? 0 : 1);
+}
+__device__ __forceinline__ void poly_w(int o, const float (&tp)[4], float (&w)[4]) {
+    const bool odd = o & 1;
+    w[0] = odd ? tp[1] : tp[0];
+    w[1] = odd ? tp[3] : tp[2];
+    w[2] = odd ? tp[2] : tp[3];
+    w[3] = odd ? tp[0] : tp[1];
 }
 
 }  // namespace cc

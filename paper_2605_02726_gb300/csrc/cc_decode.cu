@@ -36,10 +36,12 @@ __device__ __forceinline__ long long cdf_q16(int s, long long t) {
     return t >= 0 ? 65536 - e : e;
 }
 
-__global__ void k_decode_arm(Geom g, const int32_t* __restrict__ q, const float* __restrict__ P, float* yq,
+__global__ void k_decode_arm(Geom gp, const int32_t* __restrict__ q, const float* __restrict__ P, float* yq,
                              uint32_t* prob, int32_t* mu_out, int32_t* logb_out) {
     __shared__ long long sW[po::arm_block];
+    __shared__ Geom g;  // shared copy: the grid tables are indexed with a runtime grid number
     for (int j = threadIdx.x; j < po::arm_block; j += blockDim.x) sW[j] = q8(P[j]);
+    if (threadIdx.x == 0) g = gp;
     __syncthreads();
     const int64_t N = g.off[kL];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {

@@ -36,7 +36,7 @@ struct Work {
     float* dR[3];      // IFCE-input gradient planes: grid k has ifce_nin(k) planes of h_k*w_k
     float* dYd;        // direct rate gradient [N]
     float* dYsyn;      // gradient reaching each grid through upsampling + synthesis [N]
-    float* dIf;        // IFCE gradient reaching grids >= 3 [N - off[3]]
+    float* dIf;        // IFCE gradient of grids 3..6 summed per grid-3 cell [4][h_3*w_3]
     float* up[kL];     // up[m], m = 1..5: channels of grids m+1..6 upsampled to grid m
     float* dup[kL];    // adjoints of up[m], m = 1..5
     float* t;          // synthesis output before the residual convs [3][HW]
@@ -48,13 +48,13 @@ struct Work {
     float* gpart_arm;  // per-CTA partial gradients [n_cta_arm][756]
     float* gpart_syn;  // [n_cta_syn][467]
     float* gpart_conv; // [n_cta_conv][168]
-    float* gpart_up;   // [6 stages][2 passes][kUpMaxCta][4]
+    float* gpart_up;   // [6 stages][kUpMaxCta][4]
     double* rate_part; // [n_cta_arm]
     double* se_part;   // [n_cta_conv]
     float* grad_params;// [1415] reduced parameter gradient
     int64_t* base_step;// step at the start of an encode call
     int n_cta_arm, n_cta_syn, n_cta_conv;
-    int n_cta_up[kL][2];  // CTAs used by each upsampling-adjoint pass (stage s = 1..6)
+    int n_cta_up[kL];  // CTAs of the upsampling-adjoint kernel of stage s = 1..6
 };
 
 int num_sms();
@@ -90,7 +90,7 @@ size_t arm_smem_bytes(int pass);
 int arm_grid(int64_t N);
 size_t syn_bwd_smem_bytes();
 int conv_tiles(int H, int W);
-int up_adj_grid(int64_t total);
+int up_adj_grid(int64_t pairs);
 void arm_init_attributes();
 void synth_init_attributes();
 

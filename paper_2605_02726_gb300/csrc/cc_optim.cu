@@ -14,51 +14,55 @@ __global__ void k_relax(const float* __restrict__ y, float* __restrict__ yt, int
     }
 }
 
-// IFCE gradient of a latent of grid g >= 3: sum over the finer grids k' = 0..2 of the block of
-// grid-k' latents whose IFCE reads it, channel g - k' - 1 of dR_k'.  One warp per latent.
-__global__ void k_ifce_pool(Geom g, const float* dR0, const float* dR1, const float* dR2, float* dIf) {
-    const int lane = threadIdx.x & 31;
-    const int64_t first = g.off[kNIfce], n = g.off[kL] - first;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = wid; j < n; j += nw) {
-        const int64_t i = first + j;
-        const int gg = grid_of(g, i);
-        const int li = (int)(i - g.off[gg]);
-        const int r = li / g.w[gg], c = li - r * g.w[gg];
-        float acc = 0.f;
-        for (int kp = 0; kp < kNIfce; ++kp) {
-            const float* dR = kp == 0 ? dR0 : (kp == 1 ? dR1 : dR2);
-            const int sh = gg - kp, ch = gg - kp - 1;
-            const int hk = g.h[kp], wk = g.w[kp];
-            const int r0 = r << sh, c0 = c << sh;
-            const int bh = min(1 << sh, hk - r0), bw = min(1 << sh, wk - c0);
-            const float* plane = dR + (int64_t)ch * hk * wk;
-            for (int e = lane; e < bh * bw; e += 32) {
-                const int rr = e / bw, cc = e - rr * bw;
-                acc += plane[(int64_t)(r0 + rr) * wk + c0 + cc];
-            }
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) dIf[j] = acc;
+// IFCE gradient reaching the coarse grids g >= 3, first stage.  A latent of grid g is read by
+// the IFCE of grid k' (k' = 0..2) at every position of the 2^(g-k') x 2^(g-k') block under it,
+// through channel g - k' - 1 of dR_k'.  Every such block is a union of the blocks under the
+// grid-3 cells, so per grid-3 cell and per g: Q[g-3][cell] = sum_k' (block of 2^(3-k') x 2^(3-k')
+// under the cell of dR_k' channel g - k' - 1).  One thread per (g, cell); fixed-size unrolled
+// loads.  The gather kernel adds Q over the 2^(g-3) x 2^(g-3) cells under each grid-g latent.
+template <int B>
+__device__ __forceinline__ float block_sum_clipped(const float* __restrict__ plane, int h, int w, int r0, int c0) {
+    float acc = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < B; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < B; ++cc)
+            if (r0 + rr < h && c0 + cc < w) acc += __ldg(plane + (int64_t)(r0 + rr) * w + c0 + cc);
+    return acc;
+}
+
+__global__ void k_ifce_cells(Geom g, const float* __restrict__ dR0, const float* __restrict__ dR1,
+                             const float* __restrict__ dR2, float* Q) {
+    const int n3 = g.h[3] * g.w[3];
+    const int64_t n0 = (int64_t)g.h[0] * g.w[0], n1 = (int64_t)g.h[1] * g.w[1], n2 = (int64_t)g.h[2] * g.w[2];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 4 * (int64_t)n3;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int gg = 3 + (int)(e / n3), cell = (int)(e % n3);
+        const int r3 = cell / g.w[3], c3 = cell - r3 * g.w[3];
+        float acc = block_sum_clipped<8>(dR0 + (gg - 1) * n0, g.h[0], g.w[0], 8 * r3, 8 * c3);
+        acc += block_sum_clipped<4>(dR1 + (gg - 2) * n1, g.h[1], g.w[1], 4 * r3, 4 * c3);
+        acc += block_sum_clipped<2>(dR2 + (gg - 3) * n2, g.h[2], g.w[2], 2 * r3, 2 * c3);
+        Q[e] = acc;
     }
 }
 
 // Latent gradient: direct rate term + the 16 context users + IFCE users + upsampling/synthesis,
 // then Adam on (y, m, v) or a copy to grad_out.
-__global__ void k_gather(Geom g, const float* __restrict__ dYd, const float* __restrict__ dS,
+__global__ void k_gather(Geom gp, const float* __restrict__ dYd, const float* __restrict__ dS,
                          const float* __restrict__ dR0, const float* __restrict__ dR1,
                          const float* __restrict__ dIf, const float* __restrict__ dYsyn, int zero_grad,
                          float* grad_out, float* y, float* m, float* v, Hp hp, const int64_t* step_dev) {
     __shared__ float s_bc[2];
-    if (!grad_out) {
-        if (threadIdx.x == 0) {
+    __shared__ Geom g;  // shared copy: the grid tables are indexed with a runtime grid number
+    if (threadIdx.x == 0) {
+        g = gp;
+        if (!grad_out) {
             const double t = (double)(*step_dev + 1);
             s_bc[0] = (float)(1.0 - pow((double)hp.beta1, t));
             s_bc[1] = (float)(1.0 - pow((double)hp.beta2, t));
         }
-        __syncthreads();
     }
+    __syncthreads();
     const int64_t N = g.off[kL];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int k = grid_of(g, i);
@@ -84,8 +88,16 @@ __global__ void k_gather(Geom g, const float* __restrict__ dYd, const float* __r
                 for (int rr = 0; rr < bh; ++rr)
                     for (int cc = 0; cc < bw; ++cc) acc += __ldg(plane + (int64_t)(r0 + rr) * wp + c0 + cc);
             }
-        } else if (k >= kNIfce) {
-            acc += dIf[i - g.off[kNIfce]];
+        } else if (k == kNIfce) {
+            acc += dIf[li];
+        } else if (k > kNIfce) {
+            // grid k >= 4: the 2^(k-3) x 2^(k-3) grid-3 cells under (r, c), plane k-3 of Q
+            const int sh = k - kNIfce, h3 = g.h[kNIfce], w3 = g.w[kNIfce];
+            const float* plane = dIf + (int64_t)sh * h3 * w3;
+            const int r0 = r << sh, c0 = c << sh;
+            const int bh = min(1 << sh, h3 - r0), bw = min(1 << sh, w3 - c0);
+            for (int rr = 0; rr < bh; ++rr)
+                for (int cc = 0; cc < bw; ++cc) acc += plane[(int64_t)(r0 + rr) * w3 + c0 + cc];
         }
         if (zero_grad) acc = 0.f;
         if (grad_out) {
@@ -101,40 +113,57 @@ __global__ void k_gather(Geom g, const float* __restrict__ dYd, const float* __r
 }
 
 // Fixed-order sum of the per-CTA partial parameter gradients, then Adam or a scaled copy.
-__global__ void k_param_reduce(const float* __restrict__ garm, int n_arm, const float* __restrict__ gup,
-                               int2 n_up0, int2 n_up1, int2 n_up2, int2 n_up3, int2 n_up4, int2 n_up5,
-                               const float* __restrict__ gsyn, int n_syn, const float* __restrict__ gconv,
-                               int n_conv, float* params, float* m, float* v, float* grad_out,
-                               float out_scale, Hp hp, const int64_t* step_dev) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= po::total) return;
-    float s0 = 0.f, s1 = 0.f;
-    if (p < po::up) {
-        for (int q = 0; q + 1 < n_arm; q += 2) {
-            s0 += garm[(int64_t)q * po::arm_block + p];
-            s1 += garm[(int64_t)(q + 1) * po::arm_block + p];
+// A CTA owns 32 consecutive parameters (one per lane); its 8 warps take interleaved slices of the
+// partial rows (coalesced across lanes) and their sums are added in warp order.
+struct UpCounts {
+    int n[kL - 1];
+};
+
+__global__ void __launch_bounds__(256) k_param_reduce(const float* __restrict__ garm, int n_arm,
+                                                      const float* __restrict__ gup, UpCounts nup,
+                                                      const float* __restrict__ gsyn, int n_syn,
+                                                      const float* __restrict__ gconv, int n_conv, float* params,
+                                                      float* m, float* v, float* grad_out, float out_scale, Hp hp,
+                                                      const int64_t* step_dev) {
+    __shared__ float red[8][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int p = blockIdx.x * 32 + lane;
+    float a0 = 0.f, a1 = 0.f;
+    if (p < po::total) {
+        const float* base;
+        int64_t stride;
+        int cnt;
+        if (p < po::up) {
+            base = garm + p;
+            stride = po::arm_block;
+            cnt = n_arm;
+        } else if (p < po::syn_w1) {
+            const int st = (p - po::up) >> 2;
+            base = gup + (int64_t)st * kUpMaxCta * 4 + ((p - po::up) & 3);
+            stride = 4;
+            cnt = nup.n[st];
+        } else if (p < po::cv1_w) {
+            base = gsyn + (p - po::syn_w1);
+            stride = po::syn_block;
+            cnt = n_syn;
+        } else {
+            base = gconv + (p - po::cv1_w);
+            stride = po::conv_block;
+            cnt = n_conv;
         }
-        if (n_arm & 1) s0 += garm[(int64_t)(n_arm - 1) * po::arm_block + p];
-    } else if (p < po::syn_w1) {
-        const int st = (p - po::up) >> 2, tap = (p - po::up) & 3;
-        const int2 nn[6] = {n_up0, n_up1, n_up2, n_up3, n_up4, n_up5};
-        for (int pass = 0; pass < 2; ++pass) {
-            const int cnt = pass == 0 ? nn[st].x : nn[st].y;
-            const float* base = gup + ((int64_t)(st * 2 + pass) * kUpMaxCta) * 4;
-            for (int q = 0; q < cnt; ++q) s0 += base[q * 4 + tap];
+        int q = wid;
+        for (; q + 8 < cnt; q += 16) {
+            a0 += __ldg(base + (int64_t)q * stride);
+            a1 += __ldg(base + (int64_t)(q + 8) * stride);
         }
-    } else if (p < po::cv1_w) {
-        const int j = p - po::syn_w1;
-        for (int q = 0; q + 1 < n_syn; q += 2) {
-            s0 += gsyn[(int64_t)q * po::syn_block + j];
-            s1 += gsyn[(int64_t)(q + 1) * po::syn_block + j];
-        }
-        if (n_syn & 1) s0 += gsyn[(int64_t)(n_syn - 1) * po::syn_block + j];
-    } else {
-        const int j = p - po::cv1_w;
-        for (int q = 0; q < n_conv; ++q) s0 += gconv[(int64_t)q * po::conv_block + j];
+        if (q < cnt) a0 += __ldg(base + (int64_t)q * stride);
     }
-    const float gsum = s0 + s1;
+    red[wid][lane] = a0 + a1;
+    __syncthreads();
+    if (wid != 0 || p >= po::total) return;
+    float gsum = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) gsum += red[w][lane];
     if (grad_out) {
         grad_out[p] = gsum * out_scale;
         return;
@@ -203,19 +232,19 @@ void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_
 void launch_gather(const Work& w, const float* params, int relax, float* grad_out, float* y, float* m, float* v,
                    const Hp& hp, const int64_t* step_dev, cudaStream_t s) {
     (void)params;
-    const int64_t n_coarse = w.N - w.g.off[kNIfce];
-    if (n_coarse > 0) k_ifce_pool<<<grid_for(n_coarse * 32, 256, 8), 256, 0, s>>>(w.g, w.dR[0], w.dR[1], w.dR[2], w.dIf);
+    const int64_t n_cells = 4 * (int64_t)w.g.h[kNIfce] * w.g.w[kNIfce];
+    k_ifce_cells<<<grid_for(n_cells, 128, 8), 128, 0, s>>>(w.g, w.dR[0], w.dR[1], w.dR[2], w.dIf);
     k_gather<<<grid_for(w.N, 256, 8), 256, 0, s>>>(w.g, w.dYd, w.dS, w.dR[0], w.dR[1], w.dIf, w.dYsyn,
                                                    relax == kRelaxHard ? 1 : 0, grad_out, y, m, v, hp, step_dev);
 }
 
 void launch_param_reduce(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,
                          const Hp& hp, const int64_t* step_dev, cudaStream_t s) {
-    int2 nu[6];
-    for (int st = 1; st < kL; ++st) nu[st - 1] = make_int2(w.n_cta_up[st][0], w.n_cta_up[st][1]);
-    k_param_reduce<<<(po::total + 127) / 128, 128, 0, s>>>(w.gpart_arm, w.n_cta_arm, w.gpart_up, nu[0], nu[1], nu[2],
-                                                           nu[3], nu[4], nu[5], w.gpart_syn, w.n_cta_syn, w.gpart_conv,
-                                                           w.n_cta_conv, params, m, v, grad_out, out_scale, hp, step_dev);
+    UpCounts nu;
+    for (int st = 1; st < kL; ++st) nu.n[st - 1] = w.n_cta_up[st];
+    k_param_reduce<<<(po::total + 31) / 32, 256, 0, s>>>(w.gpart_arm, w.n_cta_arm, w.gpart_up, nu, w.gpart_syn,
+                                                         w.n_cta_syn, w.gpart_conv, w.n_cta_conv, params, m, v,
+                                                         grad_out, out_scale, hp, step_dev);
 }
 
 void launch_finish(const Work& w, const Hp& hp, int have_arm, int have_conv, double* rd_out, int64_t* step_dev,

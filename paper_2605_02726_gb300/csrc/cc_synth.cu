@@ -27,17 +27,18 @@ __global__ void k_up_fwd(UpFwdArgs a) {
         const int rem = (int)(e - (int64_t)j * a.ht * a.wt);
         const int y = rem / a.wt, x = rem - y * a.wt;
         const float* S = j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws;
-        int fy, fx, ty[4], tx[4];
-        poly(y, fy, ty);
-        poly(x, fx, tx);
+        const int fy = poly_first(y), fx = poly_first(x);
+        float wy[4], wx[4];
+        poly_w(y, tp, wy);
+        poly_w(x, tp, wx);
         float acc = 0.f;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const float* row = S + clampi(fy + p, 0, a.hs - 1) * a.ws;
             float rs = 0.f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) rs = fmaf(tp[tx[q]], __ldg(row + clampi(fx + q, 0, a.ws - 1)), rs);
-            acc = fmaf(tp[ty[p]], rs, acc);
+            for (int q = 0; q < 4; ++q) rs = fmaf(wx[q], __ldg(row + clampi(fx + q, 0, a.ws - 1)), rs);
+            acc = fmaf(wy[p], rs, acc);
         }
         a.dst[e] = acc;
     }
@@ -48,17 +49,15 @@ __device__ __forceinline__ void dense_latents(const Geom& g, const float* yt, co
                                               const float (&tp)[4], int y, int x, float (&z)[kL]) {
     const int hs = g.h[1], ws = g.w[1];
     z[0] = __ldg(yt + (int64_t)y * g.W + x);
-    int fy, fx, ty[4], tx[4];
-    poly(y, fy, ty);
-    poly(x, fx, tx);
+    const int fy = poly_first(y), fx = poly_first(x);
     int ro[4], co[4];
     float wy[4], wx[4];
+    poly_w(y, tp, wy);
+    poly_w(x, tp, wx);
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         ro[p] = clampi(fy + p, 0, hs - 1) * ws;
         co[p] = clampi(fx + p, 0, ws - 1);
-        wy[p] = tp[ty[p]];
-        wx[p] = tp[tx[p]];
     }
     const int64_t n1 = (int64_t)hs * ws;
 #pragma unroll
@@ -307,270 +306,6 @@ __global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd(SynArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Residual 3x3 convolutions, distortion and adjoint on 16x32 pixel tiles with recomputed halos.
-//   x1 = t + b1 + conv1(t),  xh = x1 + b2 + conv2(x1)  (replicate padding),  D = mean (xh - x)^2.
-//   dxh = 2 (xh - x) / (3HW);  dx1 = dxh + conv2^T(dxh);  dt = dx1 + conv1^T(dx1).
-// The transposed convolution gathers, per axis, the 3 (source, tap) pairs whose clamped index
-// lands on the target: interior q <- (q+1, 0), (q, 1), (q-1, 2); q = 0 <- (0,0), (0,1), (1,0);
-// q = n-1 <- (n-1,1), (n-1,2), (n-2,2); n = 1 <- (0,0), (0,1), (0,2).
-// ---------------------------------------------------------------------------------------------
-constexpr int kTH = kConvTH, kTW = kConvTW;
-constexpr int kConvThreads = 256;
-constexpr int R4H = kTH + 8, R4W = kTW + 8;  // t region (halo 4)
-constexpr int R3H = kTH + 6, R3W = kTW + 6;  // x1
-constexpr int R2H = kTH + 4, R2W = kTW + 4;  // xh / dxh
-constexpr int R1H = kTH + 2, R1W = kTW + 2;  // dx1
-
-struct ConvArgs {
-    int H, W;
-    int64_t HW;
-    const float* t;
-    const float* img;
-    const float* params;
-    float gscale;      // 2 / (3 HW) times the caller's outer scale
-    float* dt;
-    float* xhat;       // optional
-    float* gpart;      // [gridDim.x][168]
-    double* se_part;   // [gridDim.x]
-    int tiles_x, n_tiles;
-};
-
-__device__ __forceinline__ void conv_pairs(int q, int n, int (&src)[3], int (&tap)[3]) {
-    if (n == 1) {
-        src[0] = 0; tap[0] = 0; src[1] = 0; tap[1] = 1; src[2] = 0; tap[2] = 2;
-    } else if (q == 0) {
-        src[0] = 0; tap[0] = 0; src[1] = 0; tap[1] = 1; src[2] = 1; tap[2] = 0;
-    } else if (q == n - 1) {
-        src[0] = n - 1; tap[0] = 1; src[1] = n - 1; tap[1] = 2; src[2] = n - 2; tap[2] = 2;
-    } else {
-        src[0] = q + 1; tap[0] = 0; src[1] = q; tap[1] = 1; src[2] = q - 1; tap[2] = 2;
-    }
-}
-
-template <int PASS>
-__global__ void __launch_bounds__(kConvThreads) k_conv(ConvArgs a) {
-    constexpr bool BWD = pass_bwd(PASS);
-    __shared__ float sWc[2][84];
-    __shared__ float sT[3][R4H][R4W];
-    __shared__ float sX1[3][R3H][R3W];
-    __shared__ float sD[3][R2H][R2W];   // xh, then dxh in place
-    __shared__ float sD1[3][R1H][R1W];
-    __shared__ double sSe[kConvThreads / 32];
-    const int tid = threadIdx.x;
-    for (int j = tid; j < 84; j += kConvThreads) {
-        sWc[0][j] = j < 81 ? a.params[po::cv1_w + j] : a.params[po::cv1_b + j - 81];
-        sWc[1][j] = j < 81 ? a.params[po::cv2_w + j] : a.params[po::cv2_b + j - 81];
-    }
-    // weight-gradient task of this thread: conv c, out o, in i, row tap ky, row group rg
-    // tasks 0..215: (c, o, i, ky, rg) ; tasks 216..239: bias (c, o, rg)
-    float gacc[3] = {0.f, 0.f, 0.f};
-    double se = 0.0;
-    const int H = a.H, W = a.W;
-    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-        const int ty0 = (tile / a.tiles_x) * kTH, tx0 = (tile % a.tiles_x) * kTW;
-        __syncthreads();
-        // t on the halo-4 region (clamped reads; positions outside the image are never used)
-        for (int e = tid; e < 3 * R4H * R4W; e += kConvThreads) {
-            const int c = e / (R4H * R4W), rem = e % (R4H * R4W);
-            const int ry = rem / R4W, rx = rem % R4W;
-            const int gy = clampi(ty0 - 4 + ry, 0, H - 1), gx = clampi(tx0 - 4 + rx, 0, W - 1);
-            sT[c][ry][rx] = a.t[(int64_t)c * a.HW + (int64_t)gy * W + gx];
-        }
-        __syncthreads();
-        // x1 on the halo-3 region
-        for (int e = tid; e < R3H * R3W; e += kConvThreads) {
-            const int ry = e / R3W, rx = e % R3W;
-            const int gy = ty0 - 3 + ry, gx = tx0 - 3 + rx;
-            if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
-            float in[3][3][3];
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const int sy = clampi(gy + ky - 1, 0, H - 1) - (ty0 - 4);
-                    const int sx = clampi(gx + kx - 1, 0, W - 1) - (tx0 - 4);
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) in[i][ky][kx] = sT[i][sy][sx];
-                }
-#pragma unroll
-            for (int o = 0; o < 3; ++o) {
-                float acc = sT[o][ry + 1][rx + 1] + sWc[0][81 + o];
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                        for (int kx = 0; kx < 3; ++kx) acc = fmaf(sWc[0][((o * 3 + i) * 3 + ky) * 3 + kx], in[i][ky][kx], acc);
-                sX1[o][ry][rx] = acc;
-            }
-        }
-        __syncthreads();
-        // xh, distortion and dxh on the halo-2 region
-        for (int e = tid; e < R2H * R2W; e += kConvThreads) {
-            const int ry = e / R2W, rx = e % R2W;
-            const int gy = ty0 - 2 + ry, gx = tx0 - 2 + rx;
-            if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
-            const bool core = ry >= 2 && ry < 2 + kTH && rx >= 2 && rx < 2 + kTW;
-            float in[3][3][3];
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const int sy = clampi(gy + ky - 1, 0, H - 1) - (ty0 - 3);
-                    const int sx = clampi(gx + kx - 1, 0, W - 1) - (tx0 - 3);
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) in[i][ky][kx] = sX1[i][sy][sx];
-                }
-#pragma unroll
-            for (int o = 0; o < 3; ++o) {
-                float acc = sX1[o][ry + 1][rx + 1] + sWc[1][81 + o];
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                        for (int kx = 0; kx < 3; ++kx) acc = fmaf(sWc[1][((o * 3 + i) * 3 + ky) * 3 + kx], in[i][ky][kx], acc);
-                const int64_t gi = (int64_t)o * a.HW + (int64_t)gy * W + gx;
-                const float diff = acc - __ldg(a.img + gi);
-                if (core) {
-                    se += (double)diff * diff;
-                    if (a.xhat) a.xhat[gi] = acc;
-                }
-                sD[o][ry][rx] = diff * a.gscale;
-            }
-        }
-        if (!BWD) continue;
-        __syncthreads();
-        // dx1 on the halo-1 region: dxh + conv2^T(dxh)
-        for (int e = tid; e < R1H * R1W; e += kConvThreads) {
-            const int ry = e / R1W, rx = e % R1W;
-            const int gy = ty0 - 1 + ry, gx = tx0 - 1 + rx;
-            if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
-            int sy[3], ky[3], sx[3], kx[3];
-            conv_pairs(gy, H, sy, ky);
-            conv_pairs(gx, W, sx, kx);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float acc = sD[i][ry + 1][rx + 1];
-#pragma unroll
-                for (int p = 0; p < 3; ++p)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q)
-#pragma unroll
-                        for (int o = 0; o < 3; ++o)
-                            acc = fmaf(sWc[1][((o * 3 + i) * 3 + ky[p]) * 3 + kx[q]],
-                                       sD[o][sy[p] - (ty0 - 2)][sx[q] - (tx0 - 2)], acc);
-                sD1[i][ry][rx] = acc;
-            }
-        }
-        __syncthreads();
-        // dt on the core: dx1 + conv1^T(dx1)
-        for (int e = tid; e < kTH * kTW; e += kConvThreads) {
-            const int ry = e / kTW, rx = e % kTW;
-            const int gy = ty0 + ry, gx = tx0 + rx;
-            if (gy >= H || gx >= W) continue;
-            int sy[3], ky[3], sx[3], kx[3];
-            conv_pairs(gy, H, sy, ky);
-            conv_pairs(gx, W, sx, kx);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float acc = sD1[i][ry + 1][rx + 1];
-#pragma unroll
-                for (int p = 0; p < 3; ++p)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q)
-#pragma unroll
-                        for (int o = 0; o < 3; ++o)
-                            acc = fmaf(sWc[0][((o * 3 + i) * 3 + ky[p]) * 3 + kx[q]],
-                                       sD1[o][sy[p] - (ty0 - 1)][sx[q] - (tx0 - 1)], acc);
-                a.dt[(int64_t)i * a.HW + (int64_t)gy * W + gx] = acc;
-            }
-        }
-        // parameter gradients over the core pixels (sums in a fixed order per thread)
-        if (tid < 216) {
-            const int rg = tid & 3, task = tid >> 2;          // task 0..53
-            const int c = task / 27, r27 = task % 27;
-            const int o = r27 / 9, i = (r27 / 3) % 3, ky = r27 % 3;
-            // conv c: gradient dU (sD for conv2, sD1 for conv1) times its input (sX1 / sT)
-            for (int ry = rg * 4; ry < rg * 4 + 4; ++ry) {
-                const int gy = ty0 + ry;
-                if (gy >= H) break;
-                const int iy = clampi(gy + ky - 1, 0, H - 1);
-                for (int rx = 0; rx < kTW; ++rx) {
-                    const int gx = tx0 + rx;
-                    if (gx >= W) break;
-                    float gval, v0, v1, v2;
-                    const int x0 = clampi(gx - 1, 0, W - 1), x2 = clampi(gx + 1, 0, W - 1);
-                    if (c == 1) {  // conv2 (second residual layer)
-                        gval = sD[o][ry + 2][rx + 2];
-                        v0 = sX1[i][iy - (ty0 - 3)][x0 - (tx0 - 3)];
-                        v1 = sX1[i][iy - (ty0 - 3)][gx - (tx0 - 3)];
-                        v2 = sX1[i][iy - (ty0 - 3)][x2 - (tx0 - 3)];
-                    } else {
-                        gval = sD1[o][ry + 1][rx + 1];
-                        v0 = sT[i][iy - (ty0 - 4)][x0 - (tx0 - 4)];
-                        v1 = sT[i][iy - (ty0 - 4)][gx - (tx0 - 4)];
-                        v2 = sT[i][iy - (ty0 - 4)][x2 - (tx0 - 4)];
-                    }
-                    gacc[0] = fmaf(gval, v0, gacc[0]);
-                    gacc[1] = fmaf(gval, v1, gacc[1]);
-                    gacc[2] = fmaf(gval, v2, gacc[2]);
-                }
-            }
-        } else if (tid < 240) {
-            const int rg = tid & 3, task = (tid - 216) >> 2;  // 0..5: conv c, out o
-            const int c = task / 3, o = task % 3;
-            for (int ry = rg * 4; ry < rg * 4 + 4; ++ry) {
-                const int gy = ty0 + ry;
-                if (gy >= H) break;
-                for (int rx = 0; rx < kTW; ++rx) {
-                    if (tx0 + rx >= W) break;
-                    gacc[0] += c == 1 ? sD[o][ry + 2][rx + 2] : sD1[o][ry + 1][rx + 1];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    // distortion partial
-    {
-        double v = warp_sum_d(se);
-        if ((tid & 31) == 0) sSe[tid >> 5] = v;
-        __syncthreads();
-        if (tid == 0) {
-            double s = 0.0;
-            for (int q = 0; q < kConvThreads / 32; ++q) s += sSe[q];
-            a.se_part[blockIdx.x] = s;
-        }
-    }
-    if (!BWD) return;
-    // reduce the 4 row groups of each task in a fixed order and write this CTA's partial
-    __shared__ float sG[240][3];
-    if (tid < 240) {
-        sG[tid][0] = gacc[0];
-        sG[tid][1] = gacc[1];
-        sG[tid][2] = gacc[2];
-    }
-    __syncthreads();
-    float* gp = a.gpart + (int64_t)blockIdx.x * po::conv_block;
-    if (tid < 54) {
-        const int c = tid / 27, r27 = tid % 27;
-        const int o = r27 / 9, i = (r27 / 3) % 3, ky = r27 % 3;
-        const int base = c == 0 ? 0 : 84;  // conv1 block first, then conv2
-#pragma unroll
-        for (int kx = 0; kx < 3; ++kx) {
-            float s = 0.f;
-            for (int rg = 0; rg < 4; ++rg) s += sG[tid * 4 + rg][kx];
-            gp[base + ((o * 3 + i) * 3 + ky) * 3 + kx] = s;
-        }
-    } else if (tid < 60) {
-        const int task = tid - 54, c = task / 3, o = task % 3;
-        float s = 0.f;
-        for (int rg = 0; rg < 4; ++rg) s += sG[216 + task * 4 + rg][0];
-        gp[(c == 0 ? 81 : 84 + 81) + o] = s;
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
 // Upsampling adjoint, stage s: D = d up[s-1] (7-s channels at grid s-1) -> dS_s at grid s.
 // Pass A (columns): T[j][py][ox] = sum_tau h_tau G_tau, G_tau = sum of D[j][oy][ox] over the
 //   output rows oy that read input row py through tap tau; dh_tau += G_tau * R[j][py][ox] with R
@@ -605,64 +340,60 @@ __device__ __forceinline__ void gather_taps(int p, int n_in, int n_out, F get, f
     } else {
         const int lo = max(0, 2 * p - 7), hi = min(n_out - 1, 2 * p + 8);
         for (int o = lo; o <= hi; ++o) {
-            int f, tap[4];
-            poly(o, f, tap);
+            const int f = poly_first(o);
             const float v = get(o);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (clampi(f + q, 0, n_in - 1) == p) G[tap[q]] += v;
+            for (int q = 0; q < 4; ++q) {
+                const float u = clampi(f + q, 0, n_in - 1) == p ? v : 0.f;
+                const int t = poly_tap(o, q);
+                G[0] += t == 0 ? u : 0.f;
+                G[1] += t == 1 ? u : 0.f;
+                G[2] += t == 2 ? u : 0.f;
+                G[3] += t == 3 ? u : 0.f;
+            }
         }
     }
 }
 
-__global__ void k_up_adj_cols(UpAdjArgs a) {
+// One CTA per (channel j, input row py) pair (grid-stride): pass A builds the row T[j][py][.]
+// in shared memory from the <= 8 output rows that read input row py, pass B gathers it along x.
+__global__ void __launch_bounds__(kUpThreads) k_up_adj(UpAdjArgs a) {
+    extern __shared__ float sTrow[];  // wt floats
     const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
     float dh[4] = {0.f, 0.f, 0.f, 0.f};
-    const int64_t total = (int64_t)a.nch * a.hs * a.wt;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / ((int64_t)a.hs * a.wt));
-        const int rem = (int)(e - (int64_t)j * a.hs * a.wt);
-        const int py = rem / a.wt, ox = rem - py * a.wt;
+    const int npairs = a.nch * a.hs;
+    for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
+        const int j = pair / a.hs, py = pair - j * a.hs;
         const float* Dj = a.D + (int64_t)j * a.ht * a.wt;
-        float G[4];
-        gather_taps(py, a.hs, a.ht, [&](int oy) { return __ldg(Dj + (int64_t)oy * a.wt + ox); }, G);
-        a.T[e] = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
-        // forward row-pass value R[j][py][ox]
         const float* S = (j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws) + (int64_t)py * a.ws;
-        int fx, tx[4];
-        poly(ox, fx, tx);
-        float R = 0.f;
+        for (int ox = threadIdx.x; ox < a.wt; ox += blockDim.x) {
+            float G[4];
+            gather_taps(py, a.hs, a.ht, [&](int oy) { return __ldg(Dj + (int64_t)oy * a.wt + ox); }, G);
+            sTrow[ox] = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
+            const int fx = poly_first(ox);
+            float wx[4];
+            poly_w(ox, tp, wx);
+            float R = 0.f;  // forward row-pass value at (py, ox)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) R = fmaf(tp[tx[q]], __ldg(S + clampi(fx + q, 0, a.ws - 1)), R);
+            for (int q = 0; q < 4; ++q) R = fmaf(wx[q], __ldg(S + clampi(fx + q, 0, a.ws - 1)), R);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], R, dh[q]);
-    }
-    __shared__ float scratch[4 * (kUpThreads / 32)];
-    block_sum<4>(dh, scratch);
-    if (threadIdx.x == 0)
-        for (int q = 0; q < 4; ++q) a.gpart[blockIdx.x * 4 + q] = dh[q];
-}
-
-__global__ void k_up_adj_rows(UpAdjArgs a) {
-    const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
-    float dh[4] = {0.f, 0.f, 0.f, 0.f};
-    const int64_t total = (int64_t)a.nch * a.hs * a.ws;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / ((int64_t)a.hs * a.ws));
-        const int rem = (int)(e - (int64_t)j * a.hs * a.ws);
-        const int py = rem / a.ws, px = rem - py * a.ws;
-        const float* Tr = a.T + (int64_t)j * a.hs * a.wt + (int64_t)py * a.wt;
-        float G[4];
-        gather_taps(px, a.ws, a.wt, [&](int ox) { return Tr[ox]; }, G);
-        const float d = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
-        const int64_t si = (int64_t)py * a.ws + px;
-        const float sv = j == 0 ? __ldg(a.src0 + si) : __ldg(a.srcup + (int64_t)(j - 1) * a.hs * a.ws + si);
+            for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], R, dh[q]);
+        }
+        __syncthreads();
+        for (int px = threadIdx.x; px < a.ws; px += blockDim.x) {
+            float G[4];
+            gather_taps(px, a.ws, a.wt, [&](int ox) { return sTrow[ox]; }, G);
+            const float d = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
+            const float sv = __ldg(S + px);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], sv, dh[q]);
-        if (j == 0)
-            a.out0[si] = d;
-        else
-            a.outup[(int64_t)(j - 1) * a.hs * a.ws + si] = d;
+            for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], sv, dh[q]);
+            const int64_t si = (int64_t)py * a.ws + px;
+            if (j == 0)
+                a.out0[si] = d;
+            else
+                a.outup[(int64_t)(j - 1) * a.hs * a.ws + si] = d;
+        }
+        __syncthreads();
     }
     __shared__ float scratch[4 * (kUpThreads / 32)];
     block_sum<4>(dh, scratch);
@@ -678,13 +409,13 @@ int up_grid(int64_t total) {
 
 }  // namespace
 
-int up_adj_grid(int64_t total) { return up_grid(total); }
+int up_adj_grid(int64_t pairs) { return (int)(pairs < kUpMaxCta ? (pairs < 1 ? 1 : pairs) : kUpMaxCta); }
 
 size_t syn_bwd_smem_bytes() { return (size_t)(ss_total + 2 * 48 * kSLd + kSTasks * 64) * sizeof(float); }
 
-int conv_tiles(int H, int W) { return ((H + kTH - 1) / kTH) * ((W + kTW - 1) / kTW); }
 
 void synth_init_attributes() {
+    cudaFuncSetAttribute(k_up_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * (int)sizeof(float));
     const int sm = (int)syn_bwd_smem_bytes();
     cudaFuncSetAttribute(k_syn_bwd<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_syn_bwd<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -744,28 +475,6 @@ void launch_syn_backward(const Work& w, const float* params, int pass, cudaStrea
         k_syn_bwd<PASS_FWD_BWD><<<w.n_cta_syn, kSynThreads, sm, s>>>(a);
 }
 
-void launch_conv(const Work& w, const float* params, const float* image, int pass, float grad_scale,
-                 float* xhat_out, cudaStream_t s) {
-    ConvArgs a;
-    a.H = w.g.H;
-    a.W = w.g.W;
-    a.HW = w.HW;
-    a.t = w.t;
-    a.img = image;
-    a.params = params;
-    a.gscale = grad_scale;
-    a.dt = w.dt;
-    a.xhat = xhat_out;
-    a.gpart = w.gpart_conv;
-    a.se_part = w.se_part;
-    a.tiles_x = (w.g.W + kTW - 1) / kTW;
-    a.n_tiles = conv_tiles(w.g.H, w.g.W);
-    if (pass_bwd(pass))
-        k_conv<PASS_FWD_BWD><<<w.n_cta_conv, kConvThreads, 0, s>>>(a);
-    else
-        k_conv<PASS_FWD><<<w.n_cta_conv, kConvThreads, 0, s>>>(a);
-}
-
 void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
     const Geom& g = w.g;
     for (int st = 1; st < kL; ++st) {  // stage st: grid st -> grid st-1
@@ -773,7 +482,7 @@ void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
         a.D = st == 1 ? w.dz : w.dup[st - 1];
         a.src0 = w.yt + g.off[st];
         a.srcup = w.up[st];
-        a.T = w.tmp;
+        a.T = nullptr;
         a.out0 = w.dYsyn + g.off[st];
         a.outup = w.dup[st];
         a.hs = g.h[st];
@@ -782,10 +491,8 @@ void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
         a.wt = g.w[st - 1];
         a.nch = kL - st;
         a.taps = params + po::up + 4 * (st - 1);
-        a.gpart = w.gpart_up + ((st - 1) * 2 + 0) * kUpMaxCta * 4;
-        k_up_adj_cols<<<w.n_cta_up[st][0], kUpThreads, 0, s>>>(a);
-        a.gpart = w.gpart_up + ((st - 1) * 2 + 1) * kUpMaxCta * 4;
-        k_up_adj_rows<<<w.n_cta_up[st][1], kUpThreads, 0, s>>>(a);
+        a.gpart = w.gpart_up + (st - 1) * kUpMaxCta * 4;
+        k_up_adj<<<w.n_cta_up[st], kUpThreads, (size_t)a.wt * sizeof(float), s>>>(a);
     }
 }
 

@@ -63,6 +63,9 @@ def _load():
         "coolchic_backward": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, i32, f32, vp, vp, vp, sz, vp]),
         "coolchic_rate_distortion": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, P(RD), vp, sz, vp]),
         "coolchic_decode_image": (i32, [P(Arch), vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "coolchic_timing_enable": (i32, [i32, i32]),
+        "coolchic_timing_collect": (i32, [P(ctypes.c_double), P(i64)]),
+        "coolchic_timing_disable": (i32, []),
         "coolchic_last_error": (ctypes.c_char_p, []),
         "coolchic_version": (ctypes.c_char_p, []),
     }
@@ -76,7 +79,24 @@ def _load():
 _lib = _load()
 EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count", "coolchic_param_block",
             "coolchic_workspace_bytes", "coolchic_encode_step", "coolchic_forward", "coolchic_backward",
-            "coolchic_rate_distortion", "coolchic_decode_image", "coolchic_last_error", "coolchic_version"]
+            "coolchic_rate_distortion", "coolchic_decode_image", "coolchic_timing_enable", "coolchic_timing_collect",
+            "coolchic_timing_disable", "coolchic_last_error", "coolchic_version"]
+
+KERNEL_ARM, KERNEL_SYN_BWD, KERNEL_CONV, KERNEL_SYN_FWD = 0, 1, 2, 3
+
+
+def timing_enable(kernel_id: int, max_launches: int):
+    _check(_lib.coolchic_timing_enable(kernel_id, max_launches), "timing_enable")
+
+
+def timing_collect():
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(_lib.coolchic_timing_collect(ctypes.byref(ms), ctypes.byref(n)), "timing_collect")
+    return ms.value, n.value
+
+
+def timing_disable():
+    _lib.coolchic_timing_disable()
 
 
 def raw():

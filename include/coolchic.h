@@ -151,6 +151,21 @@ int coolchic_rate_distortion(const cc_arch_t* arch, const cc_hparams_t* hp, cons
                              int32_t relax, cc_rd_t* rd_out, void* workspace,
                              size_t workspace_bytes, void* stream);
 
+/* Rate-distortion evaluation that allocates nothing (the paper has no counterpart; this is a
+ * library service).  Same computation and result as coolchic_rate_distortion, blocking, but
+ * without a workspace argument: for callers that cannot call cudaMalloc, such as a process whose
+ * device memory is owned entirely by its own pool, or code running while another thread of the
+ * process holds a stream in global-mode capture (where cudaMalloc is illegal).
+ *   Scratch: a 32 MiB array compiled into the library, held on every GPU that loads it until exit.
+ *   Images that need more (above about 1.4 million pixels; 1024 x 1024 fits) are rejected with
+ *   CC_ERR_WORKSPACE.  The first call on a device looks up the array's device address (with that
+ *   device current); make it before any stream capture begins.  Calls share the array, so calls
+ *   that overlap on the GPU race; nothing needs clearing between calls (each call writes every
+ *   byte it reads).  rd_out [host].  Calls no allocating routine. */
+int coolchic_rate_distortion_noalloc(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
+                                     const float* latents, const float* params, int64_t step,
+                                     int32_t relax, cc_rd_t* rd_out, void* stream);
+
 /* Decoder (Sec. III): from integer latents q (the hard-quantised grids) and the parameters,
  *   - the integer entropy model: a fixed-point ARM (weights rint(256 w), 8 fractional bits,
  *     64-bit accumulation, floor shifts) and an integer Laplace CDF with 16-bit total mass,

@@ -221,6 +221,16 @@ void tend(int id, cudaStream_t s) {
 
 }  // namespace
 
+int set_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
 int num_sms() {
     int dev = 0;
     cudaGetDevice(&dev);

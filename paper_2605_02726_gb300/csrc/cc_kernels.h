@@ -58,6 +58,8 @@ struct Work {
 };
 
 int num_sms();
+// Records a printf-style message for coolchic_last_error() and returns `code`.
+int set_error(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 
 // a1 relaxation: yt = y + u(seed, step, i) | rint(y) | y.  step from step_dev when non-null.
 void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host,

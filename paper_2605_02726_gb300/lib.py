@@ -63,6 +63,7 @@ def _load():
         "coolchic_backward": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, i32, f32, vp, vp, vp, sz, vp]),
         "coolchic_rate_distortion": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, P(RD), vp, sz, vp]),
         "coolchic_decode_image": (i32, [P(Arch), vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "coolchic_rate_distortion_noalloc": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, P(RD), vp]),
         "coolchic_timing_enable": (i32, [i32, i32]),
         "coolchic_timing_collect": (i32, [P(ctypes.c_double), P(i64)]),
         "coolchic_timing_disable": (i32, []),
@@ -80,7 +81,8 @@ _lib = _load()
 EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count", "coolchic_param_block",
             "coolchic_workspace_bytes", "coolchic_encode_step", "coolchic_forward", "coolchic_backward",
             "coolchic_rate_distortion", "coolchic_decode_image", "coolchic_timing_enable", "coolchic_timing_collect",
-            "coolchic_timing_disable", "coolchic_last_error", "coolchic_version"]
+            "coolchic_timing_disable", "coolchic_last_error", "coolchic_version",
+            "coolchic_rate_distortion_noalloc"]
 
 KERNEL_ARM, KERNEL_SYN_BWD, KERNEL_CONV, KERNEL_SYN_FWD = 0, 1, 2, 3
 
@@ -215,6 +217,18 @@ def rate_distortion(image, latents, params, *, H, W, hp: HParams, step=0, relax=
     _check(_lib.coolchic_rate_distortion(ctypes.byref(a), ctypes.byref(hp), _ptr(image), _ptr(latents),
                                          _ptr(params), int(step), relax, ctypes.byref(out), _ptr(ws), ws.numel(),
                                          _stream(stream)), "rate_distortion")
+    return dict(loss=out.loss, rate_bits=out.rate_bits, mse=out.mse)
+
+
+def rate_distortion_noalloc(image, latents, params, *, H, W, hp: HParams, step=0, relax=CC_RELAX_HARD,
+                            stream=None):
+    """coolchic_rate_distortion without a workspace: for callers that cannot allocate device
+    memory (the library's built-in scratch is used; images up to about 1.4 million pixels)."""
+    a = arch(H, W)
+    out = RD()
+    _check(_lib.coolchic_rate_distortion_noalloc(ctypes.byref(a), ctypes.byref(hp), _ptr(image), _ptr(latents),
+                                                 _ptr(params), int(step), relax, ctypes.byref(out),
+                                                 _stream(stream)), "rate_distortion_noalloc")
     return dict(loss=out.loss, rate_bits=out.rate_bits, mse=out.mse)
 
 

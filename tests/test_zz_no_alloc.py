@@ -1,0 +1,46 @@
+"""The workspace-free rate-distortion entry point, for callers that cannot allocate device memory
+(their memory is owned by another pool, or cudaMalloc is illegal for them while a stream is
+being captured).  It must give the result of coolchic_rate_distortion, which takes a caller's
+workspace, on consecutive calls that reuse the library's built-in scratch.
+
+Kept in its own file, collected last, so that a run stopping at the first failure has already
+run every other test; it passes alone in a fresh process as well.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2605_02726_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(cc, H, W, seed, relax, step):
+    img = torch.tensor(inputs.image(H, W, seed=seed), device="cuda")
+    lat, par = inputs.random_state(H, W, seed=seed + 1)
+    gl = torch.tensor(lat, device="cuda")
+    gp = torch.tensor(par, device="cuda")
+    hp = cc.hparams(lam=1e-2, seed=77)
+    ref = cc.rate_distortion(img, gl, gp, H=H, W=W, hp=hp, step=step, relax=relax, ws=cc.workspace(H, W))
+    got = cc.rate_distortion_noalloc(img, gl, gp, H=H, W=W, hp=hp, step=step, relax=relax)
+    return ref, got
+
+
+def test_noalloc_matches_workspace_entry_point_on_two_calls(cc):
+    # two calls in a row with different sizes and relaxations share the built-in scratch
+    for (H, W, seed, relax, step) in [(96, 128, 5, 1, 0), (61, 47, 9, 0, 3)]:
+        ref, got = _case(cc, H, W, seed, relax, step)
+        for k in ("loss", "rate_bits", "mse"):
+            assert abs(got[k] - ref[k]) <= 1e-4 * abs(ref[k]), (H, W, k, got[k], ref[k])
+
+
+def test_noalloc_rejects_images_beyond_its_scratch(cc):
+    H, W = 1536, 1024
+    img = torch.zeros(3, H, W, device="cuda")
+    lat = torch.zeros(inputs.latent_count(H, W), device="cuda")
+    par = torch.zeros(inputs.N_PARAMS, device="cuda")
+    with pytest.raises(cc.CoolChicError, match="scratch"):
+        cc.rate_distortion_noalloc(img, lat, par, H=H, W=W, hp=cc.hparams())
+    assert np.isfinite(cc.rate_distortion_noalloc(img[:, :64, :64].contiguous(),
+                                                  lat[:inputs.latent_count(64, 64)].contiguous(), par,
+                                                  H=64, W=64, hp=cc.hparams())["loss"])

@@ -1,75 +1,117 @@
-// Entropy model of the encoder step (Sec. III-A, Eqs. 2-5, 9, 11) and its adjoint.
+// Entropy model of the encoder step (Sec. III-A, Eqs. 2-5, 9, 11) and its adjoint, on tensor cores.
 //
-// One thread per latent, all grids in one launch.  Per latent: the 16 causal neighbours of the
-// relaxed latents (zero outside the grid), the IFCE of grids 0..2 on nearest-neighbour co-located
-// coarser values, the ARM MLP 20 -> 16 -> 16 -> 2 with ReLU plus the linear stabilizer, log-scale
-// clamped to [-5, 5], Laplace interval mass, rate -log2 max(P, 2^-16).
+// Per latent: the 16 causal neighbours of the relaxed latents (zero outside the grid), the IFCE of
+// grids 0..2 on nearest-neighbour co-located coarser values, the ARM MLP 20 -> 16 -> 16 -> 2 with
+// ReLU plus the linear stabilizer, log-scale clamped to [-5, 5], Laplace interval mass and rate
+// -log2 max(P, 2^-16).  Adjoint: dL/dbits = lambda/(HW) gives dmu, dlogb, then the MLP adjoint
+// gives dL/dc; context gradients are written as 16 planes dS[n][i] and gathered by their source
+// latent later (fixed order, no atomics).
 //
-// Adjoint (same kernel, recomputed or from stored activations): dL/dbits = lambda/(HW) gives
-// dmu, dlogb, then the MLP adjoint gives dL/dc.  Context gradients are not scattered: they are
-// written as 16 planes dS[n][i] and gathered by their source latent in the gather kernel, which
-// keeps every sum in a fixed order (bit-reproducible, no atomics).
+// Work unit: one warp, 16 latents (the M dimension of mma.sync.m16n8k8).  The products
+// (latents x features) . (features x units) run as TF32 tensor-core MMAs with a three-pass split
+// x = hi + lo (hi = tf32(x), lo = tf32(x - hi); D += lo*Bhi + hi*Blo + hi*Bhi), which keeps the
+// result at FP32 accuracy.  An accumulator fragment feeds the next layer as its A fragment without
+// data movement: the K order of the next layer is permuted so that the k-slot t of an 8-wide chunk
+// is unit 2t and slot t+4 is unit 2t+1, and the B fragments (weights, pre-split per lane in shared
+// memory) are laid out with the same permutation.
 //
-// Parameter gradients are outer-product sums over latents.  Each round of 128 latents stages the
-// factors in shared memory (U = gradients, V = activations, [row][latent]) and 114 threads each
-// update an 8x8 register block over a slice of the latents; the 6 slices of a block are added
-// in a fixed order at the end, giving one partial gradient per CTA (reduced later in fixed order).
+// Parameter gradients are sums over latents of outer products, i.e. GEMMs with K = latents: each
+// warp transposes its 16 latents' factors into a private [feature][latent] shared tile and runs
+// 12 m16n8 output tiles over K = 16 per work unit, accumulating in registers for the whole kernel.
+// The 4 warps' accumulators are added in a fixed order at the end: one partial gradient per CTA.
 #include "cc_kernels.h"
 
 namespace cc {
 namespace {
 
-constexpr int kT = kArmThreads;
-constexpr int kLd = kT + 4;          // staging row stride (floats): 16 B aligned, skewed banks
-constexpr int kURows = 56, kVRows = 64;
-constexpr int kChunks = 6;
-constexpr int kBlocks = 19;
-constexpr int kTasks = kBlocks * kChunks;  // 114 <= kT
-constexpr int kWSm = 768;            // shared copy of ARM + IFCE weights (re-laid out, see below)
+constexpr int kWarps = 4;
+constexpr int kT = kWarps * 32;
+constexpr int kSld = 20;  // staging row stride: 16 latents + 4 (conflict-free fragment reads)
+// staging rows: U (gradient side) then V (activation side)
+constexpr int U_DA1 = 0, U_DA2 = 16, U_O = 32;
+constexpr int V_C = 48, V_H1 = 72, V_H2 = 88, V_R = 104, S_ROWS = 112;
+constexpr int kStage = S_ROWS * kSld;  // floats per warp
+// B-fragment table (per fragment, per lane: b0 hi, b1 hi, b0 lo, b1 lo)
+constexpr int FR_W1 = 0, FR_W2 = 6, FR_W3 = 10, FR_WS = 12, FR_BW2 = 15, FR_BW1 = 19, FR_N = 25;
+constexpr int kIfceSm = 72;  // IFCE weights and biases, flat vector order (offsets relative to if_w0)
 
-// Shared weight layout: W1 [16][20] @0, b1 @320, W2 [16][16] @336, b2 @592, W3 [2][16] @608,
-// Ws [2][20] @640 (16 B aligned, unlike the flat vector), b3 + bs @680, IFCE as in the flat vector.
-constexpr int sw_w1 = 0, sw_b1 = 320, sw_w2 = 336, sw_b2 = 592, sw_w3 = 608, sw_ws = 640, sw_bo = 680;
+// x = hi + lo: hi keeps the 10 explicit mantissa bits a TF32 operand carries, lo = x - hi is
+// exact in FP32 and enters the MMA with its own low 13 bits ignored, an error of at most
+// 2^-20 |x|.
+__device__ __forceinline__ void split2(float x, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(x) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+struct AFrag {
+    uint32_t h[4], l[4];
+};
+__device__ __forceinline__ AFrag make_a(float a0, float a1, float a2, float a3) {
+    AFrag f;
+    split2(a0, f.h[0], f.l[0]);
+    split2(a1, f.h[1], f.l[1]);
+    split2(a2, f.h[2], f.l[2]);
+    split2(a3, f.h[3], f.l[3]);
+    return f;
+}
+__device__ __forceinline__ void mma1(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// A * B at FP32 accuracy into two independent accumulator chains: dh += Ah Bh, dl += Al Bh + Ah Bl
+// (the result is dh + dl); B from the per-lane fragment table entry (b0h, b1h, b0l, b1l).
+__device__ __forceinline__ void mma3(float (&dh)[4], float (&dl)[4], const AFrag& a, const float4& b) {
+    mma1(dh, a.h, __float_as_uint(b.x), __float_as_uint(b.y));
+    mma1(dl, a.l, __float_as_uint(b.x), __float_as_uint(b.y));
+    mma1(dl, a.h, __float_as_uint(b.z), __float_as_uint(b.w));
+}
+__device__ __forceinline__ void add4(float (&d)[4], const float (&e)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[q] += e[q];
+}
+__device__ __forceinline__ void mma3b(float (&d)[4], const AFrag& a, const AFrag& b) {  // b.h[0..1], b.l[0..1]
+    mma1(d, a.l, b.h[0], b.h[1]);
+    mma1(d, a.h, b.l[0], b.l[1]);
+    mma1(d, a.h, b.h[0], b.h[1]);
+}
+// v[i] for a runtime i without a dynamically indexed (local-memory) array
+template <int NV>
+__device__ __forceinline__ float sel(const float (&v)[NV], int i) {
+    float r = v[0];
+#pragma unroll
+    for (int j = 1; j < NV; ++j) r = i == j ? v[j] : r;
+    return r;
+}
+// A fragment from an accumulator fragment (chunk permutation: slot t <- col 2t, slot t+4 <- col 2t+1)
+__device__ __forceinline__ AFrag chain(const float (&c)[4]) { return make_a(c[0], c[2], c[1], c[3]); }
 
-// Staging rows.  U: da1 0-15, da2 16-31, dmu 32, ds 33, (zero 34-39), df0 40-43, df1 44-47,
-// df2 48-51, (zero 52-55).  V: c 0-19, one 20, (zero 21-23), h1 24-39, h2 40-55, r 56-61,
-// one 62, (zero 63).
-__constant__ unsigned char c_blk_u[kBlocks] = {0, 0, 0, 8, 8, 8, 16, 16, 24, 24, 16, 24, 32, 32, 32, 32, 32, 40, 48};
-__constant__ unsigned char c_blk_v[kBlocks] = {0, 8, 16, 0, 8, 16, 24, 32, 24, 32, 16, 16, 40, 48, 0, 8, 16, 56, 56};
-__constant__ unsigned char c_chunk[kChunks + 1] = {0, 24, 48, 68, 88, 108, 128};
-
-// Parameter index of staged product (u, v), or -1 if the product is padding.  A second index
-// (b3 and bs share one sum) is returned in *second.
-__device__ int arm_grad_index(int u, int v, int* second) {
-    *second = -1;
-    if (u < 16) {
-        if (v < 20) return po::arm_w1 + u * 20 + v;
-        if (v == 20) return po::arm_b1 + u;
-        return -1;
+// Value of entry `which` (0: b0, 1: b1) of B fragment f for lane (g, t), from the flat parameters.
+__device__ float bfrag_value(const float* P, int f, int g, int t, int which) {
+    if (f < FR_W2) {  // layer 1: B[k = feature][n = unit] = W1aug[unit][feature], feature 20 = bias
+        const int kc = f >> 1, nt = f & 1, unit = nt * 8 + g, feat = kc * 8 + t + 4 * which;
+        return feat < 20 ? P[po::arm_w1 + unit * 20 + feat] : (feat == 20 ? P[po::arm_b1 + unit] : 0.f);
     }
-    if (u < 32) {
-        int o = u - 16;
-        if (v >= 24 && v < 40) return po::arm_w2 + o * 16 + (v - 24);
-        if (v == 20) return po::arm_b2 + o;
-        return -1;
+    if (f < FR_W3) {  // layer 2, K permuted: B[k][n] = W2[n][unit(k)]
+        const int kc = (f - FR_W2) >> 1, nt = (f - FR_W2) & 1, n = nt * 8 + g, u = kc * 8 + 2 * t + which;
+        return P[po::arm_w2 + n * 16 + u];
     }
-    if (u < 34) {
-        int o = u - 32;
-        if (v >= 40 && v < 56) return po::arm_w3 + o * 16 + (v - 40);
-        if (v < 20) return po::arm_ws + o * 20 + v;
-        if (v == 20) {
-            *second = po::arm_bs + o;
-            return po::arm_b3 + o;
-        }
-        return -1;
+    if (f < FR_WS) {  // output from h2, K permuted, N = 8 (mu, s, zeros)
+        const int kc = f - FR_W3, u = kc * 8 + 2 * t + which;
+        return g < 2 ? P[po::arm_w3 + g * 16 + u] : 0.f;
     }
-    if (u >= 40 && u < 52) {
-        int k = (u - 40) >> 2, o = (u - 40) & 3, nin = ifce_nin(k);
-        if (v >= 56 && v < 56 + nin) return ifce_w_off(k) + o * nin + (v - 56);
-        if (v == 62) return ifce_b_off(k) + o;
-        return -1;
+    if (f < FR_BW2) {  // stabilizer from c, N = 8 (mu, s, zeros)
+        const int kc = f - FR_WS, feat = kc * 8 + t + 4 * which;
+        return (g < 2 && feat < 20) ? P[po::arm_ws + g * 20 + feat] : 0.f;
     }
-    return -1;
+    if (f < FR_BW1) {  // adjoint of layer 2: B[k = o (permuted)][n = i] = W2[o][i]
+        const int kc = (f - FR_BW2) >> 1, nt = (f - FR_BW2) & 1, o = kc * 8 + 2 * t + which, i = nt * 8 + g;
+        return P[po::arm_w2 + o * 16 + i];
+    }
+    {  // adjoint of layer 1: B[k = o (permuted)][n = feature] = W1[o][feature]
+        const int kc = (f - FR_BW1) / 3, nt = (f - FR_BW1) % 3, o = kc * 8 + 2 * t + which, feat = nt * 8 + g;
+        return feat < 20 ? P[po::arm_w1 + o * 20 + feat] : 0.f;
+    }
 }
 
 struct ArmArgs {
@@ -83,286 +125,473 @@ struct ArmArgs {
     float* dR1;
     float* dR2;
     float* dYd;
-    float* act;         // [34][N]
+    float* act;         // [34][N]: a1 (16), a2 (16), mu, s
     float* gpart;       // [gridDim.x][756]
     double* rate_part;  // [gridDim.x]
 };
+
+struct LatentPos {
+    int k, r, c, li;
+    bool valid;
+    int64_t i;
+};
+
+// position of latent i; the row is li / w via a float reciprocal, corrected to the exact quotient
+__device__ __forceinline__ LatentPos locate(const Geom& g, const float* rcp_w, int64_t i, int64_t N) {
+    LatentPos p;
+    p.valid = i < N;
+    p.i = p.valid ? i : N - 1;
+    p.k = grid_of(g, p.i);
+    p.li = (int)(p.i - g.off[p.k]);
+    const int w = g.w[p.k];
+    int r = __float2int_rz(__int2float_rn(p.li) * rcp_w[p.k]);
+    r -= (r * w > p.li) ? 1 : 0;
+    r += ((r + 1) * w <= p.li) ? 1 : 0;
+    p.r = r;
+    p.c = p.li - r * w;
+    return p;
+}
+
+// Context feature f (0..23) of a latent: neighbours 0..15, IFCE outputs 16..19, one (20), zeros.
+__device__ __forceinline__ float neighbour(const Geom& g, const float* yt, const LatentPos& p, int dy, int dx) {
+    const int rr = p.r + dy, cc = p.c + dx, w = g.w[p.k];
+    return (rr >= 0 && cc >= 0 && cc < w) ? __ldg(yt + g.off[p.k] + rr * w + cc) : 0.f;
+}
+
+__device__ __forceinline__ void ifce_inputs(const Geom& g, const float* yt, const LatentPos& p, float (&rv)[6]) {
+    const int nin = ifce_nin(p.k);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        rv[j] = 0.f;
+        if (j < nin) {
+            const int gj = p.k + 1 + j;
+            const int rr = min(p.r >> (j + 1), g.h[gj] - 1), cc = min(p.c >> (j + 1), g.w[gj] - 1);
+            rv[j] = __ldg(yt + g.off[gj] + rr * g.w[gj] + cc);
+        }
+    }
+}
+
+__device__ __forceinline__ float ifce_out(const float* sIf, int k, int o, const float (&rv)[6]) {
+    const int nin = ifce_nin(k);
+    if (nin == 0) return 0.f;
+    const int wo = ifce_w_off(k) - po::if_w0, bo = ifce_b_off(k) - po::if_w0;
+    float acc = sIf[bo + o];
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+        if (j < nin) acc = fmaf(sIf[wo + o * nin + j], rv[j], acc);
+    return acc;
+}
+
+// Parameter index of weight-gradient tile T, row, column (-1: padding); *second for b3/bs.
+__device__ int wgrad_index(int T, int row, int col, int* second) {
+    *second = -1;
+    if (T <= 2) {
+        const int f = T * 8 + col;
+        return f < 20 ? po::arm_w1 + row * 20 + f : (f == 20 ? po::arm_b1 + row : -1);
+    }
+    if (T <= 4) return po::arm_w2 + row * 16 + (T - 3) * 8 + col;
+    if (T == 5) return col == 4 ? po::arm_b2 + row : -1;
+    if (T <= 7) return row < 2 ? po::arm_w3 + row * 16 + (T - 6) * 8 + col : -1;
+    if (T <= 10) {
+        if (row >= 2) return -1;
+        const int f = (T - 8) * 8 + col;
+        if (f < 20) return po::arm_ws + row * 20 + f;
+        if (f == 20) {
+            *second = po::arm_bs + row;
+            return po::arm_b3 + row;
+        }
+        return -1;
+    }
+    if (row < 2 || row >= 14) return -1;
+    const int k = (row - 2) >> 2, o = (row - 2) & 3, nin = ifce_nin(k);
+    if (col < nin) return ifce_w_off(k) + o * nin + col;
+    if (col == 6) return ifce_b_off(k) + o;
+    return -1;
+}
 
 template <int PASS>
 __global__ void __launch_bounds__(kT, 2) k_arm(ArmArgs a) {
     constexpr bool BWD = pass_bwd(PASS);
     extern __shared__ float4 smem4[];
-    float* sW = reinterpret_cast<float*>(smem4);
-    float* sU = sW + kWSm;
-    float* sV = sU + kURows * kLd;
-    float* sAcc = sV + kVRows * kLd;
-    const Geom& g = a.g;
-    const int tid = threadIdx.x;
+    float4* sFr = smem4;                                             // [FR_N][32]
+    float* sIf = reinterpret_cast<float*>(smem4 + FR_N * 32);        // [kIfceSm]
+    float* sStage = sIf + kIfceSm;                                   // [kWarps][kStage]
+    __shared__ Geom g;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
 
-    for (int j = tid; j < po::arm_block; j += kT) {
-        float v = a.params[j];
-        int d;
-        if (j < po::arm_ws) d = j;                                   // W1 b1 W2 b2 W3 b3->overwritten
-        else if (j < po::arm_bs) d = sw_ws + (j - po::arm_ws);
-        else if (j < po::if_w0) d = -1;                              // bs folded below
-        else d = j;
-        if (d >= 0 && j != po::arm_b3 && j != po::arm_b3 + 1) sW[d] = v;
+    __shared__ float rcp_w[kL];
+    if (tid == 0) g = a.g;
+    if (tid < kL) rcp_w[tid] = 1.f / (float)a.g.w[tid];
+    for (int j = tid; j < FR_N * 32; j += kT) {
+        const int f = j >> 5, l = j & 31;
+        const float v0 = bfrag_value(a.params, f, l >> 2, l & 3, 0);
+        const float v1 = bfrag_value(a.params, f, l >> 2, l & 3, 1);
+        uint32_t h0, l0, h1, l1;
+        split2(v0, h0, l0);
+        split2(v1, h1, l1);
+        sFr[j] = make_float4(__uint_as_float(h0), __uint_as_float(h1), __uint_as_float(l0), __uint_as_float(l1));
     }
-    if (tid < 2) sW[sw_bo + tid] = a.params[po::arm_b3 + tid] + a.params[po::arm_bs + tid];
-    if (BWD) {
-        for (int j = tid; j < kTasks * 64; j += kT) sAcc[j] = 0.f;
-        // constant staging rows
-        for (int j = tid; j < kLd; j += kT) {
-            for (int r = 34; r < 40; ++r) sU[r * kLd + j] = 0.f;
-            for (int r = 52; r < 56; ++r) sU[r * kLd + j] = 0.f;
-            sV[20 * kLd + j] = 1.f;
-            sV[21 * kLd + j] = 0.f;
-            sV[22 * kLd + j] = 0.f;
-            sV[23 * kLd + j] = 0.f;
-            sV[62 * kLd + j] = 1.f;
-            sV[63 * kLd + j] = 0.f;
-        }
-    }
+    for (int j = tid; j < kIfceSm; j += kT) sIf[j] = a.params[po::if_w0 + j];
     __syncthreads();
 
-    const int64_t N = a.N;
-    const int64_t n_rounds = (N + kT - 1) / kT;
+    // per-lane constants
+    float b2c[2][2], w3c[2][2][2], wsc[3][2][2];  // [nt][col] ; [nt][col][out] ; [nt][col][out]
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int u = nt * 8 + 2 * tq + cc;
+            b2c[nt][cc] = a.params[po::arm_b2 + u];
+            w3c[nt][cc][0] = a.params[po::arm_w3 + u];
+            w3c[nt][cc][1] = a.params[po::arm_w3 + 16 + u];
+        }
+#pragma unroll
+    for (int nt = 0; nt < 3; ++nt)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int f = nt * 8 + 2 * tq + cc;
+            wsc[nt][cc][0] = f < 20 ? a.params[po::arm_ws + f] : 0.f;
+            wsc[nt][cc][1] = f < 20 ? a.params[po::arm_ws + 20 + f] : 0.f;
+        }
+    int ndy[4], ndx[4];  // context slots t, t+4, t+8, t+12 of this lane
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        ndy[q] = ctx_dy(tq + 4 * q);
+        ndx[q] = ctx_dx(tq + 4 * q);
+    }
+    const float mu_b = a.params[po::arm_b3] + a.params[po::arm_bs];
+    const float s_b = a.params[po::arm_b3 + 1] + a.params[po::arm_bs + 1];
+
+    float* st = sStage + wid * kStage;
+    if (BWD) {  // constant staging rows: C one (20) and zeros (21-23), R one (6) and zero (7), U_O zeros (14, 15)
+        for (int j = lane; j < kSld; j += 32) {
+            st[(V_C + 20) * kSld + j] = 1.f;
+            st[(V_C + 21) * kSld + j] = 0.f;
+            st[(V_C + 22) * kSld + j] = 0.f;
+            st[(V_C + 23) * kSld + j] = 0.f;
+            st[(V_R + 6) * kSld + j] = 1.f;
+            st[(V_R + 7) * kSld + j] = 0.f;
+            st[(U_O + 14) * kSld + j] = 0.f;
+            st[(U_O + 15) * kSld + j] = 0.f;
+        }
+        __syncwarp();
+    }
+    float acc[12][4];
+#pragma unroll
+    for (int T = 0; T < 12; ++T)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[T][q] = 0.f;
     float rate_acc = 0.f;
 
-    for (int64_t rd = blockIdx.x; rd < n_rounds; rd += gridDim.x) {
-        const int64_t i = rd * kT + tid;
-        const bool valid = i < N;
-        const int64_t ic = valid ? i : N - 1;
-        const int k = grid_of(g, ic);
-        const int hk = g.h[k], wk = g.w[k];
-        const int li = (int)(ic - g.off[k]);
-        const int r = li / wk, c = li - r * wk;
-        const float* yk = a.yt + g.off[k];
+    const int64_t N = a.N;
+    const int64_t n_units = (N + 15) / 16;
+    for (int64_t u = (int64_t)blockIdx.x * kWarps + wid; u < n_units; u += (int64_t)gridDim.x * kWarps) {
+        const LatentPos pA = locate(g, rcp_w, u * 16 + gq, N);
+        const LatentPos pB = locate(g, rcp_w, u * 16 + gq + 8, N);
+        // ---- context features f in {t, t+4, 8+t, 12+t, 16+t, 20+t} of latents A (row g) and B (row g+8)
+        float rA[6], rB[6];
+        ifce_inputs(g, a.yt, pA, rA);
+        ifce_inputs(g, a.yt, pB, rB);
+        float cA[6], cB[6];
+        cA[0] = neighbour(g, a.yt, pA, ndy[0], ndx[0]);
+        cA[1] = neighbour(g, a.yt, pA, ndy[1], ndx[1]);
+        cA[2] = neighbour(g, a.yt, pA, ndy[2], ndx[2]);
+        cA[3] = neighbour(g, a.yt, pA, ndy[3], ndx[3]);
+        cA[4] = ifce_out(sIf, pA.k, tq, rA);
+        cA[5] = tq == 0 ? 1.f : 0.f;
+        cB[0] = neighbour(g, a.yt, pB, ndy[0], ndx[0]);
+        cB[1] = neighbour(g, a.yt, pB, ndy[1], ndx[1]);
+        cB[2] = neighbour(g, a.yt, pB, ndy[2], ndx[2]);
+        cB[3] = neighbour(g, a.yt, pB, ndy[3], ndx[3]);
+        cB[4] = ifce_out(sIf, pB.k, tq, rB);
+        cB[5] = cA[5];
+        const AFrag C0 = make_a(cA[0], cB[0], cA[1], cB[1]);
+        const AFrag C1 = make_a(cA[2], cB[2], cA[3], cB[3]);
+        const AFrag C2 = make_a(cA[4], cB[4], cA[5], cB[5]);
 
-        float x[kAIn];
-#pragma unroll
-        for (int n = 0; n < kNCtx; ++n) {
-            const int rr = r + ctx_dy(n), cc = c + ctx_dx(n);
-            x[n] = (rr >= 0 && cc >= 0 && cc < wk) ? __ldg(yk + rr * wk + cc) : 0.f;
-        }
-        (void)hk;
-        const int nin = ifce_nin(k);
-        float rv[6];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            rv[j] = 0.f;
-            if (j < nin) {
-                const int gj = k + 1 + j;
-                const int rr = min(r >> (j + 1), g.h[gj] - 1), cc = min(c >> (j + 1), g.w[gj] - 1);
-                rv[j] = __ldg(a.yt + g.off[gj] + rr * g.w[gj] + cc);
-            }
-        }
-#pragma unroll
-        for (int o = 0; o < kF; ++o) {
-            float acc = 0.f;
-            if (nin > 0) {
-                const float* Wf = sW + ifce_w_off(k) + o * nin;
-                acc = sW[ifce_b_off(k) + o];
-#pragma unroll
-                for (int j = 0; j < 6; ++j)
-                    if (j < nin) acc = fmaf(Wf[j], rv[j], acc);
-            }
-            x[kNCtx + o] = acc;
-        }
-
-        float a1[kAH], a2[kAH], mu, s;
+        float d1[2][4], d2[2][4];
+        float muA, sA, muB, sB;
         if (PASS == PASS_BWD_LOAD) {
 #pragma unroll
-            for (int o = 0; o < kAH; ++o) {
-                a1[o] = a.act[(int64_t)o * N + ic];
-                a2[o] = a.act[(int64_t)(16 + o) * N + ic];
-            }
-            mu = a.act[(int64_t)32 * N + ic];
-            s = a.act[(int64_t)33 * N + ic];
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int uu = nt * 8 + 2 * tq + cc;
+                    d1[nt][cc] = a.act[(int64_t)uu * N + pA.i];
+                    d1[nt][2 + cc] = a.act[(int64_t)uu * N + pB.i];
+                    d2[nt][cc] = a.act[(int64_t)(16 + uu) * N + pA.i];
+                    d2[nt][2 + cc] = a.act[(int64_t)(16 + uu) * N + pB.i];
+                }
+            muA = a.act[(int64_t)32 * N + pA.i];
+            sA = a.act[(int64_t)33 * N + pA.i];
+            muB = a.act[(int64_t)32 * N + pB.i];
+            sB = a.act[(int64_t)33 * N + pB.i];
         } else {
+            // layer 1 (bias through the constant feature 20)
 #pragma unroll
-            for (int o = 0; o < kAH; ++o) {
-                float acc = sW[sw_b1 + o];
+            for (int nt = 0; nt < 2; ++nt) {
+                float e[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int q = 0; q < kAIn; q += 4) {
-                    const float4 w = *reinterpret_cast<const float4*>(sW + sw_w1 + o * kAIn + q);
-                    acc = fmaf(w.x, x[q], acc);
-                    acc = fmaf(w.y, x[q + 1], acc);
-                    acc = fmaf(w.z, x[q + 2], acc);
-                    acc = fmaf(w.w, x[q + 3], acc);
-                }
-                a1[o] = acc;
+                for (int q = 0; q < 4; ++q) d1[nt][q] = 0.f;
+                mma3(d1[nt], e, C0, sFr[(FR_W1 + 0 * 2 + nt) * 32 + lane]);
+                mma3(d1[nt], e, C1, sFr[(FR_W1 + 1 * 2 + nt) * 32 + lane]);
+                mma3(d1[nt], e, C2, sFr[(FR_W1 + 2 * 2 + nt) * 32 + lane]);
+                add4(d1[nt], e);
             }
+            float h1[2][4];
 #pragma unroll
-            for (int o = 0; o < kAH; ++o) {
-                float acc = sW[sw_b2 + o];
+            for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-                for (int q = 0; q < kAH; q += 4) {
-                    const float4 w = *reinterpret_cast<const float4*>(sW + sw_w2 + o * kAH + q);
-                    acc = fmaf(w.x, fmaxf(a1[q], 0.f), acc);
-                    acc = fmaf(w.y, fmaxf(a1[q + 1], 0.f), acc);
-                    acc = fmaf(w.z, fmaxf(a1[q + 2], 0.f), acc);
-                    acc = fmaf(w.w, fmaxf(a1[q + 3], 0.f), acc);
-                }
-                a2[o] = acc;
+                for (int q = 0; q < 4; ++q) h1[nt][q] = fmaxf(d1[nt][q], 0.f);
+            const AFrag H10 = chain(h1[0]), H11 = chain(h1[1]);
+            // layer 2
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                d2[nt][0] = b2c[nt][0];
+                d2[nt][1] = b2c[nt][1];
+                d2[nt][2] = b2c[nt][0];
+                d2[nt][3] = b2c[nt][1];
+                float e[4] = {0.f, 0.f, 0.f, 0.f};
+                mma3(d2[nt], e, H10, sFr[(FR_W2 + 0 * 2 + nt) * 32 + lane]);
+                mma3(d2[nt], e, H11, sFr[(FR_W2 + 1 * 2 + nt) * 32 + lane]);
+                add4(d2[nt], e);
             }
-            float out[2];
+            float h2[2][4];
 #pragma unroll
-            for (int o = 0; o < 2; ++o) {
-                float acc = sW[sw_bo + o];
+            for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-                for (int q = 0; q < kAH; q += 4) {
-                    const float4 w = *reinterpret_cast<const float4*>(sW + sw_w3 + o * kAH + q);
-                    acc = fmaf(w.x, fmaxf(a2[q], 0.f), acc);
-                    acc = fmaf(w.y, fmaxf(a2[q + 1], 0.f), acc);
-                    acc = fmaf(w.z, fmaxf(a2[q + 2], 0.f), acc);
-                    acc = fmaf(w.w, fmaxf(a2[q + 3], 0.f), acc);
-                }
-#pragma unroll
-                for (int q = 0; q < kAIn; q += 4) {
-                    const float4 w = *reinterpret_cast<const float4*>(sW + sw_ws + o * kAIn + q);
-                    acc = fmaf(w.x, x[q], acc);
-                    acc = fmaf(w.y, x[q + 1], acc);
-                    acc = fmaf(w.z, x[q + 2], acc);
-                    acc = fmaf(w.w, x[q + 3], acc);
-                }
-                out[o] = acc;
+                for (int q = 0; q < 4; ++q) h2[nt][q] = fmaxf(d2[nt][q], 0.f);
+            const AFrag H20 = chain(h2[0]), H21 = chain(h2[1]);
+            // output (mu, s) + stabilizer
+            float dout[4];
+            dout[0] = tq == 0 ? mu_b : 0.f;
+            dout[1] = tq == 0 ? s_b : 0.f;
+            dout[2] = dout[0];
+            dout[3] = dout[1];
+            {
+                float e[4] = {0.f, 0.f, 0.f, 0.f}, f2[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
+                mma3(dout, e, H20, sFr[(FR_W3 + 0) * 32 + lane]);
+                mma3(dout, e, H21, sFr[(FR_W3 + 1) * 32 + lane]);
+                mma3(f2, e2, C0, sFr[(FR_WS + 0) * 32 + lane]);
+                mma3(f2, e2, C1, sFr[(FR_WS + 1) * 32 + lane]);
+                mma3(f2, e2, C2, sFr[(FR_WS + 2) * 32 + lane]);
+                add4(e, e2);
+                add4(f2, e);
+                add4(dout, f2);
             }
-            mu = out[0];
-            s = out[1];
-            if (PASS == PASS_FWD_STORE && valid) {
+            const int q0 = lane & ~3;
+            muA = __shfl_sync(0xffffffffu, dout[0], q0);
+            sA = __shfl_sync(0xffffffffu, dout[1], q0);
+            muB = __shfl_sync(0xffffffffu, dout[2], q0);
+            sB = __shfl_sync(0xffffffffu, dout[3], q0);
+            if (PASS == PASS_FWD_STORE) {
 #pragma unroll
-                for (int o = 0; o < kAH; ++o) {
-                    a.act[(int64_t)o * N + i] = a1[o];
-                    a.act[(int64_t)(16 + o) * N + i] = a2[o];
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int uu = nt * 8 + 2 * tq + cc;
+                        if (pA.valid) {
+                            a.act[(int64_t)uu * N + pA.i] = d1[nt][cc];
+                            a.act[(int64_t)(16 + uu) * N + pA.i] = d2[nt][cc];
+                        }
+                        if (pB.valid) {
+                            a.act[(int64_t)uu * N + pB.i] = d1[nt][2 + cc];
+                            a.act[(int64_t)(16 + uu) * N + pB.i] = d2[nt][2 + cc];
+                        }
+                    }
+                if (tq == 0 && pA.valid) {
+                    a.act[(int64_t)32 * N + pA.i] = muA;
+                    a.act[(int64_t)33 * N + pA.i] = sA;
                 }
-                a.act[(int64_t)32 * N + i] = mu;
-                a.act[(int64_t)33 * N + i] = s;
+                if (tq == 0 && pB.valid) {
+                    a.act[(int64_t)32 * N + pB.i] = muB;
+                    a.act[(int64_t)33 * N + pB.i] = sB;
+                }
             }
         }
+        // ---- Laplace mass: lanes with even t take latent A, odd t latent B
+        const bool odd = tq & 1;
+        const LatentPos& pm = odd ? pB : pA;
+        const float mu = odd ? muB : muA, s = odd ? sB : sA;
         const float logb = fminf(fmaxf(s, kLogbMin), kLogbMax);
-        const float yv = __ldg(a.yt + ic);
-        const LapOut L = laplace_mass(yv, mu, logb);
-        if (valid) rate_acc += -log2f(fmaxf(L.p, kPMin));
+        const LapOut L = laplace_mass(__ldg(a.yt + pm.i), mu, logb);
+        if (tq < 2 && pm.valid) rate_acc += -log2f(fmaxf(L.p, kPMin));
+        if (!BWD) continue;
 
-        if (BWD) {
-            const float dp = (valid && L.p >= kPMin) ? -a.gscale / (L.p * 0.69314718055994531f) : 0.f;
-            const float dyd = dp * L.dp_dy;
-            const float dmu = -dyd;
-            const float ds = (s >= kLogbMin && s <= kLogbMax) ? dp * L.dp_dlogb : 0.f;
-            float da2[kAH], da1[kAH], dx[kAIn];
+        const float dp = (pm.valid && L.p >= kPMin) ? -a.gscale / (L.p * 0.69314718055994531f) : 0.f;
+        const float dyd = dp * L.dp_dy;
+        const float dmu = -dyd;
+        const float ds = (s >= kLogbMin && s <= kLogbMax) ? dp * L.dp_dlogb : 0.f;
+        if (tq < 2 && pm.valid) a.dYd[pm.i] = dyd;
+        const int q0 = lane & ~3;
+        const float dmuA = __shfl_sync(0xffffffffu, dmu, q0), dsA = __shfl_sync(0xffffffffu, ds, q0);
+        const float dmuB = __shfl_sync(0xffffffffu, dmu, q0 + 1), dsB = __shfl_sync(0xffffffffu, ds, q0 + 1);
+
+        // dA2 = (dout . W3) masked by a2 > 0
+        float da2[2][4];
 #pragma unroll
-            for (int q = 0; q < kAH; ++q) {
-                const float d = sW[sw_w3 + q] * dmu + sW[sw_w3 + kAH + q] * ds;
-                da2[q] = a2[q] > 0.f ? d : 0.f;
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const float vA = dmuA * w3c[nt][cc][0] + dsA * w3c[nt][cc][1];
+                const float vB = dmuB * w3c[nt][cc][0] + dsB * w3c[nt][cc][1];
+                da2[nt][cc] = d2[nt][cc] > 0.f ? vA : 0.f;
+                da2[nt][2 + cc] = d2[nt][2 + cc] > 0.f ? vB : 0.f;
             }
+        const AFrag DA20 = chain(da2[0]), DA21 = chain(da2[1]);
+        // dA1 = (dA2 . W2) masked by a1 > 0
+        float da1[2][4];
 #pragma unroll
-            for (int q = 0; q < kAH; ++q) da1[q] = 0.f;
+        for (int nt = 0; nt < 2; ++nt) {
 #pragma unroll
-            for (int o = 0; o < kAH; ++o) {
+            for (int q = 0; q < 4; ++q) da1[nt][q] = 0.f;
+            float e[4] = {0.f, 0.f, 0.f, 0.f};
+            mma3(da1[nt], e, DA20, sFr[(FR_BW2 + 0 * 2 + nt) * 32 + lane]);
+            mma3(da1[nt], e, DA21, sFr[(FR_BW2 + 1 * 2 + nt) * 32 + lane]);
+            add4(da1[nt], e);
 #pragma unroll
-                for (int q = 0; q < kAH; q += 4) {
-                    const float4 w = *reinterpret_cast<const float4*>(sW + sw_w2 + o * kAH + q);
-                    da1[q] = fmaf(w.x, da2[o], da1[q]);
-                    da1[q + 1] = fmaf(w.y, da2[o], da1[q + 1]);
-                    da1[q + 2] = fmaf(w.z, da2[o], da1[q + 2]);
-                    da1[q + 3] = fmaf(w.w, da2[o], da1[q + 3]);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kAH; ++q) da1[q] = a1[q] > 0.f ? da1[q] : 0.f;
-#pragma unroll
-            for (int q = 0; q < kAIn; q += 4) {
-                const float4 w0 = *reinterpret_cast<const float4*>(sW + sw_ws + q);
-                const float4 w1 = *reinterpret_cast<const float4*>(sW + sw_ws + kAIn + q);
-                dx[q] = w0.x * dmu + w1.x * ds;
-                dx[q + 1] = w0.y * dmu + w1.y * ds;
-                dx[q + 2] = w0.z * dmu + w1.z * ds;
-                dx[q + 3] = w0.w * dmu + w1.w * ds;
-            }
-#pragma unroll
-            for (int o = 0; o < kAH; ++o) {
-#pragma unroll
-                for (int q = 0; q < kAIn; q += 4) {
-                    const float4 w = *reinterpret_cast<const float4*>(sW + sw_w1 + o * kAIn + q);
-                    dx[q] = fmaf(w.x, da1[o], dx[q]);
-                    dx[q + 1] = fmaf(w.y, da1[o], dx[q + 1]);
-                    dx[q + 2] = fmaf(w.z, da1[o], dx[q + 2]);
-                    dx[q + 3] = fmaf(w.w, da1[o], dx[q + 3]);
-                }
-            }
-            if (valid) {
-#pragma unroll
-                for (int n = 0; n < kNCtx; ++n) a.dS[(int64_t)n * N + i] = dx[n];
-                a.dYd[i] = dyd;
-                if (nin > 0) {
-                    float* dR = k == 0 ? a.dR0 : (k == 1 ? a.dR1 : a.dR2);
-                    const int nk = hk * wk;
-#pragma unroll
-                    for (int j = 0; j < 6; ++j)
-                        if (j < nin) {
-                            float acc = 0.f;
-#pragma unroll
-                            for (int o = 0; o < kF; ++o) acc = fmaf(sW[ifce_w_off(k) + o * nin + j], dx[kNCtx + o], acc);
-                            dR[(int64_t)j * nk + li] = acc;
-                        }
-                }
-            }
-            // stage the outer-product factors (zero for padding latents)
-            const float m = valid ? 1.f : 0.f;
-#pragma unroll
-            for (int q = 0; q < kAH; ++q) {
-                sU[q * kLd + tid] = da1[q] * m;
-                sU[(16 + q) * kLd + tid] = da2[q] * m;
-                sV[(24 + q) * kLd + tid] = fmaxf(a1[q], 0.f) * m;
-                sV[(40 + q) * kLd + tid] = fmaxf(a2[q], 0.f) * m;
-            }
-            sU[32 * kLd + tid] = dmu * m;
-            sU[33 * kLd + tid] = ds * m;
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk)
-#pragma unroll
-                for (int o = 0; o < kF; ++o) sU[(40 + 4 * kk + o) * kLd + tid] = (k == kk) ? dx[kNCtx + o] * m : 0.f;
-#pragma unroll
-            for (int q = 0; q < kAIn; ++q) sV[q * kLd + tid] = x[q] * m;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) sV[(56 + j) * kLd + tid] = rv[j] * m;
-            __syncthreads();
-            if (tid < kTasks) {
-                const int blk = tid / kChunks, ch = tid - blk * kChunks;
-                const float* U = sU + c_blk_u[blk] * kLd;
-                const float* V = sV + c_blk_v[blk] * kLd;
-                float acc[8][8];
-                float* A = sAcc + tid * 64;
-#pragma unroll
-                for (int p = 0; p < 8; ++p)
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) acc[p][q] = A[p * 8 + q];
-                for (int l = c_chunk[ch]; l < c_chunk[ch + 1]; l += 4) {
-                    float4 u[8], v[8];
-#pragma unroll
-                    for (int p = 0; p < 8; ++p) u[p] = *reinterpret_cast<const float4*>(U + p * kLd + l);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const float4*>(V + q * kLd + l);
-#pragma unroll
-                    for (int p = 0; p < 8; ++p)
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            float t = acc[p][q];
-                            t = fmaf(u[p].x, v[q].x, t);
-                            t = fmaf(u[p].y, v[q].y, t);
-                            t = fmaf(u[p].z, v[q].z, t);
-                            t = fmaf(u[p].w, v[q].w, t);
-                            acc[p][q] = t;
-                        }
-                }
-#pragma unroll
-                for (int p = 0; p < 8; ++p)
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) A[p * 8 + q] = acc[p][q];
-            }
-            __syncthreads();
+            for (int q = 0; q < 4; ++q) da1[nt][q] = d1[nt][q] > 0.f ? da1[nt][q] : 0.f;
         }
+        const AFrag DA10 = chain(da1[0]), DA11 = chain(da1[1]);
+        // dC = dA1 . W1 + dout . Ws
+        float dc[3][4];
+#pragma unroll
+        for (int nt = 0; nt < 3; ++nt) {
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                dc[nt][cc] = dmuA * wsc[nt][cc][0] + dsA * wsc[nt][cc][1];
+                dc[nt][2 + cc] = dmuB * wsc[nt][cc][0] + dsB * wsc[nt][cc][1];
+            }
+            float e[4] = {0.f, 0.f, 0.f, 0.f};
+            mma3(dc[nt], e, DA10, sFr[(FR_BW1 + 0 * 3 + nt) * 32 + lane]);
+            mma3(dc[nt], e, DA11, sFr[(FR_BW1 + 1 * 3 + nt) * 32 + lane]);
+            add4(dc[nt], e);
+        }
+        // context-gradient planes (features 0..15)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const int f = nt * 8 + 2 * tq + cc;
+                if (pA.valid) a.dS[(int64_t)f * N + pA.i] = dc[nt][cc];
+                if (pB.valid) a.dS[(int64_t)f * N + pB.i] = dc[nt][2 + cc];
+            }
+        // IFCE output gradients df[0..3] (features 16..19 live in lanes t = 0, 1 of tile 2)
+        float dfA[4], dfB[4];
+        dfA[0] = __shfl_sync(0xffffffffu, dc[2][0], q0);
+        dfA[1] = __shfl_sync(0xffffffffu, dc[2][1], q0);
+        dfA[2] = __shfl_sync(0xffffffffu, dc[2][0], q0 + 1);
+        dfA[3] = __shfl_sync(0xffffffffu, dc[2][1], q0 + 1);
+        dfB[0] = __shfl_sync(0xffffffffu, dc[2][2], q0);
+        dfB[1] = __shfl_sync(0xffffffffu, dc[2][3], q0);
+        dfB[2] = __shfl_sync(0xffffffffu, dc[2][2], q0 + 1);
+        dfB[3] = __shfl_sync(0xffffffffu, dc[2][3], q0 + 1);
+        // IFCE input gradients dr_j = sum_o W_k[o][j] df[o]; lane t writes j = t and t + 4
+        auto write_dr = [&](const LatentPos& p, const float (&df)[4]) {
+            const int nin = ifce_nin(p.k);
+            if (nin > 0 && p.valid) {
+                float* dR = p.k == 0 ? a.dR0 : (p.k == 1 ? a.dR1 : a.dR2);
+                const int nk = g.h[p.k] * g.w[p.k];
+                const int wo = ifce_w_off(p.k) - po::if_w0;
+#pragma unroll
+                for (int jj = 0; jj < 2; ++jj) {
+                    const int j = tq + 4 * jj;
+                    if (j < nin) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int o = 0; o < kF; ++o) v = fmaf(sIf[wo + o * nin + j], df[o], v);
+                        dR[(int64_t)j * nk + p.li] = v;
+                    }
+                }
+            }
+        };
+        write_dr(pA, dfA);
+        write_dr(pB, dfB);
+        // ---- stage the outer-product factors, transposed to [feature][latent]
+        const float mA = pA.valid ? 1.f : 0.f, mB = pB.valid ? 1.f : 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const int uu = nt * 8 + 2 * tq + cc;
+                st[(U_DA1 + uu) * kSld + gq] = da1[nt][cc] * mA;
+                st[(U_DA1 + uu) * kSld + gq + 8] = da1[nt][2 + cc] * mB;
+                st[(U_DA2 + uu) * kSld + gq] = da2[nt][cc] * mA;
+                st[(U_DA2 + uu) * kSld + gq + 8] = da2[nt][2 + cc] * mB;
+                st[(V_H1 + uu) * kSld + gq] = fmaxf(d1[nt][cc], 0.f);
+                st[(V_H1 + uu) * kSld + gq + 8] = fmaxf(d1[nt][2 + cc], 0.f);
+                st[(V_H2 + uu) * kSld + gq] = fmaxf(d2[nt][cc], 0.f);
+                st[(V_H2 + uu) * kSld + gq + 8] = fmaxf(d2[nt][2 + cc], 0.f);
+            }
+        {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                st[(V_C + tq + 4 * q) * kSld + gq] = cA[q];
+                st[(V_C + tq + 4 * q) * kSld + gq + 8] = cB[q];
+            }
+            // U_O rows t, t+4, t+8, t+12: 0 dmu, 1 ds, 2..13 df of grid (row-2)/4, 14..15 zero (preset)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = tq + 4 * q;
+                if (row >= 14) continue;
+                float vA, vB;
+                if (row == 0) {
+                    vA = dmuA;
+                    vB = dmuB;
+                } else if (row == 1) {
+                    vA = dsA;
+                    vB = dsB;
+                } else {
+                    const int kk = (row - 2) >> 2, o = (row - 2) & 3;
+                    vA = pA.k == kk ? sel(dfA, o) : 0.f;
+                    vB = pB.k == kk ? sel(dfB, o) : 0.f;
+                }
+                st[(U_O + row) * kSld + gq] = vA * mA;
+                st[(U_O + row) * kSld + gq + 8] = vB * mB;
+            }
+            // R rows t and t+4 (rows 6, 7 are the preset one and zero)
+            st[(V_R + tq) * kSld + gq] = sel(rA, tq);
+            st[(V_R + tq) * kSld + gq + 8] = sel(rB, tq);
+            if (tq < 2) {
+                st[(V_R + tq + 4) * kSld + gq] = tq == 0 ? rA[4] : rA[5];
+                st[(V_R + tq + 4) * kSld + gq + 8] = tq == 0 ? rB[4] : rB[5];
+            }
+        }
+        __syncwarp();
+        // ---- parameter-gradient tiles over K = 16 latents (two k-steps of 8)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int k0 = ks * 8;
+            auto afrag = [&](int row0) {
+                return make_a(st[(row0 + gq) * kSld + k0 + tq], st[(row0 + gq + 8) * kSld + k0 + tq],
+                              st[(row0 + gq) * kSld + k0 + tq + 4], st[(row0 + gq + 8) * kSld + k0 + tq + 4]);
+            };
+            auto bfrag = [&](int row0) {  // as an AFrag whose h[0..1], l[0..1] hold (b0, b1)
+                AFrag f;
+                split2(st[(row0 + gq) * kSld + k0 + tq], f.h[0], f.l[0]);
+                split2(st[(row0 + gq) * kSld + k0 + tq + 4], f.h[1], f.l[1]);
+                return f;
+            };
+            const AFrag UA1 = afrag(U_DA1), UA2 = afrag(U_DA2), UO = afrag(U_O);
+            const AFrag VC0 = bfrag(V_C), VC1 = bfrag(V_C + 8), VC2 = bfrag(V_C + 16);
+            const AFrag VH10 = bfrag(V_H1), VH11 = bfrag(V_H1 + 8);
+            const AFrag VH20 = bfrag(V_H2), VH21 = bfrag(V_H2 + 8);
+            const AFrag VR = bfrag(V_R);
+            mma3b(acc[0], UA1, VC0);
+            mma3b(acc[1], UA1, VC1);
+            mma3b(acc[2], UA1, VC2);
+            mma3b(acc[3], UA2, VH10);
+            mma3b(acc[4], UA2, VH11);
+            mma3b(acc[5], UA2, VC2);
+            mma3b(acc[6], UO, VH20);
+            mma3b(acc[7], UO, VH21);
+            mma3b(acc[8], UO, VC0);
+            mma3b(acc[9], UO, VC1);
+            mma3b(acc[10], UO, VC2);
+            mma3b(acc[11], UO, VR);
+        }
+        __syncwarp();
     }
 
     // rate partial of this CTA
@@ -372,33 +601,41 @@ __global__ void __launch_bounds__(kT, 2) k_arm(ArmArgs a) {
         block_sum<1>(v, scratch);
         if (tid == 0) a.rate_part[blockIdx.x] = (double)v[0];
     }
-    if (BWD) {
-        float* gp = a.gpart + (int64_t)blockIdx.x * po::arm_block;
-        for (int e = tid; e < kBlocks * 64; e += kT) {
-            const int blk = e >> 6, pq = e & 63;
-            const int u = c_blk_u[blk] + (pq >> 3), v = c_blk_v[blk] + (pq & 7);
-            int second;
-            const int idx = arm_grad_index(u, v, &second);
-            if (idx < 0) continue;
-            float sum = 0.f;
-            for (int ch = 0; ch < kChunks; ++ch) sum += sAcc[(blk * kChunks + ch) * 64 + pq];
-            gp[idx] = sum;
-            if (second >= 0) gp[second] = sum;
-        }
+    if (!BWD) return;
+    // the 4 warps' gradient tiles, added in warp order
+    __syncthreads();
+    float* sAcc = sStage;  // [warp][T][lane][4]
+#pragma unroll
+    for (int T = 0; T < 12; ++T)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sAcc[((wid * 12 + T) * 32 + lane) * 4 + q] = acc[T][q];
+    __syncthreads();
+    float* gp = a.gpart + (int64_t)blockIdx.x * po::arm_block;
+    for (int e = tid; e < 12 * 32 * 4; e += kT) {
+        const int T = e >> 7, l = (e >> 2) & 31, q = e & 3;
+        const int row = (l >> 2) + (q >= 2 ? 8 : 0), col = 2 * (l & 3) + (q & 1);
+        int second;
+        const int idx = wgrad_index(T, row, col, &second);
+        if (idx < 0) continue;
+        float s = 0.f;
+        for (int w = 0; w < kWarps; ++w) s += sAcc[((w * 12 + T) * 32 + l) * 4 + q];
+        gp[idx] = s;
+        if (second >= 0) gp[second] = s;
     }
 }
 
 }  // namespace
 
-size_t arm_smem_bytes(int pass) {
-    if (!pass_bwd(pass)) return (size_t)kWSm * sizeof(float);
-    return (size_t)(kWSm + (kURows + kVRows) * kLd + kTasks * 64) * sizeof(float);
+size_t arm_smem_bytes(int pass) {  // the staging tiles exist only for the adjoint passes
+    return (size_t)FR_N * 32 * sizeof(float4) +
+           (size_t)(kIfceSm + (pass_bwd(pass) ? kWarps * kStage : 0)) * sizeof(float);
 }
 
 int arm_grid(int64_t N) {
-    const int64_t rounds = (N + kT - 1) / kT;
+    const int64_t units = (N + 15) / 16;
+    const int64_t ctas = (units + kWarps - 1) / kWarps;
     const int64_t cap = (int64_t)num_sms() * 2;
-    return (int)(rounds < cap ? rounds : cap);
+    return (int)(ctas < cap ? (ctas < 1 ? 1 : ctas) : cap);
 }
 
 void launch_arm(const Work& w, const float* params, int pass, float grad_scale, cudaStream_t s) {
@@ -427,9 +664,11 @@ void launch_arm(const Work& w, const float* params, int pass, float grad_scale, 
 }
 
 void arm_init_attributes() {
-    const int big = (int)arm_smem_bytes(PASS_FWD_BWD);
-    cudaFuncSetAttribute(k_arm<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_arm<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    const int sm = (int)arm_smem_bytes(PASS_FWD_BWD);
+    cudaFuncSetAttribute(k_arm<PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_arm<PASS_FWD_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_arm<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_arm<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 }  // namespace cc

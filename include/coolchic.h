@@ -121,6 +121,33 @@ int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const fl
                          const cc_state_t* state, int32_t n_iters, cc_rd_t* rd_per_iter,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* Batched encoder iterations (no counterpart in the paper, which encodes one image at a time):
+ * n_jobs images of any sizes, each with its own hyper-parameters, state and workspace (sized by
+ * coolchic_workspace_bytes(arch, 0)), advance together; every kernel of the iteration is one
+ * launch for all jobs.  The result of each job equals that of coolchic_encode_step on it, up to
+ * the summation order of its parameter gradients (which the schedule changes).
+ *
+ * coolchic_batch_create (blocking, not capturable) validates the jobs, plans the launches and
+ * uploads the plan to `table` [device, 256-byte aligned, coolchic_batch_table_bytes bytes, owned
+ * by the caller and kept alive and unmodified until coolchic_batch_destroy].  `schedule`
+ * (nullable: all 1) gives, per kernel class, the fraction (0, 1] of each job's single-image CTA
+ * count used in the batch.  rd_capacity: records kept per coolchic_batch_step call (0: none).
+ * coolchic_batch_step (asynchronous, capturable in a CUDA graph) runs n_iters iterations on every
+ * job (n_iters <= rd_capacity when rd_capacity > 0); the records of the last call are at
+ * coolchic_batch_records(): [device] rd_capacity x n_jobs cc_rd_t, slot [iteration][job]. */
+typedef struct {
+    float arm, syn, conv, other;
+} cc_schedule_t;
+typedef struct cc_batch cc_batch_t;
+size_t coolchic_batch_table_bytes(int32_t n_jobs, int32_t rd_capacity);
+int coolchic_batch_create(int32_t n_jobs, const cc_arch_t* archs, const cc_hparams_t* hps,
+                          const float* const* images, const cc_state_t* states, void* const* workspaces,
+                          const size_t* workspace_bytes, const cc_schedule_t* schedule,
+                          int32_t rd_capacity, void* table, size_t table_bytes, cc_batch_t** batch);
+int coolchic_batch_step(cc_batch_t* batch, int32_t n_iters, void* stream);
+const cc_rd_t* coolchic_batch_records(const cc_batch_t* batch);
+int coolchic_batch_destroy(cc_batch_t* batch);
+
 /* Forward pass only (Eq. 10): rate of the relaxed latents (Eq. 3, Eq. 11), reconstruction and
  * distortion.  relax = CC_RELAX_*; `step` keys the noise for CC_RELAX_NOISE.
  *   latents, params [device];  rd_out [device, nullable] one record;

@@ -221,6 +221,9 @@ void tend(int id, cudaStream_t s) {
 
 }  // namespace
 
+size_t layout_job(const cc_arch_t* arch, int flags, char* base, Work* w) { return build_work(arch, flags, base, w); }
+int device_setup_checked() { return device_setup(); }
+
 int set_error(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;

@@ -114,21 +114,6 @@ __device__ float bfrag_value(const float* P, int f, int g, int t, int which) {
     }
 }
 
-struct ArmArgs {
-    Geom g;
-    int64_t N;
-    const float* yt;
-    const float* params;
-    float gscale;       // dLoss / dbits
-    float* dS;
-    float* dR0;
-    float* dR1;
-    float* dR2;
-    float* dYd;
-    float* act;         // [34][N]: a1 (16), a2 (16), mu, s
-    float* gpart;       // [gridDim.x][756]
-    double* rate_part;  // [gridDim.x]
-};
 
 struct LatentPos {
     int k, r, c, li;
@@ -210,7 +195,7 @@ __device__ int wgrad_index(int T, int row, int col, int* second) {
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(kT, 2) k_arm(ArmArgs a) {
+__device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     constexpr bool BWD = pass_bwd(PASS);
     extern __shared__ float4 smem4[];
     float4* sFr = smem4;                                             // [FR_N][32]
@@ -286,7 +271,7 @@ __global__ void __launch_bounds__(kT, 2) k_arm(ArmArgs a) {
 
     const int64_t N = a.N;
     const int64_t n_units = (N + 15) / 16;
-    for (int64_t u = (int64_t)blockIdx.x * kWarps + wid; u < n_units; u += (int64_t)gridDim.x * kWarps) {
+    for (int64_t u = (int64_t)cta * kWarps + wid; u < n_units; u += (int64_t)ncta * kWarps) {
         const LatentPos pA = locate(g, rcp_w, u * 16 + gq, N);
         const LatentPos pB = locate(g, rcp_w, u * 16 + gq + 8, N);
         // ---- context features f in {t, t+4, 8+t, 12+t, 16+t, 20+t} of latents A (row g) and B (row g+8)
@@ -599,7 +584,7 @@ __global__ void __launch_bounds__(kT, 2) k_arm(ArmArgs a) {
         float v[1] = {rate_acc};
         __shared__ float scratch[kT / 32];
         block_sum<1>(v, scratch);
-        if (tid == 0) a.rate_part[blockIdx.x] = (double)v[0];
+        if (tid == 0) a.rate_part[cta] = (double)v[0];
     }
     if (!BWD) return;
     // the 4 warps' gradient tiles, added in warp order
@@ -610,7 +595,7 @@ __global__ void __launch_bounds__(kT, 2) k_arm(ArmArgs a) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) sAcc[((wid * 12 + T) * 32 + lane) * 4 + q] = acc[T][q];
     __syncthreads();
-    float* gp = a.gpart + (int64_t)blockIdx.x * po::arm_block;
+    float* gp = a.gpart + (int64_t)cta * po::arm_block;
     for (int e = tid; e < 12 * 32 * 4; e += kT) {
         const int T = e >> 7, l = (e >> 2) & 31, q = e & 3;
         const int row = (l >> 2) + (q >= 2 ? 8 : 0), col = 2 * (l & 3) + (q & 1);
@@ -622,6 +607,20 @@ __global__ void __launch_bounds__(kT, 2) k_arm(ArmArgs a) {
         gp[idx] = s;
         if (second >= 0) gp[second] = s;
     }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kT, 2) k_arm(ArmArgs a) {
+    __shared__ ArmArgs sa;
+    param_fetch(a, sa);
+    arm_body<PASS>(sa, blockIdx.x, gridDim.x);
+}
+template <int PASS>
+__global__ void __launch_bounds__(kT, 2) k_arm_b(Batch<ArmArgs> b) {
+    __shared__ ArmArgs sa;
+    const int j = batch_job(b.cta_begin, b.njobs);
+    batch_fetch(b.args, j, sa);
+    arm_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
 }
 
 }  // namespace
@@ -638,8 +637,9 @@ int arm_grid(int64_t N) {
     return (int)(ctas < cap ? (ctas < 1 ? 1 : ctas) : cap);
 }
 
-void launch_arm(const Work& w, const float* params, int pass, float grad_scale, cudaStream_t s) {
+ArmArgs arm_args(const Work& w, const float* params, float grad_scale) {
     ArmArgs a;
+    a.pad_ = 0;
     a.g = w.g;
     a.N = w.N;
     a.yt = w.yt;
@@ -653,6 +653,11 @@ void launch_arm(const Work& w, const float* params, int pass, float grad_scale, 
     a.act = w.act_arm;
     a.gpart = w.gpart_arm;
     a.rate_part = w.rate_part;
+    return a;
+}
+
+void launch_arm(const Work& w, const float* params, int pass, float grad_scale, cudaStream_t s) {
+    const ArmArgs a = arm_args(w, params, grad_scale);
     const size_t sm = arm_smem_bytes(pass);
     const int grid = w.n_cta_arm;
     switch (pass) {
@@ -663,12 +668,26 @@ void launch_arm(const Work& w, const float* params, int pass, float grad_scale, 
     }
 }
 
+void launch_arm_b(const Batch<ArmArgs>& b, int pass, cudaStream_t s) {
+    const size_t sm = arm_smem_bytes(pass);
+    switch (pass) {
+        case PASS_FWD: k_arm_b<PASS_FWD><<<b.total_ctas, kT, sm, s>>>(b); break;
+        case PASS_FWD_STORE: k_arm_b<PASS_FWD_STORE><<<b.total_ctas, kT, sm, s>>>(b); break;
+        case PASS_FWD_BWD: k_arm_b<PASS_FWD_BWD><<<b.total_ctas, kT, sm, s>>>(b); break;
+        default: k_arm_b<PASS_BWD_LOAD><<<b.total_ctas, kT, sm, s>>>(b); break;
+    }
+}
+
 void arm_init_attributes() {
     const int sm = (int)arm_smem_bytes(PASS_FWD_BWD);
     cudaFuncSetAttribute(k_arm<PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_arm<PASS_FWD_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_arm<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_arm<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_arm_b<PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_arm_b<PASS_FWD_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_arm_b<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_arm_b<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 }  // namespace cc

@@ -20,19 +20,6 @@ constexpr int R2H = kTH + 4, R2W = kTW + 4;  // dxh (halo 2)
 constexpr int R1H = kTH + 2, R1W = kTW + 2;  // dx1 (halo 1)
 constexpr int kSlices = 8;                   // weight-gradient row slices of 2 rows
 
-struct ConvArgs {
-    int H, W;
-    int64_t HW;
-    const float* t;
-    const float* img;
-    const float* params;
-    float gscale;     // 2 / (3 HW) times the caller's outer scale
-    float* dt;
-    float* xhat;      // optional
-    float* gpart;     // [gridDim.x][168]
-    double* se_part;  // [gridDim.x]
-    int tiles_x, n_tiles;
-};
 
 __device__ __forceinline__ void conv_pairs(int q, int n, int (&src)[3], int (&tap)[3]) {
     if (n == 1) {
@@ -47,7 +34,7 @@ __device__ __forceinline__ void conv_pairs(int q, int n, int (&src)[3], int (&ta
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs a) {
+__device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) {
     constexpr bool BWD = pass_bwd(PASS);
     __shared__ float sWc[2][84];
     __shared__ float sT[3][R4H][R4W];
@@ -66,7 +53,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs a) {
     for (int q = 0; q < 9; ++q) gacc[q] = 0.f;
     double se = 0.0;
     const int H = a.H, W = a.W;
-    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    for (int tile = cta; tile < a.n_tiles; tile += ncta) {
         const int ty0 = (tile / a.tiles_x) * kTH, tx0 = (tile % a.tiles_x) * kTW;
         __syncthreads();
         {
@@ -234,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs a) {
         if (tid == 0) {
             double s = 0.0;
             for (int q = 0; q < kThreads / 32; ++q) s += sSe[q];
-            a.se_part[blockIdx.x] = s;
+            a.se_part[cta] = s;
         }
     }
     if (!BWD) return;
@@ -244,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs a) {
     for (int q = 0; q < 9; ++q)
         if (tid < 192) sG[tid * 9 + q] = gacc[q];
     __syncthreads();
-    float* gp = a.gpart + (int64_t)blockIdx.x * po::conv_block;
+    float* gp = a.gpart + (int64_t)cta * po::conv_block;
     if (tid < 18 * 9) {
         const int task = tid / 9, q = tid % 9;
         const int c = task / 9, o = (task / 3) % 3, i = task % 3;
@@ -259,13 +246,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs a) {
     }
 }
 
+template <int PASS>
+__global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs a) {
+    __shared__ ConvArgs sa;
+    param_fetch(a, sa);
+    conv_body<PASS>(sa, blockIdx.x, gridDim.x);
+}
+template <int PASS>
+__global__ void __launch_bounds__(kThreads, 2) k_conv_b(Batch<ConvArgs> b) {
+    __shared__ ConvArgs sa;
+    const int j = batch_job(b.cta_begin, b.njobs);
+    batch_fetch(b.args, j, sa);
+    conv_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
+}
+
 }  // namespace
 
 int conv_tiles(int H, int W) { return ((H + kTH - 1) / kTH) * ((W + kTW - 1) / kTW); }
 
-void launch_conv(const Work& w, const float* params, const float* image, int pass, float grad_scale,
-                 float* xhat_out, cudaStream_t s) {
+ConvArgs conv_args(const Work& w, const float* params, const float* image, float grad_scale, float* xhat_out) {
     ConvArgs a;
+    a.pad_ = 0;
     a.H = w.g.H;
     a.W = w.g.W;
     a.HW = w.HW;
@@ -279,10 +280,18 @@ void launch_conv(const Work& w, const float* params, const float* image, int pas
     a.se_part = w.se_part;
     a.tiles_x = (w.g.W + kTW - 1) / kTW;
     a.n_tiles = conv_tiles(w.g.H, w.g.W);
+    return a;
+}
+
+void launch_conv(const Work& w, const float* params, const float* image, int pass, float grad_scale,
+                 float* xhat_out, cudaStream_t s) {
+    const ConvArgs a = conv_args(w, params, image, grad_scale, xhat_out);
     if (pass_bwd(pass))
         k_conv<PASS_FWD_BWD><<<w.n_cta_conv, kThreads, 0, s>>>(a);
     else
         k_conv<PASS_FWD><<<w.n_cta_conv, kThreads, 0, s>>>(a);
 }
+
+void launch_conv_b(const Batch<ConvArgs>& b, cudaStream_t s) { k_conv_b<PASS_FWD_BWD><<<b.total_ctas, kThreads, 0, s>>>(b); }
 
 }  // namespace cc

@@ -1,6 +1,7 @@
 // Host-side launch wrappers of the encoder-step kernels (internal to the library).
 #pragma once
 
+#include "../../include/coolchic.h"
 #include "cc_common.cuh"
 
 namespace cc {
@@ -57,6 +58,163 @@ struct Work {
     int n_cta_up[kL];  // CTAs of the upsampling-adjoint kernel of stage s = 1..6
 };
 
+// ---------------------------------------------------------------------------------------------
+// Multi-job launches.  Every kernel body takes its arguments, its CTA index within the job and
+// the job's CTA count.  A single-job launch passes the arguments by value; a multi-job launch
+// reads an array of per-job arguments and the first CTA of each job (njobs + 1 entries) from
+// device memory, so that one launch serves many images of different sizes.
+// ---------------------------------------------------------------------------------------------
+template <typename A>
+struct Batch {
+    const A* args;         // [njobs], device
+    const int* cta_begin;  // [njobs + 1], device
+    int njobs;
+    int total_ctas;
+};
+
+__device__ __forceinline__ int batch_job(const int* __restrict__ cb, int nj) {
+    int j = 0;
+    while (j + 1 < nj && (int)blockIdx.x >= __ldg(cb + j + 1)) ++j;
+    return j;
+}
+
+// Copies job j's arguments into shared memory (all threads), then synchronises.
+template <typename A>
+__device__ __forceinline__ void batch_fetch(const A* __restrict__ args, int j, A& sa) {
+    static_assert(sizeof(A) % 4 == 0, "argument structs are copied as 32-bit words");
+    const int* src = reinterpret_cast<const int*>(args + j);
+    int* dst = reinterpret_cast<int*>(&sa);
+    for (int i = threadIdx.x; i < (int)(sizeof(A) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+}
+
+// Copies a single-job launch's arguments into shared memory, so that the kernel body runs on
+// arguments in the same memory space as in a multi-job launch (one compiled body, bitwise equal
+// results whether an image runs alone or in a batch).
+template <typename A>
+__device__ __forceinline__ void param_fetch(const A& a, A& sa) {
+    if (threadIdx.x == 0) sa = a;
+    __syncthreads();
+}
+
+// Argument structs of the kernels (filled by the launchers and by the batch planner).
+struct RelaxArgs {
+    const float* y;
+    float* yt;
+    int64_t N;
+    uint64_t seed;
+    const int64_t* step_dev;  // step from here when non-null, else step_host
+    int64_t step_host;
+    int relax;
+    int pad_;
+};
+struct ArmArgs {
+    Geom g;
+    int64_t N;
+    const float* yt;
+    const float* params;
+    float gscale;  // dLoss / dbits
+    int pad_;
+    float* dS;
+    float* dR0;
+    float* dR1;
+    float* dR2;
+    float* dYd;
+    float* act;         // [34][N]: a1 (16), a2 (16), mu, s
+    float* gpart;       // [n_cta][756]
+    double* rate_part;  // [n_cta]
+};
+struct UpFwdArgs {
+    const float* src0;   // y~ of grid m+1
+    const float* srcup;  // up[m+1] (channels 1..), may be null when nch == 1
+    float* dst;          // up[m]
+    const float* taps;   // 4 taps of this stage (device)
+    int hs, ws, ht, wt, nch, pad_;
+};
+struct SynArgs {
+    Geom g;
+    int64_t HW;
+    const float* yt;
+    const float* up1;
+    const float* params;
+    float* t;         // [3][HW]
+    const float* dt;  // [3][HW]
+    float* act;       // [40][HW]
+    float* dYsyn0;    // grid-0 part of dYsyn [HW]
+    float* dz;        // [6][HW]
+    float* gpart;     // [n_cta][467]
+};
+struct ConvArgs {
+    int H, W;
+    int64_t HW;
+    const float* t;
+    const float* img;
+    const float* params;
+    float* dt;
+    float* xhat;      // optional
+    float* gpart;     // [n_cta][168]
+    double* se_part;  // [n_cta]
+    float gscale;     // 2 / (3 HW) times the caller's outer scale
+    int tiles_x, n_tiles, pad_;
+};
+struct UpAdjArgs {
+    const float* D;      // [nch][ht][wt]
+    const float* src0;   // S_s channel 0 = y~ of grid s
+    const float* srcup;  // S_s channels 1.. = up[s]
+    float* out0;         // dYsyn of grid s
+    float* outup;        // dup[s]
+    float* gpart;        // [n_cta][4]
+    const float* taps;
+    int hs, ws, ht, wt, nch, pad_;
+};
+struct IfceArgs {
+    Geom g;
+    const float* dR0;
+    const float* dR1;
+    const float* dR2;
+    float* Q;
+};
+struct GatherArgs {
+    Geom g;
+    const float* dYd;
+    const float* dS;
+    const float* dR0;
+    const float* dR1;
+    const float* dIf;
+    const float* dYsyn;
+    float* grad_out;  // non-null: write the gradient instead of taking an Adam step
+    float* y;
+    float* m;
+    float* v;
+    const int64_t* step_dev;
+    Hp hp;
+    int zero_grad, pad_;
+};
+struct ReduceArgs {
+    const float* garm;
+    const float* gup;  // [6][kUpMaxCta][4]
+    const float* gsyn;
+    const float* gconv;
+    float* params;
+    float* m;
+    float* v;
+    float* grad_out;  // non-null: write the gradient (times out_scale) instead of Adam
+    const int64_t* step_dev;
+    Hp hp;
+    int n_arm, n_syn, n_conv;
+    int nup[kL - 1];
+    float out_scale;
+};
+struct FinishArgs {
+    const double* rate_part;
+    const double* se_part;
+    double* rd;         // record base (3 doubles per slot), may be null
+    int64_t* step_dev;  // slot = *step_dev - *base_step when both non-null, else 0
+    int64_t* base_step;
+    double inv_hw, inv_3hw, lambda;
+    int n_rate, n_se, rd_stride, mark_base, increment, pad_;
+};
+
 int num_sms();
 // Records a printf-style message for coolchic_last_error() and returns `code`.
 int set_error(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -95,6 +253,43 @@ int conv_tiles(int H, int W);
 int up_adj_grid(int64_t pairs);
 void arm_init_attributes();
 void synth_init_attributes();
+
+// argument builders, CTA counts and multi-job launches (batched encode)
+RelaxArgs relax_args(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, uint64_t seed,
+                     int relax);
+ArmArgs arm_args(const Work& w, const float* params, float grad_scale);
+UpFwdArgs up_fwd_args(const Work& w, const float* params, int m);
+SynArgs syn_args(const Work& w, const float* params);
+ConvArgs conv_args(const Work& w, const float* params, const float* image, float grad_scale, float* xhat_out);
+UpAdjArgs up_adj_args(const Work& w, const float* params, int st);
+IfceArgs ifce_args(const Work& w);
+GatherArgs gather_args(const Work& w, int relax, float* grad_out, float* y, float* m, float* v, const Hp& hp,
+                       const int64_t* step_dev);
+ReduceArgs reduce_args(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,
+                       const Hp& hp, const int64_t* step_dev);
+FinishArgs finish_args(const Work& w, const Hp& hp, int have_arm, int have_conv, double* rd, int rd_stride,
+                       int64_t* step_dev, int mark_base, int increment);
+int relax_ctas(const Work& w);
+int up_fwd_ctas(const Work& w, int m);
+int syn_fwd_ctas(const Work& w);
+int ifce_ctas(const Work& w);
+int gather_ctas(const Work& w);
+int reduce_ctas();
+void launch_relax_b(const Batch<RelaxArgs>& b, cudaStream_t s);
+void launch_arm_b(const Batch<ArmArgs>& b, int pass, cudaStream_t s);
+void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s);
+void launch_syn_fwd_b(const Batch<SynArgs>& b, cudaStream_t s);
+void launch_conv_b(const Batch<ConvArgs>& b, cudaStream_t s);
+void launch_syn_bwd_b(const Batch<SynArgs>& b, cudaStream_t s);
+void launch_up_adj_b(const Batch<UpAdjArgs>& b, int max_wt, cudaStream_t s);
+void launch_ifce_b(const Batch<IfceArgs>& b, cudaStream_t s);
+void launch_gather_b(const Batch<GatherArgs>& b, cudaStream_t s);
+void launch_reduce_b(const Batch<ReduceArgs>& b, cudaStream_t s);
+void launch_finish_b(const Batch<FinishArgs>& b, cudaStream_t s);
+void launch_mark_base_b(const Batch<FinishArgs>& b, cudaStream_t s);
+// workspace layout of one job (cc_api.cu); returns the bytes needed, fills *w when base != null
+size_t layout_job(const cc_arch_t* arch, int flags, char* base, Work* w);
+int device_setup_checked();
 
 // decoder
 void decode_init_tables();

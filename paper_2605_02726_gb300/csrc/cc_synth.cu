@@ -11,18 +11,11 @@ namespace {
 // the channels of grids m+1..6: channel 0 comes from y~^(m+1), channel j >= 1 from up[m+1][j-1].
 // Separable 4x4 polyphase taps with replicate (clamped) indices, cropped to the grid size.
 // ---------------------------------------------------------------------------------------------
-struct UpFwdArgs {
-    const float* src0;   // y~ of grid m+1
-    const float* srcup;  // up[m+1] (channels 1..), may be null when nch == 1
-    float* dst;          // up[m]
-    int hs, ws, ht, wt, nch;
-    const float* taps;   // 4 taps of this stage (device)
-};
 
-__global__ void k_up_fwd(UpFwdArgs a) {
+__device__ __forceinline__ void up_fwd_body(const UpFwdArgs& a, int cta, int ncta) {
     const int64_t total = (int64_t)a.nch * a.ht * a.wt;
     const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = cta * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)ncta * blockDim.x) {
         const int j = (int)(e / ((int64_t)a.ht * a.wt));
         const int rem = (int)(e - (int64_t)j * a.ht * a.wt);
         const int y = rem / a.wt, x = rem - y * a.wt;
@@ -42,6 +35,17 @@ __global__ void k_up_fwd(UpFwdArgs a) {
         }
         a.dst[e] = acc;
     }
+}
+__global__ void k_up_fwd(UpFwdArgs a) {
+    __shared__ UpFwdArgs sa;
+    param_fetch(a, sa);
+    up_fwd_body(sa, blockIdx.x, gridDim.x);
+}
+__global__ void k_up_fwd_b(Batch<UpFwdArgs> b) {
+    __shared__ UpFwdArgs sa;
+    const int j = batch_job(b.cta_begin, b.njobs);
+    batch_fetch(b.args, j, sa);
+    up_fwd_body(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
 }
 
 // Stage-1 upsampling of S_1 = [y~^(1), up[1]] at full-resolution pixel (y, x): z[1..6].
@@ -78,19 +82,6 @@ __device__ __forceinline__ void dense_latents(const Geom& g, const float* yt, co
 // ---------------------------------------------------------------------------------------------
 // Synthesis MLP forward: t = W2 gelu(W1 z + b1) + b2 + Ws z + bs.  One thread per pixel.
 // ---------------------------------------------------------------------------------------------
-struct SynArgs {
-    Geom g;
-    int64_t HW;
-    const float* yt;
-    const float* up1;
-    const float* params;
-    float* t;        // [3][HW]
-    const float* dt; // [3][HW]
-    float* act;      // [40][HW]
-    float* dYsyn0;   // grid-0 part of dYsyn [HW]
-    float* dz;       // [6][HW]
-    float* gpart;    // [gridDim.x][467]
-};
 
 // shared weight layout of the synthesis kernels
 constexpr int ss_w1 = 0;      // [40][8] (7 used, 8th = bias b1)
@@ -115,13 +106,13 @@ __device__ __forceinline__ void load_syn_weights(const float* P, float* sW) {
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(kSynThreads) k_syn_fwd(SynArgs a) {
+__device__ __forceinline__ void syn_fwd_body(const SynArgs& a, int cta, int ncta) {
     __shared__ __align__(16) float sW[ss_total];
     load_syn_weights(a.params, sW);
     const float tp[4] = {a.params[po::up], a.params[po::up + 1], a.params[po::up + 2], a.params[po::up + 3]};
     __syncthreads();
     const Geom& g = a.g;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.HW; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t p = cta * (int64_t)blockDim.x + threadIdx.x; p < a.HW; p += (int64_t)ncta * blockDim.x) {
         const int y = (int)(p / g.W), x = (int)(p - (int64_t)y * g.W);
         float z[kL];
         dense_latents(g, a.yt, a.up1, tp, y, x, z);
@@ -155,6 +146,19 @@ __global__ void __launch_bounds__(kSynThreads) k_syn_fwd(SynArgs a) {
         a.t[2 * a.HW + p] = t2;
     }
 }
+template <int PASS>
+__global__ void __launch_bounds__(kSynThreads) k_syn_fwd(SynArgs a) {
+    __shared__ SynArgs sa;
+    param_fetch(a, sa);
+    syn_fwd_body<PASS>(sa, blockIdx.x, gridDim.x);
+}
+template <int PASS>
+__global__ void __launch_bounds__(kSynThreads) k_syn_fwd_b(Batch<SynArgs> b) {
+    __shared__ SynArgs sa;
+    const int j = batch_job(b.cta_begin, b.njobs);
+    batch_fetch(b.args, j, sa);
+    syn_fwd_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
+}
 
 // ---------------------------------------------------------------------------------------------
 // Synthesis MLP adjoint, one thread per pixel, rounds of 128 pixels.  dz = W1^T da + Ws^T dt,
@@ -186,7 +190,7 @@ __device__ int syn_grad_index(int u, int v) {  // index relative to po::syn_w1, 
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd(SynArgs a) {
+__device__ __forceinline__ void syn_bwd_body(const SynArgs& a, int cta, int ncta) {
     extern __shared__ float4 smem4[];
     float* sW = reinterpret_cast<float*>(smem4);
     float* sU = sW + ss_total;
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd(SynArgs a) {
     const Geom& g = a.g;
     const int64_t HW = a.HW;
     const int64_t n_rounds = (HW + kSynThreads - 1) / kSynThreads;
-    for (int64_t rd = blockIdx.x; rd < n_rounds; rd += gridDim.x) {
+    for (int64_t rd = cta; rd < n_rounds; rd += ncta) {
         const int64_t p = rd * kSynThreads + tid;
         const bool valid = p < HW;
         const int64_t pc = valid ? p : HW - 1;
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd(SynArgs a) {
         }
         __syncthreads();
     }
-    float* gp = a.gpart + (int64_t)blockIdx.x * po::syn_block;
+    float* gp = a.gpart + (int64_t)cta * po::syn_block;
     for (int e = tid; e < kSBlocks * 64; e += kSynThreads) {
         const int blk = e >> 6, pq = e & 63;
         const int u = c_sblk_u[blk] + (pq >> 3), v = c_sblk_v[blk] + (pq & 7);
@@ -304,6 +308,19 @@ __global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd(SynArgs a) {
         if (u >= 40 && u < 43 && v == 7) gp[po::syn_b2 - po::syn_w1 + (u - 40)] = sum;
     }
 }
+template <int PASS>
+__global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd(SynArgs a) {
+    __shared__ SynArgs sa;
+    param_fetch(a, sa);
+    syn_bwd_body<PASS>(sa, blockIdx.x, gridDim.x);
+}
+template <int PASS>
+__global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd_b(Batch<SynArgs> b) {
+    __shared__ SynArgs sa;
+    const int j = batch_job(b.cta_begin, b.njobs);
+    batch_fetch(b.args, j, sa);
+    syn_bwd_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
+}
 
 // ---------------------------------------------------------------------------------------------
 // Upsampling adjoint, stage s: D = d up[s-1] (7-s channels at grid s-1) -> dS_s at grid s.
@@ -312,17 +329,6 @@ __global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd(SynArgs a) {
 //   the forward row-pass value.
 // Pass B (rows): dS[j][py][px] = sum_tau h_tau G'_tau over T; dh_tau += G'_tau * S[j][py][px].
 // ---------------------------------------------------------------------------------------------
-struct UpAdjArgs {
-    const float* D;      // [nch][ht][wt]
-    const float* src0;   // S_s channel 0 = y~ of grid s
-    const float* srcup;  // S_s channels 1.. = up[s]
-    float* T;            // [nch][hs][wt]
-    float* out0;         // dYsyn of grid s
-    float* outup;        // dup[s]
-    float* gpart;        // [gridDim.x][4]
-    int hs, ws, ht, wt, nch;
-    const float* taps;
-};
 
 // G[tau] for input index p along an axis with n_in inputs and n_out (cropped) outputs, reading
 // the output-side values through `get(o)`.
@@ -357,12 +363,12 @@ __device__ __forceinline__ void gather_taps(int p, int n_in, int n_out, F get, f
 
 // One CTA per (channel j, input row py) pair (grid-stride): pass A builds the row T[j][py][.]
 // in shared memory from the <= 8 output rows that read input row py, pass B gathers it along x.
-__global__ void __launch_bounds__(kUpThreads) k_up_adj(UpAdjArgs a) {
+__device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int ncta) {
     extern __shared__ float sTrow[];  // wt floats
     const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
     float dh[4] = {0.f, 0.f, 0.f, 0.f};
     const int npairs = a.nch * a.hs;
-    for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
+    for (int pair = cta; pair < npairs; pair += ncta) {
         const int j = pair / a.hs, py = pair - j * a.hs;
         const float* Dj = a.D + (int64_t)j * a.ht * a.wt;
         const float* S = (j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws) + (int64_t)py * a.ws;
@@ -398,7 +404,18 @@ __global__ void __launch_bounds__(kUpThreads) k_up_adj(UpAdjArgs a) {
     __shared__ float scratch[4 * (kUpThreads / 32)];
     block_sum<4>(dh, scratch);
     if (threadIdx.x == 0)
-        for (int q = 0; q < 4; ++q) a.gpart[blockIdx.x * 4 + q] = dh[q];
+        for (int q = 0; q < 4; ++q) a.gpart[cta * 4 + q] = dh[q];
+}
+__global__ void __launch_bounds__(kUpThreads) k_up_adj(UpAdjArgs a) {
+    __shared__ UpAdjArgs sa;
+    param_fetch(a, sa);
+    up_adj_body(sa, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kUpThreads) k_up_adj_b(Batch<UpAdjArgs> b) {
+    __shared__ UpAdjArgs sa;
+    const int j = batch_job(b.cta_begin, b.njobs);
+    batch_fetch(b.args, j, sa);
+    up_adj_body(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
 }
 
 int up_grid(int64_t total) {
@@ -416,30 +433,33 @@ size_t syn_bwd_smem_bytes() { return (size_t)(ss_total + 2 * 48 * kSLd + kSTasks
 
 void synth_init_attributes() {
     cudaFuncSetAttribute(k_up_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * (int)sizeof(float));
+    cudaFuncSetAttribute(k_up_adj_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * (int)sizeof(float));
     const int sm = (int)syn_bwd_smem_bytes();
     cudaFuncSetAttribute(k_syn_bwd<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_syn_bwd<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_syn_bwd_b<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_syn_bwd_b<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
-void launch_up_forward(const Work& w, const float* params, cudaStream_t s) {
+// ---- argument builders and CTA counts
+UpFwdArgs up_fwd_args(const Work& w, const float* params, int m) {  // stage s = m + 1 -> up[m]
     const Geom& g = w.g;
-    for (int m = kL - 2; m >= 1; --m) {  // stage s = m + 1
-        UpFwdArgs a;
-        a.src0 = w.yt + g.off[m + 1];
-        a.srcup = w.up[m + 1];
-        a.dst = w.up[m];
-        a.hs = g.h[m + 1];
-        a.ws = g.w[m + 1];
-        a.ht = g.h[m];
-        a.wt = g.w[m];
-        a.nch = kL - 1 - m;
-        a.taps = params + po::up + 4 * m;
-        const int64_t total = (int64_t)a.nch * a.ht * a.wt;
-        k_up_fwd<<<up_grid(total), kUpThreads, 0, s>>>(a);
-    }
+    UpFwdArgs a;
+    a.src0 = w.yt + g.off[m + 1];
+    a.srcup = w.up[m + 1];
+    a.dst = w.up[m];
+    a.taps = params + po::up + 4 * m;
+    a.hs = g.h[m + 1];
+    a.ws = g.w[m + 1];
+    a.ht = g.h[m];
+    a.wt = g.w[m];
+    a.nch = kL - 1 - m;
+    a.pad_ = 0;
+    return a;
 }
+int up_fwd_ctas(const Work& w, int m) { return up_grid((int64_t)(kL - 1 - m) * w.g.h[m] * w.g.w[m]); }
 
-static SynArgs syn_args(const Work& w, const float* params) {
+SynArgs syn_args(const Work& w, const float* params) {
     SynArgs a;
     a.g = w.g;
     a.HW = w.HW;
@@ -454,20 +474,45 @@ static SynArgs syn_args(const Work& w, const float* params) {
     a.gpart = w.gpart_syn;
     return a;
 }
+int syn_fwd_ctas(const Work& w) {
+    const int64_t blocks = (w.HW + kSynThreads - 1) / kSynThreads, cap = (int64_t)num_sms() * 16;
+    return (int)(blocks < cap ? blocks : cap);
+}
+
+UpAdjArgs up_adj_args(const Work& w, const float* params, int st) {  // stage st: grid st -> grid st-1
+    const Geom& g = w.g;
+    UpAdjArgs a;
+    a.D = st == 1 ? w.dz : w.dup[st - 1];
+    a.src0 = w.yt + g.off[st];
+    a.srcup = w.up[st];
+    a.out0 = w.dYsyn + g.off[st];
+    a.outup = w.dup[st];
+    a.gpart = w.gpart_up + (st - 1) * kUpMaxCta * 4;
+    a.taps = params + po::up + 4 * (st - 1);
+    a.hs = g.h[st];
+    a.ws = g.w[st];
+    a.ht = g.h[st - 1];
+    a.wt = g.w[st - 1];
+    a.nch = kL - st;
+    a.pad_ = 0;
+    return a;
+}
+
+// ---- single-job launches
+void launch_up_forward(const Work& w, const float* params, cudaStream_t s) {
+    for (int m = kL - 2; m >= 1; --m) k_up_fwd<<<up_fwd_ctas(w, m), kUpThreads, 0, s>>>(up_fwd_args(w, params, m));
+}
 
 void launch_syn_forward(const Work& w, const float* params, int pass, cudaStream_t s) {
-    SynArgs a = syn_args(w, params);
-    int64_t blocks = (w.HW + kSynThreads - 1) / kSynThreads;
-    const int64_t cap = (int64_t)num_sms() * 16;
-    if (blocks > cap) blocks = cap;
+    const SynArgs a = syn_args(w, params);
     if (pass == PASS_FWD_STORE)
-        k_syn_fwd<PASS_FWD_STORE><<<(int)blocks, kSynThreads, 0, s>>>(a);
+        k_syn_fwd<PASS_FWD_STORE><<<syn_fwd_ctas(w), kSynThreads, 0, s>>>(a);
     else
-        k_syn_fwd<PASS_FWD><<<(int)blocks, kSynThreads, 0, s>>>(a);
+        k_syn_fwd<PASS_FWD><<<syn_fwd_ctas(w), kSynThreads, 0, s>>>(a);
 }
 
 void launch_syn_backward(const Work& w, const float* params, int pass, cudaStream_t s) {
-    SynArgs a = syn_args(w, params);
+    const SynArgs a = syn_args(w, params);
     const size_t sm = syn_bwd_smem_bytes();
     if (pass == PASS_BWD_LOAD)
         k_syn_bwd<PASS_BWD_LOAD><<<w.n_cta_syn, kSynThreads, sm, s>>>(a);
@@ -476,24 +521,20 @@ void launch_syn_backward(const Work& w, const float* params, int pass, cudaStrea
 }
 
 void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
-    const Geom& g = w.g;
-    for (int st = 1; st < kL; ++st) {  // stage st: grid st -> grid st-1
-        UpAdjArgs a;
-        a.D = st == 1 ? w.dz : w.dup[st - 1];
-        a.src0 = w.yt + g.off[st];
-        a.srcup = w.up[st];
-        a.T = nullptr;
-        a.out0 = w.dYsyn + g.off[st];
-        a.outup = w.dup[st];
-        a.hs = g.h[st];
-        a.ws = g.w[st];
-        a.ht = g.h[st - 1];
-        a.wt = g.w[st - 1];
-        a.nch = kL - st;
-        a.taps = params + po::up + 4 * (st - 1);
-        a.gpart = w.gpart_up + (st - 1) * kUpMaxCta * 4;
-        k_up_adj<<<w.n_cta_up[st], kUpThreads, (size_t)a.wt * sizeof(float), s>>>(a);
-    }
+    for (int st = 1; st < kL; ++st)
+        k_up_adj<<<w.n_cta_up[st], kUpThreads, (size_t)w.g.w[st - 1] * sizeof(float), s>>>(up_adj_args(w, params, st));
+}
+
+// ---- multi-job launches (max_wt: the widest row any job's stage reads, for the shared row buffer)
+void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s) { k_up_fwd_b<<<b.total_ctas, kUpThreads, 0, s>>>(b); }
+void launch_syn_fwd_b(const Batch<SynArgs>& b, cudaStream_t s) {
+    k_syn_fwd_b<PASS_FWD><<<b.total_ctas, kSynThreads, 0, s>>>(b);
+}
+void launch_syn_bwd_b(const Batch<SynArgs>& b, cudaStream_t s) {
+    k_syn_bwd_b<PASS_FWD_BWD><<<b.total_ctas, kSynThreads, syn_bwd_smem_bytes(), s>>>(b);
+}
+void launch_up_adj_b(const Batch<UpAdjArgs>& b, int max_wt, cudaStream_t s) {
+    k_up_adj_b<<<b.total_ctas, kUpThreads, (size_t)max_wt * sizeof(float), s>>>(b);
 }
 
 }  // namespace cc

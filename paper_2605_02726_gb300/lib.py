@@ -42,6 +42,14 @@ class RD(ctypes.Structure):
     _fields_ = [("loss", ctypes.c_double), ("rate_bits", ctypes.c_double), ("mse", ctypes.c_double)]
 
 
+class Schedule(ctypes.Structure):
+    """Per kernel class, the fraction (0, 1] of each job's single-image CTA count used in a batch."""
+    _fields_ = [("arm", ctypes.c_float), ("syn", ctypes.c_float), ("conv", ctypes.c_float), ("other", ctypes.c_float)]
+
+    def as_tuple(self):
+        return (self.arm, self.syn, self.conv, self.other)
+
+
 class CoolChicError(RuntimeError):
     pass
 
@@ -64,6 +72,11 @@ def _load():
         "coolchic_rate_distortion": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, P(RD), vp, sz, vp]),
         "coolchic_decode_image": (i32, [P(Arch), vp, vp, vp, vp, vp, vp, vp, sz, vp]),
         "coolchic_rate_distortion_noalloc": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, P(RD), vp]),
+        "coolchic_batch_table_bytes": (sz, [i32, i32]),
+        "coolchic_batch_create": (i32, [i32, vp, vp, vp, vp, vp, vp, P(Schedule), i32, vp, sz, P(vp)]),
+        "coolchic_batch_step": (i32, [vp, i32, vp]),
+        "coolchic_batch_records": (vp, [vp]),
+        "coolchic_batch_destroy": (i32, [vp]),
         "coolchic_timing_enable": (i32, [i32, i32]),
         "coolchic_timing_collect": (i32, [P(ctypes.c_double), P(i64)]),
         "coolchic_timing_disable": (i32, []),
@@ -82,7 +95,8 @@ EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count
             "coolchic_workspace_bytes", "coolchic_encode_step", "coolchic_forward", "coolchic_backward",
             "coolchic_rate_distortion", "coolchic_decode_image", "coolchic_timing_enable", "coolchic_timing_collect",
             "coolchic_timing_disable", "coolchic_last_error", "coolchic_version",
-            "coolchic_rate_distortion_noalloc"]
+            "coolchic_rate_distortion_noalloc", "coolchic_batch_table_bytes", "coolchic_batch_create",
+            "coolchic_batch_step", "coolchic_batch_records", "coolchic_batch_destroy"]
 
 KERNEL_ARM, KERNEL_SYN_BWD, KERNEL_CONV, KERNEL_SYN_FWD = 0, 1, 2, 3
 
@@ -237,3 +251,68 @@ def decode_image(q_latents, params, *, H, W, ws, image_out=None, prob=None, mu_q
     _check(_lib.coolchic_decode_image(ctypes.byref(a), _ptr(q_latents), _ptr(params), _ptr(image_out), _ptr(prob),
                                       _ptr(mu_q), _ptr(logb_q), _ptr(ws), ws.numel(), _stream(stream)),
            "decode_image")
+
+
+class BatchEncoder:
+    """Encoder iterations of many images in one set of launches (coolchic_batch_*).
+
+    jobs: list of (image [3,H,W] CUDA float32, EncoderState, HParams).  Each job keeps its own
+    workspace; the plan table lives in a device buffer owned by this object.  `step(n)` is
+    asynchronous; `graph(n)` captures n iterations in a CUDA graph for replay."""
+
+    def __init__(self, jobs, schedule=None, rd_capacity=1, device=None):
+        self.jobs = list(jobs)
+        n = len(self.jobs)
+        if n == 0:
+            raise ValueError("empty batch")
+        self.shapes = [(int(img.shape[1]), int(img.shape[2])) for img, _, _ in self.jobs]
+        dev = device or self.jobs[0][0].device
+        self.workspaces = [workspace(H, W, device=dev) for H, W in self.shapes]
+        archs = (Arch * n)(*[arch(H, W) for H, W in self.shapes])
+        hps = (HParams * n)(*[hp for _, _, hp in self.jobs])
+        images = (ctypes.c_void_p * n)(*[img.data_ptr() for img, _, _ in self.jobs])
+        states = (State * n)(*[st.c_state() for _, st, _ in self.jobs])
+        wss = (ctypes.c_void_p * n)(*[w.data_ptr() for w in self.workspaces])
+        wsb = (ctypes.c_size_t * n)(*[w.numel() for w in self.workspaces])
+        tb = int(_lib.coolchic_batch_table_bytes(n, rd_capacity))
+        buf = torch.empty(tb + 256, dtype=torch.uint8, device=dev)
+        off = (-buf.data_ptr()) % 256
+        self.table = buf[off:off + tb]
+        self.rd_capacity = rd_capacity
+        self.schedule = schedule
+        handle = ctypes.c_void_p()
+        torch.cuda.synchronize(dev)
+        _check(_lib.coolchic_batch_create(n, archs, hps, images, states, wss, wsb,
+                                          ctypes.byref(schedule) if schedule is not None else None,
+                                          rd_capacity, ctypes.c_void_p(self.table.data_ptr()), tb,
+                                          ctypes.byref(handle)), "batch_create")
+        self.handle = handle
+
+    def step(self, n_iters=1, stream=None):
+        _check(_lib.coolchic_batch_step(self.handle, int(n_iters), _stream(stream)), "batch_step")
+
+    def records(self):
+        """float64 [rd_capacity, n_jobs, 3] view (loss, rate_bits, mse) of the last step call."""
+        ptr = _lib.coolchic_batch_records(self.handle)
+        off = ptr - self.table.data_ptr()
+        n = len(self.jobs)
+        return self.table[off:off + self.rd_capacity * n * 24].view(torch.float64).view(self.rd_capacity, n, 3)
+
+    def graph(self, n_iters=1):
+        s = torch.cuda.Stream(device=self.table.device)
+        s.wait_stream(torch.cuda.current_stream(self.table.device))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.step(n_iters, stream=s)
+        return g
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.coolchic_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -93,7 +93,14 @@ __device__ __forceinline__ void batch_fetch(const A* __restrict__ args, int j, A
 // results whether an image runs alone or in a batch).
 template <typename A>
 __device__ __forceinline__ void param_fetch(const A& a, A& sa) {
-    if (threadIdx.x == 0) sa = a;
+    static_assert(sizeof(A) % 4 == 0, "argument structs are copied as 32-bit words");
+    constexpr int NW = (int)(sizeof(A) / 4);
+    const int* src = reinterpret_cast<const int*>(&a);
+    int* dst = reinterpret_cast<int*>(&sa);
+    // word w goes through lane w % 32 of the first warp; constant indices keep `a` in param space
+#pragma unroll
+    for (int w = 0; w < NW; ++w)
+        if ((int)threadIdx.x == (w & 31)) dst[w] = src[w];
     __syncthreads();
 }
 

@@ -260,14 +260,15 @@ class BatchEncoder:
     workspace; the plan table lives in a device buffer owned by this object.  `step(n)` is
     asynchronous; `graph(n)` captures n iterations in a CUDA graph for replay."""
 
-    def __init__(self, jobs, schedule=None, rd_capacity=1, device=None):
+    def __init__(self, jobs, schedule=None, rd_capacity=1, device=None, workspaces=None):
         self.jobs = list(jobs)
         n = len(self.jobs)
         if n == 0:
             raise ValueError("empty batch")
         self.shapes = [(int(img.shape[1]), int(img.shape[2])) for img, _, _ in self.jobs]
         dev = device or self.jobs[0][0].device
-        self.workspaces = [workspace(H, W, device=dev) for H, W in self.shapes]
+        self.workspaces = list(workspaces) if workspaces is not None else [workspace(H, W, device=dev)
+                                                                           for H, W in self.shapes]
         archs = (Arch * n)(*[arch(H, W) for H, W in self.shapes])
         hps = (HParams * n)(*[hp for _, _, hp in self.jobs])
         images = (ctypes.c_void_p * n)(*[img.data_ptr() for img, _, _ in self.jobs])

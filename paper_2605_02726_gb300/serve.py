@@ -1,0 +1,218 @@
+"""Continuous-batching encode server.
+
+Encode requests (an image, lambda, a seed, an iteration budget) arrive over time.  A request is
+admitted when its device memory (image, latents, parameters, Adam state, workspace) fits in the
+HBM budget next to the jobs already running; admitted jobs stay resident on the device and advance
+together: every tick runs `tick_iters` encoder iterations of all active jobs through the batched
+launches (one launch per kernel for the whole set).  A job leaves when it has done its iterations
+(its final state and loss are copied to the host) or is cancelled; its memory is released and the
+next queued requests are admitted at the following tick.  Each job's trajectory is the one it
+would have alone: jobs never share state, and a job's kernels see only its own buffers.
+
+`python -m paper_2605_02726_gb300.serve` runs the Poisson-arrival benchmark (rates 2, 8, 32
+requests/s; sizes 512x768, 1024x1024, 2048x1365, 2048x2048 weighted .4/.3/.2/.1; lambda in
+{1e-4, 1e-3, 1e-2}; 5000 iterations per request; 80 GB budget) and prints one JSON line per rate
+with p50/p99 latency and images/s.
+"""
+from __future__ import annotations
+
+import argparse
+import collections
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import inputs
+from . import lib as cc
+
+
+def job_bytes(H: int, W: int) -> int:
+    """Device bytes a resident job holds: image, state (latents, params, Adam moments, step),
+    and its workspace."""
+    n = cc.latent_count(H, W)
+    ws = int(cc._lib.coolchic_workspace_bytes(__import__("ctypes").byref(cc.arch(H, W)), 0))
+    return 4 * 3 * H * W + 4 * 3 * n + 4 * 3 * cc.N_PARAMS + 8 + ws + 512
+
+
+Request = collections.namedtuple("Request", "rid arrival H W lam seed iters image")
+
+
+class Job:
+    def __init__(self, req: Request, device):
+        self.req = req
+        self.image = req.image.to(device, non_blocking=True) if req.image.device.type != "cuda" else req.image
+        lat, par = inputs.initial_state(req.H, req.W, seed=req.seed + 1)
+        self.state = cc.EncoderState(torch.tensor(lat, device=device), torch.tensor(par, device=device))
+        self.hp = cc.hparams(lam=req.lam, seed=req.seed)
+        self.ws = cc.workspace(req.H, req.W, device=device)
+        self.done_iters = 0
+        self.bytes = job_bytes(req.H, req.W)
+        self.admitted = None
+        self.finished = None
+        self.last_rd = None
+
+
+class EncodeServer:
+    def __init__(self, hbm_budget: int, tick_iters: int = 50, schedule=None, device="cuda"):
+        self.budget = int(hbm_budget)
+        self.tick_iters = int(tick_iters)
+        self.schedule = schedule
+        self.device = torch.device(device)
+        self.queue: collections.deque = collections.deque()
+        self.active: list[Job] = []
+        self.done: dict[int, Job] = {}
+        self.failed: dict[int, str] = {}
+        self.in_use = 0
+        self.peak_in_use = 0
+        self.batch = None
+        self.batch_key = None
+        self.ticks = 0
+        self._next = 0
+
+    # -- request intake -----------------------------------------------------------------------
+    def submit(self, image, lam: float, seed: int, iters: int, arrival: float | None = None) -> int:
+        """Queue a request; malformed ones are rejected at once (recorded in `failed`)."""
+        rid = self._next
+        self._next += 1
+        arrival = time.perf_counter() if arrival is None else arrival
+        img = torch.as_tensor(image)
+        if img.dim() != 3 or img.shape[0] != 3 or not (1 <= img.shape[1] <= 16384 and 1 <= img.shape[2] <= 16384):
+            self.failed[rid] = "malformed image shape"
+            return rid
+        if not (math.isfinite(lam) and lam >= 0.0) or iters < 1:
+            self.failed[rid] = "invalid lambda or iteration count"
+            return rid
+        H, W = int(img.shape[1]), int(img.shape[2])
+        if job_bytes(H, W) > self.budget:
+            self.failed[rid] = "larger than the whole HBM budget"
+            return rid
+        self.queue.append(Request(rid, arrival, H, W, float(lam), int(seed), int(iters), img.float().contiguous()))
+        return rid
+
+    def cancel(self, rid: int) -> bool:
+        for q in list(self.queue):
+            if q.rid == rid:
+                self.queue.remove(q)
+                self.failed[rid] = "cancelled"
+                return True
+        for j in self.active:
+            if j.req.rid == rid:
+                self._release(j)
+                self.failed[rid] = "cancelled"
+                return True
+        return False
+
+    # -- scheduling ---------------------------------------------------------------------------
+    def _release(self, job: Job):
+        self.active.remove(job)
+        self.in_use -= job.bytes
+
+    def _admit(self, now: float):
+        while self.queue and self.queue[0].arrival <= now:
+            need = job_bytes(self.queue[0].H, self.queue[0].W)
+            if self.in_use + need > self.budget:
+                break  # FIFO: wait for memory
+            req = self.queue.popleft()
+            job = Job(req, self.device)
+            job.admitted = now
+            self.active.append(job)
+            self.in_use += job.bytes
+            self.peak_in_use = max(self.peak_in_use, self.in_use)
+
+    def _plan(self):
+        key = tuple(j.req.rid for j in self.active)
+        if key != self.batch_key:
+            if self.batch is not None:
+                self.batch.close()
+            jobs = [(j.image, j.state, j.hp) for j in self.active]
+            self.batch = cc.BatchEncoder(jobs, schedule=self.schedule, rd_capacity=self.tick_iters,
+                                         workspaces=[j.ws for j in self.active])
+            self.batch_key = key
+        return self.batch
+
+    def tick(self, now: float) -> int:
+        """Admit what fits, run one tick of iterations on all active jobs, retire finished ones.
+        Returns the number of iterations run (0 when idle)."""
+        self._admit(now)
+        if not self.active:
+            return 0
+        n = min(self.tick_iters, min(j.req.iters - j.done_iters for j in self.active))
+        b = self._plan()
+        b.step(n)
+        torch.cuda.synchronize(self.device)
+        rec = b.records()
+        t_end = time.perf_counter()
+        for q, j in enumerate(list(self.active)):
+            j.done_iters += n
+            if j.done_iters >= j.req.iters:
+                j.last_rd = rec[n - 1, q].cpu().numpy()
+                j.final = (j.state.latents.cpu(), j.state.params.cpu())
+                j.finished = t_end
+                self.done[j.req.rid] = j
+                self._release(j)
+        self.ticks += 1
+        return n
+
+    def run(self, requests, t0: float | None = None, max_seconds: float | None = None):
+        """Serve (arrival_offset_s, image, lam, seed, iters) requests in real time."""
+        t0 = time.perf_counter() if t0 is None else t0
+        pending = sorted(requests, key=lambda r: r[0])
+        k = 0
+        while k < len(pending) or self.queue or self.active:
+            now = time.perf_counter()
+            while k < len(pending) and t0 + pending[k][0] <= now:
+                off, img, lam, seed, iters = pending[k]
+                self.submit(img, lam, seed, iters, arrival=t0 + off)
+                k += 1
+            ran = self.tick(now)
+            if ran == 0 and not self.active:
+                if k < len(pending):
+                    time.sleep(max(0.0, min(0.01, t0 + pending[k][0] - time.perf_counter())))
+                elif self.queue:
+                    continue
+            if max_seconds is not None and time.perf_counter() - t0 > max_seconds:
+                break
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+
+    def latencies(self):
+        return {rid: j.finished - j.req.arrival for rid, j in self.done.items()}
+
+
+def benchmark(rates=(2.0, 8.0, 32.0), n_requests=6, iters=5000, budget_gb=80.0, tick_iters=50, seed0=inputs.SEED0):
+    out = []
+    for rate in rates:
+        reqs = []
+        for q, (t, (H, W), lam) in enumerate(inputs.serve_requests(rate, n_requests, seed0)):
+            img = torch.tensor(inputs.image(H, W, seed=seed0 + 1000 + q, texture_sigma=0.02))
+            reqs.append((t, img, lam, seed0 + 7 * q, iters))
+        srv = EncodeServer(int(budget_gb * 2 ** 30), tick_iters=tick_iters)
+        t0 = time.perf_counter()
+        srv.run(reqs, t0=t0)
+        wall = time.perf_counter() - t0
+        lat = np.array(sorted(srv.latencies().values()))
+        pix = sum(r[1].shape[1] * r[1].shape[2] for r in reqs)
+        out.append({
+            "rate_offered_per_s": rate, "requests": n_requests, "iters_per_request": iters,
+            "served": len(srv.done), "images_per_s": len(srv.done) / wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mpix_iter_per_s": pix * iters / wall / 1e6, "wall_s": wall, "ticks": srv.ticks,
+            "peak_hbm_gb": srv.peak_in_use / 2 ** 30, "budget_gb": budget_gb,
+        })
+    return out
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--rates", default="2,8,32")
+    ap.add_argument("--requests", type=int, default=6)
+    ap.add_argument("--iters", type=int, default=5000)
+    ap.add_argument("--budget-gb", type=float, default=80.0)
+    ap.add_argument("--tick-iters", type=int, default=50)
+    a = ap.parse_args()
+    for line in benchmark(tuple(float(r) for r in a.rates.split(",")), a.requests, a.iters, a.budget_gb, a.tick_iters):
+        print(json.dumps(line), flush=True)

@@ -108,7 +108,7 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     W.n_cta_arm = arm_grid(W.N);
     {
         int64_t rounds = (W.HW + kSynThreads - 1) / kSynThreads;
-        W.n_cta_syn = (int)(rounds < 2 * sms ? rounds : 2 * sms);
+        W.n_cta_syn = (int)(rounds < 3 * sms ? rounds : 3 * sms);  // 3 resident CTAs per SM
         int64_t tiles = conv_tiles(a->H, a->W);
         W.n_cta_conv = (int)(tiles < 2 * sms ? tiles : 2 * sms);
     }

@@ -164,9 +164,34 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // GELU, exact erf form, and its derivative.
-__device__ __forceinline__ float gelu_f(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float a) {
-    return 0.5f * (1.f + erff(a * 0.70710678118654752f)) + a * 0.39894228040143268f * expf(-0.5f * a * a);
+// GELU with the exact (erf) Gaussian CDF, Phi(a) = (1 + erf(a / sqrt 2)) / 2, through the rational
+// approximation of Abramowitz & Stegun formula 7.1.26 (Hastings):
+//   erfc(x) = (a1 s + a2 s^2 + a3 s^3 + a4 s^4 + a5 s^5) exp(-x^2),  s = 1 / (1 + p x),  x >= 0,
+// absolute error <= 1.5e-7 over the whole line.  Phi(-|a|) = erfc(|a| / sqrt 2) / 2 is taken
+// straight from the product (no cancellation in the lower tail), Phi(|a|) = 1 - Phi(-|a|), and
+// exp(-a^2 / 2) is shared with the derivative gelu'(a) = Phi(a) + a exp(-a^2 / 2) / sqrt(2 pi).
+__device__ __forceinline__ float gelu_lower_tail(float a, float& ex) {  // Phi(-|a|); ex = exp(-a^2/2)
+    const float x = fabsf(a) * 0.70710678118654752f;
+    const float s = __fdividef(1.f, fmaf(0.3275911f, x, 1.f));
+    float q = fmaf(1.061405429f, s, -1.453152027f);
+    q = fmaf(q, s, 1.421413741f);
+    q = fmaf(q, s, -0.284496736f);
+    q = fmaf(q, s, 0.254829592f);
+    ex = __expf(-x * x);
+    return 0.5f * (q * s) * ex;
+}
+__device__ __forceinline__ float gelu_f(float a) {
+    float ex;
+    const float lt = gelu_lower_tail(a, ex);
+    return a * (a < 0.f ? lt : 1.f - lt);
+}
+// gelu(a) and gelu'(a) together
+__device__ __forceinline__ void gelu_fg(float a, float& g, float& dg) {
+    float ex;
+    const float lt = gelu_lower_tail(a, ex);
+    const float phi = a < 0.f ? lt : 1.f - lt;
+    g = a * phi;
+    dg = fmaf(a * 0.39894228040143268f, ex, phi);
 }
 
 // Polyphase taps of the x2 upsampler (Sec. III-B): output position o reads 4 inputs at

@@ -255,11 +255,11 @@ void launch_mark_base(const Work& w, const int64_t* step_dev, cudaStream_t s);
 // sizes that the workspace layout depends on
 size_t arm_smem_bytes(int pass);
 int arm_grid(int64_t N);
-size_t syn_bwd_smem_bytes();
 int conv_tiles(int H, int W);
 int up_adj_grid(int64_t pairs);
 void arm_init_attributes();
 void synth_init_attributes();
+void syn_init_attributes();
 
 // argument builders, CTA counts and multi-job launches (batched encode)
 RelaxArgs relax_args(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, uint64_t seed,

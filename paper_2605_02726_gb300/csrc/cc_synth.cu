@@ -1,6 +1,6 @@
-// Reconstruction side of the encoder step: upsampling cascade (Sec. III-B, Eq. 7), synthesis
-// 1x1 MLP with stabilizer (Eq. 8, Eq. 9), two residual 3x3 convolutions, distortion (Eq. 10) and
-// the adjoint of each.  Every parameter-gradient sum is reduced per CTA in a fixed order.
+// Upsampling cascade of the encoder step (Sec. III-B, Eq. 7), stages 6..2 forward, and the
+// adjoint of every stage with the tap gradients (per-CTA partials, reduced in a fixed order).
+// Stage 1 forward is fused into the synthesis kernels (cc_syn.cu).
 #include "cc_kernels.h"
 
 namespace cc {
@@ -46,280 +46,6 @@ __global__ void k_up_fwd_b(Batch<UpFwdArgs> b) {
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
     up_fwd_body(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
-}
-
-// Stage-1 upsampling of S_1 = [y~^(1), up[1]] at full-resolution pixel (y, x): z[1..6].
-__device__ __forceinline__ void dense_latents(const Geom& g, const float* yt, const float* up1,
-                                              const float (&tp)[4], int y, int x, float (&z)[kL]) {
-    const int hs = g.h[1], ws = g.w[1];
-    z[0] = __ldg(yt + (int64_t)y * g.W + x);
-    const int fy = poly_first(y), fx = poly_first(x);
-    int ro[4], co[4];
-    float wy[4], wx[4];
-    poly_w(y, tp, wy);
-    poly_w(x, tp, wx);
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        ro[p] = clampi(fy + p, 0, hs - 1) * ws;
-        co[p] = clampi(fx + p, 0, ws - 1);
-    }
-    const int64_t n1 = (int64_t)hs * ws;
-#pragma unroll
-    for (int j = 1; j < kL; ++j) {
-        const float* S = j == 1 ? yt + g.off[1] : up1 + (int64_t)(j - 2) * n1;
-        float acc = 0.f;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            float rs = 0.f;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) rs = fmaf(wx[q], __ldg(S + ro[p] + co[q]), rs);
-            acc = fmaf(wy[p], rs, acc);
-        }
-        z[j] = acc;
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
-// Synthesis MLP forward: t = W2 gelu(W1 z + b1) + b2 + Ws z + bs.  One thread per pixel.
-// ---------------------------------------------------------------------------------------------
-
-// shared weight layout of the synthesis kernels
-constexpr int ss_w1 = 0;      // [40][8] (7 used, 8th = bias b1)
-constexpr int ss_w2 = 320;    // [3][40]
-constexpr int ss_ws = 440;    // [3][8]  (7 used, 8th = b2 + bs)
-constexpr int ss_total = 464;
-
-__device__ __forceinline__ void load_syn_weights(const float* P, float* sW) {
-    for (int j = threadIdx.x; j < ss_total; j += blockDim.x) {
-        float v;
-        if (j < ss_w2) {
-            const int o = j >> 3, i = j & 7;
-            v = i < 7 ? P[po::syn_w1 + o * 7 + i] : P[po::syn_b1 + o];
-        } else if (j < ss_ws) {
-            v = P[po::syn_w2 + (j - ss_w2)];
-        } else {
-            const int o = (j - ss_ws) >> 3, i = (j - ss_ws) & 7;
-            v = i < 7 ? P[po::syn_ws + o * 7 + i] : P[po::syn_b2 + o] + P[po::syn_bs + o];
-        }
-        sW[j] = v;
-    }
-}
-
-template <int PASS>
-__device__ __forceinline__ void syn_fwd_body(const SynArgs& a, int cta, int ncta) {
-    __shared__ __align__(16) float sW[ss_total];
-    load_syn_weights(a.params, sW);
-    const float tp[4] = {a.params[po::up], a.params[po::up + 1], a.params[po::up + 2], a.params[po::up + 3]};
-    __syncthreads();
-    const Geom& g = a.g;
-    for (int64_t p = cta * (int64_t)blockDim.x + threadIdx.x; p < a.HW; p += (int64_t)ncta * blockDim.x) {
-        const int y = (int)(p / g.W), x = (int)(p - (int64_t)y * g.W);
-        float z[kL];
-        dense_latents(g, a.yt, a.up1, tp, y, x, z);
-        float t0 = sW[ss_ws + 7], t1 = sW[ss_ws + 15], t2 = sW[ss_ws + 23];
-#pragma unroll
-        for (int i = 0; i < kL; ++i) {
-            t0 = fmaf(sW[ss_ws + i], z[i], t0);
-            t1 = fmaf(sW[ss_ws + 8 + i], z[i], t1);
-            t2 = fmaf(sW[ss_ws + 16 + i], z[i], t2);
-        }
-#pragma unroll 4
-        for (int o = 0; o < kSH; ++o) {
-            const float4 w0 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8);
-            const float4 w1 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8 + 4);
-            float acc = w1.w;
-            acc = fmaf(w0.x, z[0], acc);
-            acc = fmaf(w0.y, z[1], acc);
-            acc = fmaf(w0.z, z[2], acc);
-            acc = fmaf(w0.w, z[3], acc);
-            acc = fmaf(w1.x, z[4], acc);
-            acc = fmaf(w1.y, z[5], acc);
-            acc = fmaf(w1.z, z[6], acc);
-            if (PASS == PASS_FWD_STORE) a.act[(int64_t)o * a.HW + p] = acc;
-            const float h = gelu_f(acc);
-            t0 = fmaf(sW[ss_w2 + o], h, t0);
-            t1 = fmaf(sW[ss_w2 + kSH + o], h, t1);
-            t2 = fmaf(sW[ss_w2 + 2 * kSH + o], h, t2);
-        }
-        a.t[p] = t0;
-        a.t[a.HW + p] = t1;
-        a.t[2 * a.HW + p] = t2;
-    }
-}
-template <int PASS>
-__global__ void __launch_bounds__(kSynThreads) k_syn_fwd(SynArgs a) {
-    __shared__ SynArgs sa;
-    param_fetch(a, sa);
-    syn_fwd_body<PASS>(sa, blockIdx.x, gridDim.x);
-}
-template <int PASS>
-__global__ void __launch_bounds__(kSynThreads) k_syn_fwd_b(Batch<SynArgs> b) {
-    __shared__ SynArgs sa;
-    const int j = batch_job(b.cta_begin, b.njobs);
-    batch_fetch(b.args, j, sa);
-    syn_fwd_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
-}
-
-// ---------------------------------------------------------------------------------------------
-// Synthesis MLP adjoint, one thread per pixel, rounds of 128 pixels.  dz = W1^T da + Ws^T dt,
-// da = (W2^T dt) * gelu'(a).  Parameter gradients as staged outer products:
-//   U rows: da 0-39, dt 40-42, zero 43-47;   V rows: z 0-6, one 7, g 8-47.
-//   blocks (U0, V0): da x [z, 1] -> (0..32 step 8, 0);  dt x [z, 1] -> (40, 0);  dt x g -> (40, 8..40).
-// ---------------------------------------------------------------------------------------------
-constexpr int kSLd = kSynThreads + 4;
-constexpr int kSBlocks = 11;
-constexpr int kSChunks = 11;
-constexpr int kSTasks = kSBlocks * kSChunks;  // 121
-__constant__ unsigned char c_sblk_u[kSBlocks] = {0, 8, 16, 24, 32, 40, 40, 40, 40, 40, 40};
-__constant__ unsigned char c_sblk_v[kSBlocks] = {0, 0, 0, 0, 0, 0, 8, 16, 24, 32, 40};
-__constant__ unsigned char c_schunk[kSChunks + 1] = {0, 12, 24, 36, 48, 60, 72, 84, 96, 108, 120, 128};
-
-__device__ int syn_grad_index(int u, int v) {  // index relative to po::syn_w1, or -1
-    if (u < 40) {
-        if (v < 7) return (po::syn_w1 - po::syn_w1) + u * 7 + v;
-        if (v == 7) return (po::syn_b1 - po::syn_w1) + u;
-        return -1;
-    }
-    if (u < 43) {
-        const int o = u - 40;
-        if (v < 7) return (po::syn_ws - po::syn_w1) + o * 7 + v;
-        if (v == 7) return (po::syn_bs - po::syn_w1) + o;  // b2 takes the same sum
-        if (v < 48) return (po::syn_w2 - po::syn_w1) + o * kSH + (v - 8);
-    }
-    return -1;
-}
-
-template <int PASS>
-__device__ __forceinline__ void syn_bwd_body(const SynArgs& a, int cta, int ncta) {
-    extern __shared__ float4 smem4[];
-    float* sW = reinterpret_cast<float*>(smem4);
-    float* sU = sW + ss_total;
-    float* sV = sU + 48 * kSLd;
-    float* sAcc = sV + 48 * kSLd;
-    load_syn_weights(a.params, sW);
-    const float tp[4] = {a.params[po::up], a.params[po::up + 1], a.params[po::up + 2], a.params[po::up + 3]};
-    const int tid = threadIdx.x;
-    for (int j = tid; j < kSTasks * 64; j += kSynThreads) sAcc[j] = 0.f;
-    for (int j = tid; j < kSLd; j += kSynThreads) {
-        for (int r = 43; r < 48; ++r) sU[r * kSLd + j] = 0.f;
-        sV[7 * kSLd + j] = 1.f;
-    }
-    __syncthreads();
-    const Geom& g = a.g;
-    const int64_t HW = a.HW;
-    const int64_t n_rounds = (HW + kSynThreads - 1) / kSynThreads;
-    for (int64_t rd = cta; rd < n_rounds; rd += ncta) {
-        const int64_t p = rd * kSynThreads + tid;
-        const bool valid = p < HW;
-        const int64_t pc = valid ? p : HW - 1;
-        const int y = (int)(pc / g.W), x = (int)(pc - (int64_t)y * g.W);
-        float z[kL];
-        dense_latents(g, a.yt, a.up1, tp, y, x, z);
-        const float m = valid ? 1.f : 0.f;
-        const float dt0 = a.dt[pc] * m, dt1 = a.dt[HW + pc] * m, dt2 = a.dt[2 * HW + pc] * m;
-        float dz[kL];
-#pragma unroll
-        for (int i = 0; i < kL; ++i)
-            dz[i] = sW[ss_ws + i] * dt0 + sW[ss_ws + 8 + i] * dt1 + sW[ss_ws + 16 + i] * dt2;
-#pragma unroll 4
-        for (int o = 0; o < kSH; ++o) {
-            const float4 w0 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8);
-            const float4 w1 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8 + 4);
-            float acc;
-            if (PASS == PASS_BWD_LOAD) {
-                acc = a.act[(int64_t)o * HW + pc];
-            } else {
-                acc = w1.w;
-                acc = fmaf(w0.x, z[0], acc);
-                acc = fmaf(w0.y, z[1], acc);
-                acc = fmaf(w0.z, z[2], acc);
-                acc = fmaf(w0.w, z[3], acc);
-                acc = fmaf(w1.x, z[4], acc);
-                acc = fmaf(w1.y, z[5], acc);
-                acc = fmaf(w1.z, z[6], acc);
-            }
-            const float dg = sW[ss_w2 + o] * dt0 + sW[ss_w2 + kSH + o] * dt1 + sW[ss_w2 + 2 * kSH + o] * dt2;
-            const float da = dg * gelu_grad_f(acc);
-            sU[o * kSLd + tid] = da;
-            sV[(8 + o) * kSLd + tid] = gelu_f(acc) * m;
-            dz[0] = fmaf(w0.x, da, dz[0]);
-            dz[1] = fmaf(w0.y, da, dz[1]);
-            dz[2] = fmaf(w0.z, da, dz[2]);
-            dz[3] = fmaf(w0.w, da, dz[3]);
-            dz[4] = fmaf(w1.x, da, dz[4]);
-            dz[5] = fmaf(w1.y, da, dz[5]);
-            dz[6] = fmaf(w1.z, da, dz[6]);
-        }
-        sU[40 * kSLd + tid] = dt0;
-        sU[41 * kSLd + tid] = dt1;
-        sU[42 * kSLd + tid] = dt2;
-#pragma unroll
-        for (int i = 0; i < kL; ++i) sV[i * kSLd + tid] = z[i] * m;
-        if (valid) {
-            a.dYsyn0[p] = dz[0];
-#pragma unroll
-            for (int j = 1; j < kL; ++j) a.dz[(int64_t)(j - 1) * HW + p] = dz[j];
-        }
-        __syncthreads();
-        if (tid < kSTasks) {
-            const int blk = tid / kSChunks, ch = tid - blk * kSChunks;
-            const float* U = sU + c_sblk_u[blk] * kSLd;
-            const float* V = sV + c_sblk_v[blk] * kSLd;
-            float acc[8][8];
-            float* A = sAcc + tid * 64;
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = A[i * 8 + j];
-            for (int l = c_schunk[ch]; l < c_schunk[ch + 1]; l += 4) {
-                float4 u[8], v[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) u[i] = *reinterpret_cast<const float4*>(U + i * kSLd + l);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = *reinterpret_cast<const float4*>(V + j * kSLd + l);
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float s = acc[i][j];
-                        s = fmaf(u[i].x, v[j].x, s);
-                        s = fmaf(u[i].y, v[j].y, s);
-                        s = fmaf(u[i].z, v[j].z, s);
-                        s = fmaf(u[i].w, v[j].w, s);
-                        acc[i][j] = s;
-                    }
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) A[i * 8 + j] = acc[i][j];
-        }
-        __syncthreads();
-    }
-    float* gp = a.gpart + (int64_t)cta * po::syn_block;
-    for (int e = tid; e < kSBlocks * 64; e += kSynThreads) {
-        const int blk = e >> 6, pq = e & 63;
-        const int u = c_sblk_u[blk] + (pq >> 3), v = c_sblk_v[blk] + (pq & 7);
-        const int idx = syn_grad_index(u, v);
-        if (idx < 0) continue;
-        float sum = 0.f;
-        for (int ch = 0; ch < kSChunks; ++ch) sum += sAcc[(blk * kSChunks + ch) * 64 + pq];
-        gp[idx] = sum;
-        if (u >= 40 && u < 43 && v == 7) gp[po::syn_b2 - po::syn_w1 + (u - 40)] = sum;
-    }
-}
-template <int PASS>
-__global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd(SynArgs a) {
-    __shared__ SynArgs sa;
-    param_fetch(a, sa);
-    syn_bwd_body<PASS>(sa, blockIdx.x, gridDim.x);
-}
-template <int PASS>
-__global__ void __launch_bounds__(kSynThreads, 2) k_syn_bwd_b(Batch<SynArgs> b) {
-    __shared__ SynArgs sa;
-    const int j = batch_job(b.cta_begin, b.njobs);
-    batch_fetch(b.args, j, sa);
-    syn_bwd_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -428,17 +154,10 @@ int up_grid(int64_t total) {
 
 int up_adj_grid(int64_t pairs) { return (int)(pairs < kUpMaxCta ? (pairs < 1 ? 1 : pairs) : kUpMaxCta); }
 
-size_t syn_bwd_smem_bytes() { return (size_t)(ss_total + 2 * 48 * kSLd + kSTasks * 64) * sizeof(float); }
-
-
 void synth_init_attributes() {
     cudaFuncSetAttribute(k_up_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * (int)sizeof(float));
     cudaFuncSetAttribute(k_up_adj_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * (int)sizeof(float));
-    const int sm = (int)syn_bwd_smem_bytes();
-    cudaFuncSetAttribute(k_syn_bwd<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_syn_bwd<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_syn_bwd_b<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_syn_bwd_b<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    syn_init_attributes();
 }
 
 // ---- argument builders and CTA counts
@@ -458,26 +177,6 @@ UpFwdArgs up_fwd_args(const Work& w, const float* params, int m) {  // stage s =
     return a;
 }
 int up_fwd_ctas(const Work& w, int m) { return up_grid((int64_t)(kL - 1 - m) * w.g.h[m] * w.g.w[m]); }
-
-SynArgs syn_args(const Work& w, const float* params) {
-    SynArgs a;
-    a.g = w.g;
-    a.HW = w.HW;
-    a.yt = w.yt;
-    a.up1 = w.up[1];
-    a.params = params;
-    a.t = w.t;
-    a.dt = w.dt;
-    a.act = w.act_syn;
-    a.dYsyn0 = w.dYsyn;
-    a.dz = w.dz;
-    a.gpart = w.gpart_syn;
-    return a;
-}
-int syn_fwd_ctas(const Work& w) {
-    const int64_t blocks = (w.HW + kSynThreads - 1) / kSynThreads, cap = (int64_t)num_sms() * 16;
-    return (int)(blocks < cap ? blocks : cap);
-}
 
 UpAdjArgs up_adj_args(const Work& w, const float* params, int st) {  // stage st: grid st -> grid st-1
     const Geom& g = w.g;
@@ -503,23 +202,6 @@ void launch_up_forward(const Work& w, const float* params, cudaStream_t s) {
     for (int m = kL - 2; m >= 1; --m) k_up_fwd<<<up_fwd_ctas(w, m), kUpThreads, 0, s>>>(up_fwd_args(w, params, m));
 }
 
-void launch_syn_forward(const Work& w, const float* params, int pass, cudaStream_t s) {
-    const SynArgs a = syn_args(w, params);
-    if (pass == PASS_FWD_STORE)
-        k_syn_fwd<PASS_FWD_STORE><<<syn_fwd_ctas(w), kSynThreads, 0, s>>>(a);
-    else
-        k_syn_fwd<PASS_FWD><<<syn_fwd_ctas(w), kSynThreads, 0, s>>>(a);
-}
-
-void launch_syn_backward(const Work& w, const float* params, int pass, cudaStream_t s) {
-    const SynArgs a = syn_args(w, params);
-    const size_t sm = syn_bwd_smem_bytes();
-    if (pass == PASS_BWD_LOAD)
-        k_syn_bwd<PASS_BWD_LOAD><<<w.n_cta_syn, kSynThreads, sm, s>>>(a);
-    else
-        k_syn_bwd<PASS_FWD_BWD><<<w.n_cta_syn, kSynThreads, sm, s>>>(a);
-}
-
 void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
     for (int st = 1; st < kL; ++st)
         k_up_adj<<<w.n_cta_up[st], kUpThreads, (size_t)w.g.w[st - 1] * sizeof(float), s>>>(up_adj_args(w, params, st));
@@ -527,12 +209,6 @@ void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
 
 // ---- multi-job launches (max_wt: the widest row any job's stage reads, for the shared row buffer)
 void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s) { k_up_fwd_b<<<b.total_ctas, kUpThreads, 0, s>>>(b); }
-void launch_syn_fwd_b(const Batch<SynArgs>& b, cudaStream_t s) {
-    k_syn_fwd_b<PASS_FWD><<<b.total_ctas, kSynThreads, 0, s>>>(b);
-}
-void launch_syn_bwd_b(const Batch<SynArgs>& b, cudaStream_t s) {
-    k_syn_bwd_b<PASS_FWD_BWD><<<b.total_ctas, kSynThreads, syn_bwd_smem_bytes(), s>>>(b);
-}
 void launch_up_adj_b(const Batch<UpAdjArgs>& b, int max_wt, cudaStream_t s) {
     k_up_adj_b<<<b.total_ctas, kUpThreads, (size_t)max_wt * sizeof(float), s>>>(b);
 }

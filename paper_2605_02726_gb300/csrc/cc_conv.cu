@@ -2,24 +2,34 @@
 // the distortion (Eq. 10) and their adjoint, on 16x32 pixel tiles with recomputed halos.
 //   x1 = t + b1 + conv1(t),  xh = x1 + b2 + conv2(x1)   (replicate padding, cross-correlation)
 //   D = mean (xh - x)^2;  dxh = 2 (xh - x) / (3HW);  dx1 = dxh + conv2^T(dxh);  dt = dx1 + conv1^T(dx1)
-// Shared-memory tiles of t and x1 are replicate-padded (positions outside the image hold the
-// clamped value), so the forward stencils and the weight-gradient correlations need no clamps.
-// The transposed convolutions gather, per axis, the 3 (source, tap) pairs whose clamped index
-// lands on the target: interior q <- (q+1, 0), (q, 1), (q-1, 2); q = 0 <- (0,0), (0,1), (1,0);
+//
+// All tiles of a CTA live in one frame of 24 x 40 cells whose origin is (ty0 - 4, tx0 - 4): t on
+// the whole frame (halo 4), x1 on halo 3, the image and then dxh on halo 2, dx1 on halo 1, dt on
+// the core.  Tiles of t and x1 are replicate-padded (cells outside the image hold the clamped
+// value), so the forward stencils and the weight-gradient correlations need no clamps.
+//
+// Each thread computes a vertical strip of 2 cells at one column, all 3 channels, from a 4 x 3
+// register window per input channel (162 FMAs per 36 shared loads and 27 broadcast weight loads);
+// lanes take consecutive columns, so the loads are free of bank conflicts.  The transposed
+// convolutions are plain correlations with the flipped kernel inside the image; cells on the image
+// border gather, per axis, the 3 (source, tap) pairs whose clamped index lands on the target:
+// interior q <- (q+1, 0), (q, 1), (q-1, 2); q = 0 <- (0,0), (0,1), (1,0);
 // q = n-1 <- (n-1,1), (n-1,2), (n-2,2); n = 1 <- (0,0), (0,1), (0,2).
+// Weight gradients: warp w owns the (conv, out, in) tasks w, w + 8, w + 16 with 9 + 1 accumulators
+// each, lane = core column, a sliding 3-row window down the core; summed over the lanes at the end.
 #include "cc_kernels.h"
 
 namespace cc {
 namespace {
 
-constexpr int kTH = kConvTH, kTW = kConvTW;
+constexpr int kTH = kConvTH, kTW = kConvTW;  // core 16 x 32
 constexpr int kThreads = 256;
-constexpr int R4H = kTH + 8, R4W = kTW + 8;  // t   (halo 4)
-constexpr int R3H = kTH + 6, R3W = kTW + 6;  // x1  (halo 3)
-constexpr int R2H = kTH + 4, R2W = kTW + 4;  // dxh (halo 2)
-constexpr int R1H = kTH + 2, R1W = kTW + 2;  // dx1 (halo 1)
-constexpr int kSlices = 8;                   // weight-gradient row slices of 2 rows
-
+constexpr int SW = kTW + 8;               // 40 frame columns
+constexpr int T_R0 = 0, T_NR = kTH + 8;  // frame rows held by each buffer: t 0..23
+constexpr int X_R0 = 1, X_NR = kTH + 6;  // x1 1..22
+constexpr int D_R0 = 2, D_NR = kTH + 4;  // image / dxh 2..21
+constexpr int E_R0 = 3, E_NR = kTH + 2;  // dx1 3..20
+constexpr int kTasks = 18;               // (conv, out, in) weight-gradient tasks
 
 __device__ __forceinline__ void conv_pairs(int q, int n, int (&src)[3], int (&tap)[3]) {
     if (n == 1) {
@@ -33,190 +43,308 @@ __device__ __forceinline__ void conv_pairs(int q, int n, int (&src)[3], int (&ta
     }
 }
 
+struct ConvW {
+    float4 f[2][27];  // forward:    f[c][(i*3+ky)*3+kx] = (W[0][i][ky][kx], W[1][..], W[2][..], 0)
+    float4 t[2][27];  // transposed: t[c][(o*3+ky)*3+kx] = (W[o][0][ky][kx], W[o][1][..], W[o][2][..], 0)
+    float b[2][4];
+};
+
+// x_out = x_in + b + conv(x_in) at frame rows (ir, ir + 1) of IN (buffer rows), column c.
+template <int NR>
+__device__ __forceinline__ void fwd_strip(const float (*IN)[NR][SW], int ir, int c, const float4* wf,
+                                          const float* b, float (&acc)[3][2]) {
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) acc[o][j] = IN[o][ir + j][c] + b[o];
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            float v[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] = IN[i][ir - 1 + m][c - 1 + kx];
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+                const float4 w = wf[(i * 3 + ky) * 3 + kx];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    acc[0][j] = fmaf(w.x, v[j + ky], acc[0][j]);
+                    acc[1][j] = fmaf(w.y, v[j + ky], acc[1][j]);
+                    acc[2][j] = fmaf(w.z, v[j + ky], acc[2][j]);
+                }
+            }
+        }
+}
+
+// d_out = d_in + conv^T(d_in) at buffer rows (sr, sr + 1) of S, column c, all sources inside the
+// image: source (y + 1 - ky, x + 1 - kx) with tap (ky, kx).
+template <int NR>
+__device__ __forceinline__ void adj_strip(const float (*S)[NR][SW], int sr, int c, const float4* wt, float (&acc)[3][2]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) acc[i][j] = S[i][sr + j][c];
+#pragma unroll 1
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            float v[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] = S[o][sr - 1 + m][c + 1 - kx];
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+                const float4 w = wt[(o * 3 + ky) * 3 + kx];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    acc[0][j] = fmaf(w.x, v[j + 2 - ky], acc[0][j]);
+                    acc[1][j] = fmaf(w.y, v[j + 2 - ky], acc[1][j]);
+                    acc[2][j] = fmaf(w.z, v[j + 2 - ky], acc[2][j]);
+                }
+            }
+        }
+}
+
+// the same at one cell (global gy, gx; buffer row sr, column c) on or next to the image border
+template <int NR>
+__device__ __forceinline__ void adj_cell_border(const float (*S)[NR][SW], int sr, int c, int gy, int gx, int H,
+                                                int W, const float4* wt, float (&out)[3]) {
+    int sy[3], ky[3], sx[3], kx[3];
+    conv_pairs(gy, H, sy, ky);
+    conv_pairs(gx, W, sx, kx);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i] = S[i][sr][c];
+#pragma unroll 1
+    for (int p = 0; p < 3; ++p) {
+        // row pair p without a dynamically indexed array
+        const int syp = p == 0 ? sy[0] : (p == 1 ? sy[1] : sy[2]);
+        const int kyp = p == 0 ? ky[0] : (p == 1 ? ky[1] : ky[2]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int br = sr + syp - gy, bc = c + sx[q] - gx;
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                const float4 w = wt[(o * 3 + kyp) * 3 + kx[q]];
+                const float v = S[o][br][bc];
+                out[0] = fmaf(w.x, v, out[0]);
+                out[1] = fmaf(w.y, v, out[1]);
+                out[2] = fmaf(w.z, v, out[2]);
+            }
+        }
+    }
+}
+
 template <int PASS>
 __device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) {
     constexpr bool BWD = pass_bwd(PASS);
-    __shared__ float sWc[2][84];
-    __shared__ float sT[3][R4H][R4W];
-    __shared__ float sX1[3][R3H][R3W];
-    __shared__ float sD[3][R2H][R2W];
-    __shared__ float sD1[3][R1H][R1W];
+    __shared__ ConvW sW;
+    __shared__ float sT[3][T_NR][SW];
+    __shared__ float sX[3][X_NR][SW];
+    __shared__ float sD[3][D_NR][SW];
+    __shared__ float sE[3][E_NR][SW];
     __shared__ double sSe[kThreads / 32];
-    const int tid = threadIdx.x;
-    for (int j = tid; j < 84; j += kThreads) {
-        sWc[0][j] = j < 81 ? a.params[po::cv1_w + j] : a.params[po::cv1_b + j - 81];
-        sWc[1][j] = j < 81 ? a.params[po::cv2_w + j] : a.params[po::cv2_b + j - 81];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int j = tid; j < 2 * 81; j += kThreads) {
+        const int c = j / 81, e = j - c * 81;  // e = ((o*3+i)*3+ky)*3+kx
+        const int o = e / 27, i = (e / 9) % 3, k = e % 9;
+        const float w = a.params[(c ? po::cv2_w : po::cv1_w) + e];
+        reinterpret_cast<float*>(&sW.f[c][i * 9 + k])[o] = w;
+        reinterpret_cast<float*>(&sW.t[c][o * 9 + k])[i] = w;
     }
-    // weight-gradient task: tid < 144 -> (conv c, out o, in i, slice); 144 <= tid < 192 -> bias (c, o, slice)
-    float gacc[9];
+    if (tid < 2 * 27) {
+        const int c = tid / 27, k = tid % 27;
+        sW.f[c][k].w = 0.f;
+        sW.t[c][k].w = 0.f;
+    }
+    if (tid < 8) {
+        const int c = tid >> 2, o = tid & 3;
+        sW.b[c][o] = o < 3 ? a.params[(c ? po::cv2_b : po::cv1_b) + o] : 0.f;
+    }
+    float gacc[3][9], bacc[3];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) gacc[q] = 0.f;
+    for (int s = 0; s < 3; ++s) {
+        bacc[s] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) gacc[s][q] = 0.f;
+    }
     double se = 0.0;
     const int H = a.H, W = a.W;
     for (int tile = cta; tile < a.n_tiles; tile += ncta) {
         const int ty0 = (tile / a.tiles_x) * kTH, tx0 = (tile % a.tiles_x) * kTW;
+        const int fy0 = ty0 - 4, fx0 = tx0 - 4;  // global coordinates of frame cell (0, 0)
         __syncthreads();
         {
-            // the t tile (clamped reads, i.e. replicate-padded) and the image on the halo-2 region
-            // (into sD, replaced by dxh below) arrive by asynchronous copies in flight together
-            constexpr int NT = 3 * R4H * R4W, NI = 3 * R2H * R2W;
-            for (int e = tid; e < NT; e += kThreads) {
-                const int c = e / (R4H * R4W), rem = e - c * (R4H * R4W);
-                const int ry = rem / R4W, rx = rem - ry * R4W;
-                const int gy = clampi(ty0 - 4 + ry, 0, H - 1), gx = clampi(tx0 - 4 + rx, 0, W - 1);
-                cp_async4(&sT[c][ry][rx], a.t + (int64_t)c * a.HW + (int64_t)gy * W + gx);
+            // t on the whole frame and the image on halo 2, clamped (replicate) reads in flight together
+            for (int e = tid; e < 3 * T_NR * SW; e += kThreads) {
+                const int c = e / (T_NR * SW), rem = e - c * (T_NR * SW);
+                const int r = rem / SW, x = rem - r * SW;
+                const int gy = clampi(fy0 + r, 0, H - 1), gx = clampi(fx0 + x, 0, W - 1);
+                cp_async4(&sT[c][r][x], a.t + (int64_t)c * a.HW + (int64_t)gy * W + gx);
             }
-            for (int e = tid; e < NI; e += kThreads) {
-                const int c = e / (R2H * R2W), rem = e - c * (R2H * R2W);
-                const int ry = rem / R2W, rx = rem - ry * R2W;
-                const int gy = clampi(ty0 - 2 + ry, 0, H - 1), gx = clampi(tx0 - 2 + rx, 0, W - 1);
-                cp_async4(&sD[c][ry][rx], a.img + (int64_t)c * a.HW + (int64_t)gy * W + gx);
+            constexpr int DW = kTW + 4;
+            for (int e = tid; e < 3 * D_NR * DW; e += kThreads) {
+                const int c = e / (D_NR * DW), rem = e - c * (D_NR * DW);
+                const int r = rem / DW, x = 2 + (rem - r * DW);
+                const int gy = clampi(fy0 + D_R0 + r, 0, H - 1), gx = clampi(fx0 + x, 0, W - 1);
+                cp_async4(&sD[c][r][x], a.img + (int64_t)c * a.HW + (int64_t)gy * W + gx);
             }
             cp_async_wait_all();
         }
         __syncthreads();
-        // x1 at the real positions of the halo-3 region
-        for (int e = tid; e < R3H * R3W; e += kThreads) {
-            const int ry = e / R3W, rx = e - ry * R3W;
-            const int gy = ty0 - 3 + ry, gx = tx0 - 3 + rx;
-            if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
+        // x1 on halo 3: frame rows 1..22, columns 1..38
+        {
+            constexpr int NC = kTW + 6, NT = (X_NR / 2) * NC;
+            for (int task = tid; task < NT; task += kThreads) {
+                const int rb = task / NC, c = 1 + (task - rb * NC), fr = X_R0 + 2 * rb;
+                float acc[3][2];
+                fwd_strip<T_NR>(sT, fr - T_R0, c, sW.f[0], sW.b[0], acc);
 #pragma unroll
-            for (int o = 0; o < 3; ++o) {
-                float acc = sT[o][ry + 1][rx + 1] + sWc[0][81 + o];
+                for (int o = 0; o < 3; ++o)
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                        for (int kx = 0; kx < 3; ++kx)
-                            acc = fmaf(sWc[0][((o * 3 + i) * 3 + ky) * 3 + kx], sT[i][ry + ky][rx + kx], acc);
-                sX1[o][ry][rx] = acc;
+                    for (int j = 0; j < 2; ++j) sX[o][fr - X_R0 + j][c] = acc[o][j];
             }
         }
         __syncthreads();
-        // replicate-pad x1 outside the image
-        for (int e = tid; e < R3H * R3W; e += kThreads) {
-            const int ry = e / R3W, rx = e - ry * R3W;
-            const int gy = ty0 - 3 + ry, gx = tx0 - 3 + rx;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) continue;
-            const int sy = clampi(gy, 0, H - 1) - (ty0 - 3), sx = clampi(gx, 0, W - 1) - (tx0 - 3);
+        if (fy0 + X_R0 < 0 || fx0 + 1 < 0 || fy0 + X_R0 + X_NR > H || fx0 + 1 + kTW + 6 > W) {
+            // replicate-pad x1 outside the image (tiles on the image border)
+            constexpr int NC = kTW + 6;
+            for (int e = tid; e < X_NR * NC; e += kThreads) {
+                const int r = e / NC, c = 1 + (e - r * NC);
+                const int gy = fy0 + X_R0 + r, gx = fx0 + c;
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W) continue;
+                const int sr = clampi(gy, 0, H - 1) - fy0 - X_R0, sc = clampi(gx, 0, W - 1) - fx0;
 #pragma unroll
-            for (int o = 0; o < 3; ++o) sX1[o][ry][rx] = sX1[o][sy][sx];
+                for (int o = 0; o < 3; ++o) sX[o][r][c] = sX[o][sr][sc];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        // xh, distortion and dxh at the real positions of the halo-2 region
-        for (int e = tid; e < R2H * R2W; e += kThreads) {
-            const int ry = e / R2W, rx = e - ry * R2W;
-            const int gy = ty0 - 2 + ry, gx = tx0 - 2 + rx;
-            if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
-            const bool core = ry >= 2 && ry < 2 + kTH && rx >= 2 && rx < 2 + kTW;
+        // xh, distortion and dxh on halo 2: frame rows 2..21, columns 2..37
+        {
+            constexpr int NC = kTW + 4, NT = (D_NR / 2) * NC;
+            float sef = 0.f;
+            for (int task = tid; task < NT; task += kThreads) {
+                const int rb = task / NC, c = 2 + (task - rb * NC), fr = D_R0 + 2 * rb;
+                float acc[3][2];
+                fwd_strip<X_NR>(sX, fr - X_R0, c, sW.f[1], sW.b[1], acc);
+                const int gx = fx0 + c;
+                const bool core_x = c >= 4 && c < 4 + kTW && gx < W;
 #pragma unroll
-            for (int o = 0; o < 3; ++o) {
-                float acc = sX1[o][ry + 1][rx + 1] + sWc[1][81 + o];
+                for (int j = 0; j < 2; ++j) {
+                    const int gy = fy0 + fr + j;
+                    const bool core = core_x && fr + j >= 4 && fr + j < 4 + kTH && gy < H;
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                        for (int kx = 0; kx < 3; ++kx)
-                            acc = fmaf(sWc[1][((o * 3 + i) * 3 + ky) * 3 + kx], sX1[i][ry + ky][rx + kx], acc);
-                const int64_t gi = (int64_t)o * a.HW + (int64_t)gy * W + gx;
-                const float diff = acc - sD[o][ry][rx];
-                if (core) {
-                    se += (double)diff * diff;
-                    if (a.xhat) a.xhat[gi] = acc;
-                }
-                sD[o][ry][rx] = diff * a.gscale;
-            }
-        }
-        if (!BWD) continue;
-        __syncthreads();
-        // dx1 = dxh + conv2^T(dxh) at the real positions of the halo-1 region
-        for (int e = tid; e < R1H * R1W; e += kThreads) {
-            const int ry = e / R1W, rx = e - ry * R1W;
-            const int gy = ty0 - 1 + ry, gx = tx0 - 1 + rx;
-            if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
-            int sy[3], ky[3], sx[3], kx[3];
-            conv_pairs(gy, H, sy, ky);
-            conv_pairs(gx, W, sx, kx);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                sy[p] -= ty0 - 2;
-                sx[p] -= tx0 - 2;
-            }
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float acc = sD[i][ry + 1][rx + 1];
-#pragma unroll
-                for (int p = 0; p < 3; ++p)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q)
-#pragma unroll
-                        for (int o = 0; o < 3; ++o)
-                            acc = fmaf(sWc[1][((o * 3 + i) * 3 + ky[p]) * 3 + kx[q]], sD[o][sy[p]][sx[q]], acc);
-                sD1[i][ry][rx] = acc;
-            }
-        }
-        __syncthreads();
-        // dt = dx1 + conv1^T(dx1) on the core
-        for (int e = tid; e < kTH * kTW; e += kThreads) {
-            const int ry = e / kTW, rx = e - ry * kTW;
-            const int gy = ty0 + ry, gx = tx0 + rx;
-            if (gy >= H || gx >= W) continue;
-            int sy[3], ky[3], sx[3], kx[3];
-            conv_pairs(gy, H, sy, ky);
-            conv_pairs(gx, W, sx, kx);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                sy[p] -= ty0 - 1;
-                sx[p] -= tx0 - 1;
-            }
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float acc = sD1[i][ry + 1][rx + 1];
-#pragma unroll
-                for (int p = 0; p < 3; ++p)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q)
-#pragma unroll
-                        for (int o = 0; o < 3; ++o)
-                            acc = fmaf(sWc[0][((o * 3 + i) * 3 + ky[p]) * 3 + kx[q]], sD1[o][sy[p]][sx[q]], acc);
-                a.dt[(int64_t)i * a.HW + (int64_t)gy * W + gx] = acc;
-            }
-        }
-        // parameter gradients over the core (no shared-memory writes above since the last barrier)
-        const int ry_end = min(kTH, H - ty0), rx_end = min(kTW, W - tx0);
-        if (tid < 144) {
-            const int slice = tid & 7, task = tid >> 3;  // task 0..17
-            const int c = task / 9, o = (task / 3) % 3, i = task % 3;
-            for (int ry = 2 * slice; ry < min(2 * slice + 2, ry_end); ++ry) {
-                for (int rx = 0; rx < rx_end; ++rx) {
-                    if (c == 1) {  // conv2: dxh (origin ty0-2) x padded x1 (origin ty0-3)
-                        const float gv = sD[o][ry + 2][rx + 2];
-#pragma unroll
-                        for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                            for (int kx = 0; kx < 3; ++kx) gacc[ky * 3 + kx] = fmaf(gv, sX1[i][ry + 2 + ky][rx + 2 + kx], gacc[ky * 3 + kx]);
-                    } else {       // conv1: dx1 (origin ty0-1) x padded t (origin ty0-4)
-                        const float gv = sD1[o][ry + 1][rx + 1];
-#pragma unroll
-                        for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                            for (int kx = 0; kx < 3; ++kx) gacc[ky * 3 + kx] = fmaf(gv, sT[i][ry + 3 + ky][rx + 3 + kx], gacc[ky * 3 + kx]);
+                    for (int o = 0; o < 3; ++o) {
+                        float& cell = sD[o][fr - D_R0 + j][c];
+                        const float diff = acc[o][j] - cell;
+                        if (core) {
+                            sef = fmaf(diff, diff, sef);
+                            if (a.xhat) a.xhat[(int64_t)o * a.HW + (int64_t)gy * W + gx] = acc[o][j];
+                        }
+                        cell = diff * a.gscale;
                     }
                 }
             }
-        } else if (tid < 192) {
-            const int slice = tid & 7, task = (tid - 144) >> 3;  // 0..5
-            const int c = task / 3, o = task % 3;
-            for (int ry = 2 * slice; ry < min(2 * slice + 2, ry_end); ++ry)
-                for (int rx = 0; rx < rx_end; ++rx) gacc[0] += c == 1 ? sD[o][ry + 2][rx + 2] : sD1[o][ry + 1][rx + 1];
+            se += (double)sef;
+        }
+        if (!BWD) continue;
+        __syncthreads();
+        // dx1 = dxh + conv2^T(dxh) on halo 1: frame rows 3..20, columns 3..36
+        {
+            constexpr int NC = kTW + 2, NT = (E_NR / 2) * NC;
+            for (int task = tid; task < NT; task += kThreads) {
+                const int rb = task / NC, c = 3 + (task - rb * NC), fr = E_R0 + 2 * rb;
+                const int gy = fy0 + fr, gx = fx0 + c;
+                float acc[3][2];
+                if (gy >= 1 && gy + 1 <= H - 2 && gx >= 1 && gx <= W - 2) {
+                    adj_strip<D_NR>(sD, fr - D_R0, c, sW.t[1], acc);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        float out[3] = {0.f, 0.f, 0.f};
+                        if (gy + j >= 0 && gy + j < H && gx >= 0 && gx < W)
+                            adj_cell_border<D_NR>(sD, fr - D_R0 + j, c, gy + j, gx, H, W, sW.t[1], out);
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) acc[i][j] = out[i];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) sE[i][fr - E_R0 + j][c] = acc[i][j];
+            }
+        }
+        __syncthreads();
+        // dt = dx1 + conv1^T(dx1) on the core: frame rows 4..19, columns 4..35
+        {
+            constexpr int NC = kTW, NT = (kTH / 2) * NC;
+            for (int task = tid; task < NT; task += kThreads) {
+                const int rb = task / NC, c = 4 + (task - rb * NC), fr = 4 + 2 * rb;
+                const int gy = fy0 + fr, gx = fx0 + c;
+                if (gx >= W || gy >= H) continue;
+                float acc[3][2];
+                if (gy >= 1 && gy + 1 <= H - 2 && gx >= 1 && gx <= W - 2) {
+                    adj_strip<E_NR>(sE, fr - E_R0, c, sW.t[0], acc);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        float out[3] = {0.f, 0.f, 0.f};
+                        if (gy + j < H) adj_cell_border<E_NR>(sE, fr - E_R0 + j, c, gy + j, gx, H, W, sW.t[0], out);
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) acc[i][j] = out[i];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    if (gy + j < H)
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) a.dt[(int64_t)i * a.HW + (int64_t)(gy + j) * W + gx] = acc[i][j];
+            }
+        }
+        // parameter gradients over the core (the buffers read here are not written since the last barrier)
+        {
+            const int c = 4 + lane;
+            const bool colok = tx0 + lane < W;
+            const int ny = min(kTH, H - ty0);
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const int task = wid + 8 * s;
+                if (task >= kTasks) break;
+                const int cv = task / 9, o = (task / 3) % 3, i = task % 3;
+                // G row y = core row y; IN row y = core row y (rows -1 .. 16 valid)
+                const float* G = cv ? &sD[o][4 - D_R0][0] : &sE[o][4 - E_R0][0];
+                const float* IN = cv ? &sX[i][4 - X_R0][0] : &sT[i][4 - T_R0][0];
+                float w0[3], w1[3];
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    w0[kx] = IN[-SW + c - 1 + kx];
+                    w1[kx] = IN[c - 1 + kx];
+                }
+#pragma unroll
+                for (int y = 0; y < kTH; ++y) {
+                    float w2[3];
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx) w2[kx] = IN[(y + 1) * SW + c - 1 + kx];
+                    const float g = (colok && y < ny) ? G[y * SW + c] : 0.f;
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx) {
+                        gacc[s][kx] = fmaf(g, w0[kx], gacc[s][kx]);
+                        gacc[s][3 + kx] = fmaf(g, w1[kx], gacc[s][3 + kx]);
+                        gacc[s][6 + kx] = fmaf(g, w2[kx], gacc[s][6 + kx]);
+                    }
+                    bacc[s] += g;
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx) {
+                        w0[kx] = w1[kx];
+                        w1[kx] = w2[kx];
+                    }
+                }
+            }
         }
     }
     __syncthreads();
     {
         double v = warp_sum_d(se);
-        if ((tid & 31) == 0) sSe[tid >> 5] = v;
+        if (lane == 0) sSe[wid] = v;
         __syncthreads();
         if (tid == 0) {
             double s = 0.0;
@@ -225,24 +353,20 @@ __device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) 
         }
     }
     if (!BWD) return;
-    // reduce the row slices of each task in a fixed order; the x1 tile is free now
-    float* sG = &sX1[0][0][0];  // [192][9]
-#pragma unroll
-    for (int q = 0; q < 9; ++q)
-        if (tid < 192) sG[tid * 9 + q] = gacc[q];
-    __syncthreads();
     float* gp = a.gpart + (int64_t)cta * po::conv_block;
-    if (tid < 18 * 9) {
-        const int task = tid / 9, q = tid % 9;
-        const int c = task / 9, o = (task / 3) % 3, i = task % 3;
-        float s = 0.f;
-        for (int sl = 0; sl < kSlices; ++sl) s += sG[(task * 8 + sl) * 9 + q];
-        gp[(c == 0 ? 0 : 84) + (o * 3 + i) * 9 + q] = s;
-    } else if (tid < 18 * 9 + 6) {
-        const int task = tid - 162, c = task / 3, o = task % 3;
-        float s = 0.f;
-        for (int sl = 0; sl < kSlices; ++sl) s += sG[(144 + task * 8 + sl) * 9];
-        gp[(c == 0 ? 81 : 165) + o] = s;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int task = wid + 8 * s;
+        if (task >= kTasks) break;
+        const int cv = task / 9, o = (task / 3) % 3, i = task % 3;
+        const int base = cv ? po::cv2_w - po::cv1_w : 0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float v = warp_sum(gacc[s][q]);
+            if (lane == 0) gp[base + (o * 3 + i) * 9 + q] = v;
+        }
+        const float bv = warp_sum(bacc[s]);
+        if (lane == 0 && i == 0) gp[base + 81 + o] = bv;
     }
 }
 

@@ -266,7 +266,7 @@ def main():
             v, dt = oracle_rate(H, W, args.cpu_iters, SEED)
             cpu = {"value": v, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
                    "sample": f"{args.cpu_iters} encoder iterations of the 512x768 workload ({dt:.1f} s)"}
-        launches_per_step = 19  # relax, arm, 5 upsampling, synthesis, convs, synthesis adjoint, 5 upsampling adjoints, IFCE, gather, reduce, finish
+        launches_per_step = cc.kernels_per_iteration(H, W)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -274,7 +274,7 @@ def main():
             "config": {"workload": WORKLOAD, "image": [H, W], "latents": cc.latent_count(H, W),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "flushed between timed iterations (256 MB write outside the events)",
-                       "launch": "eager, 19 kernels per iteration"},
+                       "launch": f"eager, {launches_per_step} kernels per iteration"},
             "e2e": {"value": world * H * W / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
                     "h2d_bytes_per_step": int(host_img.numel() * 4), "d2h_bytes_per_step": 24,
                     "ms_per_step": e2e_ms, "loss_readback": loss_now},

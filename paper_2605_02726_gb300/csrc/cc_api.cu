@@ -325,6 +325,13 @@ int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int3
     return CC_OK;
 }
 
+int32_t coolchic_kernels_per_iteration(const cc_arch_t* a) {
+    if (check_arch(a)) return -1;
+    // relax, entropy model, synthesis forward, convs, synthesis adjoint, IFCE, gather, reduce,
+    // finish, forward upsampling stages 2..6 and adjoint stages 1..6
+    return 9 + (kL - 2) + (kL - 1);
+}
+
 size_t coolchic_workspace_bytes(const cc_arch_t* a, int32_t flags) {
     if (check_arch(a)) return 0;
     if (device_setup()) return 0;

@@ -170,25 +170,22 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     for (int j = tid; j < kIfceSm; j += kT) sIf[j] = a.params[po::if_w0 + j];
     __syncthreads();
 
-    // per-lane constants
-    float b2c[2][2], w3c[2][2][2], wsc[3][2][2];  // [nt][col] ; [nt][col][out] ; [nt][col][out]
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int u = nt * 8 + 2 * tq + cc;
-            b2c[nt][cc] = a.params[po::arm_b2 + u];
-            w3c[nt][cc][0] = a.params[po::arm_w3 + u];
-            w3c[nt][cc][1] = a.params[po::arm_w3 + 16 + u];
+    // per-lane constants of the SIMT parts, read as float2 (units / features 2t, 2t+1 of a tile)
+    __shared__ __align__(16) float sC[16 + 2 * 16 + 2 * 24];  // b2 [16], W3 [2][16], Ws [2][24] (zero-padded)
+    for (int j = tid; j < 96; j += kT) {
+        float v;
+        if (j < 16) v = a.params[po::arm_b2 + j];
+        else if (j < 48) v = a.params[po::arm_w3 + (j - 16)];
+        else {
+            const int o = (j - 48) / 24, f = (j - 48) % 24;
+            v = f < 20 ? a.params[po::arm_ws + o * 20 + f] : 0.f;
         }
-#pragma unroll
-    for (int nt = 0; nt < 3; ++nt)
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int f = nt * 8 + 2 * tq + cc;
-            wsc[nt][cc][0] = f < 20 ? a.params[po::arm_ws + f] : 0.f;
-            wsc[nt][cc][1] = f < 20 ? a.params[po::arm_ws + 20 + f] : 0.f;
-        }
+        sC[j] = v;
+    }
+    const float2* b2c = reinterpret_cast<const float2*>(sC) + tq;          // [nt * 4]
+    const float2* w3c = reinterpret_cast<const float2*>(sC + 16) + tq;     // [o * 8 + nt * 4]
+    const float2* wsc = reinterpret_cast<const float2*>(sC + 48) + tq;     // [o * 12 + nt * 4]
+    __syncthreads();
     int ndy[4], ndx[4];  // context slots t, t+4, t+8, t+12 of this lane
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -283,10 +280,11 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             // layer 2
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
-                d2[nt][0] = b2c[nt][0];
-                d2[nt][1] = b2c[nt][1];
-                d2[nt][2] = b2c[nt][0];
-                d2[nt][3] = b2c[nt][1];
+                const float2 bb = b2c[nt * 4];
+                d2[nt][0] = bb.x;
+                d2[nt][1] = bb.y;
+                d2[nt][2] = bb.x;
+                d2[nt][3] = bb.y;
                 float e[4] = {0.f, 0.f, 0.f, 0.f};
                 mma3(d2[nt], e, H10, sFr[(FR_W2 + 0 * 2 + nt) * 32 + lane]);
                 mma3(d2[nt], e, H11, sFr[(FR_W2 + 1 * 2 + nt) * 32 + lane]);
@@ -366,14 +364,17 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         // dA2 = (dout . W3) masked by a2 > 0
         float da2[2][4];
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
+        for (int nt = 0; nt < 2; ++nt) {
+            const float2 m = w3c[nt * 4], sv = w3c[8 + nt * 4];
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
-                const float vA = dmuA * w3c[nt][cc][0] + dsA * w3c[nt][cc][1];
-                const float vB = dmuB * w3c[nt][cc][0] + dsB * w3c[nt][cc][1];
+                const float wm = cc ? m.y : m.x, ws = cc ? sv.y : sv.x;
+                const float vA = dmuA * wm + dsA * ws;
+                const float vB = dmuB * wm + dsB * ws;
                 da2[nt][cc] = d2[nt][cc] > 0.f ? vA : 0.f;
                 da2[nt][2 + cc] = d2[nt][2 + cc] > 0.f ? vB : 0.f;
             }
+        }
         const AFrag DA20 = chain(da2[0]), DA21 = chain(da2[1]);
         // dA1 = (dA2 . W2) masked by a1 > 0
         float da1[2][4];
@@ -393,10 +394,12 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         float dc[3][4];
 #pragma unroll
         for (int nt = 0; nt < 3; ++nt) {
+            const float2 m = wsc[nt * 4], sv = wsc[12 + nt * 4];
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
-                dc[nt][cc] = dmuA * wsc[nt][cc][0] + dsA * wsc[nt][cc][1];
-                dc[nt][2 + cc] = dmuB * wsc[nt][cc][0] + dsB * wsc[nt][cc][1];
+                const float wm = cc ? m.y : m.x, ws = cc ? sv.y : sv.x;
+                dc[nt][cc] = dmuA * wm + dsA * ws;
+                dc[nt][2 + cc] = dmuB * wm + dsB * ws;
             }
             float e[4] = {0.f, 0.f, 0.f, 0.f};
             mma3(dc[nt], e, DA10, sFr[(FR_BW1 + 0 * 3 + nt) * 32 + lane]);
@@ -560,13 +563,13 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(kT, 2) k_arm(ArmArgs a) {
+__global__ void __launch_bounds__(kT, 3) k_arm(ArmArgs a) {
     __shared__ ArmArgs sa;
     param_fetch(a, sa);
     arm_body<PASS>(sa, blockIdx.x, gridDim.x);
 }
 template <int PASS>
-__global__ void __launch_bounds__(kT, 2) k_arm_b(Batch<ArmArgs> b) {
+__global__ void __launch_bounds__(kT, 3) k_arm_b(Batch<ArmArgs> b) {
     __shared__ ArmArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
@@ -583,7 +586,7 @@ size_t arm_smem_bytes(int pass) {  // the staging tiles exist only for the adjoi
 int arm_grid(int64_t N) {
     const int64_t units = (N + 15) / 16;
     const int64_t ctas = (units + kWarps - 1) / kWarps;
-    const int64_t cap = (int64_t)num_sms() * 2;
+    const int64_t cap = (int64_t)num_sms() * 3;  // 3 resident CTAs per SM
     return (int)(ctas < cap ? (ctas < 1 ? 1 : ctas) : cap);
 }
 

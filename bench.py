@@ -266,7 +266,7 @@ def main():
             v, dt = oracle_rate(H, W, args.cpu_iters, SEED)
             cpu = {"value": v, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
                    "sample": f"{args.cpu_iters} encoder iterations of the 512x768 workload ({dt:.1f} s)"}
-        launches_per_step = cc.kernels_per_iteration(H, W)
+        launches_per_step = cc.kernel_launches(H, W, 1)  # one encode_step call of one iteration per step
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -108,10 +108,11 @@ int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int3
  * (coolchic_forward with store_activations = 1).  Returns 0 on a bad arch. */
 size_t coolchic_workspace_bytes(const cc_arch_t* arch, int32_t flags);
 
-/* Number of kernel launches one encoder iteration of coolchic_encode_step makes for this image
- * size (no counterpart in the paper; for profiling and graph sizing).  -1 on a bad arch; needs
- * no device. */
-int32_t coolchic_kernels_per_iteration(const cc_arch_t* arch);
+/* Number of kernel launches a coolchic_encode_step call of n_iters iterations makes (no
+ * counterpart in the paper; for profiling and graph sizing): the first iteration relaxes the
+ * latents in a launch of its own, later ones take them from the previous Adam update.  -1 on a
+ * bad arch or n_iters < 0; needs no device. */
+int64_t coolchic_kernel_launches(const cc_arch_t* arch, int32_t n_iters);
 
 /* Encoder iterations (Sec. IV-A..B): for it = 0..n_iters-1, relax the latents with the noise of
  * step *state->step, run the forward pass and its adjoint over all latents and pixels, take one

@@ -249,8 +249,9 @@ int num_sms() {
 // Forward sequence shared by the entry points: relax, entropy model, upsampling, synthesis, convs.
 static void run_forward(const Work& w, const float* image, const float* latents, const float* params,
                         const int64_t* step_dev, int64_t step_host, uint64_t seed, int relax, int arm_pass,
-                        int syn_pass, int conv_pass, float arm_gscale, float conv_gscale, float* xhat, cudaStream_t s) {
-    launch_relax(w, latents, step_dev, step_host, seed, relax, s);
+                        int syn_pass, int conv_pass, float arm_gscale, float conv_gscale, float* xhat, cudaStream_t s,
+                        bool relaxed_already = false) {
+    if (!relaxed_already) launch_relax(w, latents, step_dev, step_host, seed, relax, s);
     tbeg(CC_KERNEL_ARM, s);
     launch_arm(w, params, arm_pass, arm_gscale, s);
     tend(CC_KERNEL_ARM, s);
@@ -325,11 +326,14 @@ int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int3
     return CC_OK;
 }
 
-int32_t coolchic_kernels_per_iteration(const cc_arch_t* a) {
+int64_t coolchic_kernel_launches(const cc_arch_t* a, int32_t n_iters) {
     if (check_arch(a)) return -1;
-    // relax, entropy model, synthesis forward, convs, synthesis adjoint, IFCE, gather, reduce,
-    // finish, forward upsampling stages 2..6 and adjoint stages 1..6
-    return 9 + (kL - 2) + (kL - 1);
+    if (n_iters < 0) return fail(CC_ERR_ARG, "n_iters must be >= 0"), -1;
+    if (n_iters == 0) return 0;
+    // per iteration: entropy model, synthesis forward, convs, synthesis adjoint, IFCE, gather,
+    // reduce, finish, forward upsampling stages 2..6 and adjoint stages 1..6; relax once per call
+    const int64_t per_iter = 8 + (kL - 2) + (kL - 1);
+    return 1 + per_iter * n_iters;
 }
 
 size_t coolchic_workspace_bytes(const cc_arch_t* a, int32_t flags) {
@@ -353,11 +357,13 @@ int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const fl
     const float conv_gs = 2.f / (3.f * (float)w.HW);
     if (rd_per_iter) launch_mark_base(w, st->step, s);
     for (int it = 0; it < n_iters; ++it) {
+        // the relaxed latents of iterations after the first come from the previous Adam update
         run_forward(w, image, st->latents, st->params, st->step, 0, h.seed, kRelaxNoise, PASS_FWD_BWD, PASS_FWD,
-                    PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s);
+                    PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s, it > 0);
         syn_backward_timed(w, st->params, PASS_FWD_BWD, s);
         launch_up_adjoint(w, st->params, s);
-        launch_gather(w, st->params, kRelaxNoise, nullptr, st->latents, st->m_lat, st->v_lat, h, st->step, s);
+        launch_gather(w, st->params, kRelaxNoise, nullptr, st->latents, st->m_lat, st->v_lat, h, st->step, s,
+                      it + 1 < n_iters);
         launch_param_reduce(w, st->params, st->m_par, st->v_par, nullptr, 1.f, h, st->step, s);
         launch_finish(w, h, 1, 1, (double*)rd_per_iter, st->step, 0, 1, s);
         if ((rc = launched("encode_step"))) return rc;

@@ -27,7 +27,8 @@ struct cc_batch {
     cc::Batch<cc::UpAdjArgs> upa[cc::kL];  // stage 1..6
     int upa_wt[cc::kL];
     cc::Batch<cc::IfceArgs> ifce;
-    cc::Batch<cc::GatherArgs> gather;
+    cc::Batch<cc::GatherArgs> gather;       // last iteration of a call: Adam only
+    cc::Batch<cc::GatherArgs> gather_next;  // other iterations: Adam + next step's relaxed latents
     cc::Batch<cc::ReduceArgs> reduce;
     cc::Batch<cc::FinishArgs> finish;
     double* rd = nullptr;  // device [rd_capacity][n][3]
@@ -75,8 +76,8 @@ int scaled(int cap, float f) {
 }
 
 size_t table_bytes(int n, int rd_capacity) {
-    // upper bound: 20 kernel tables of at most 512-byte args plus CTA arrays, and the records
-    return (size_t)20 * ((size_t)512 * n + 256 + sizeof(int) * (n + 1) + 256) + (size_t)rd_capacity * n * 3 * sizeof(double) + 4096;
+    // upper bound: 21 kernel tables of at most 512-byte args plus CTA arrays, and the records
+    return (size_t)21 * ((size_t)512 * n + 256 + sizeof(int) * (n + 1) + 256) + (size_t)rd_capacity * n * 3 * sizeof(double) + 4096;
 }
 
 }  // namespace
@@ -183,6 +184,8 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
     b->ifce = fill([&](int j) { return ifce_args(W[j]); }, [&](int j) { return scaled(ifce_ctas(W[j]), sc.other); });
     b->gather = fill([&](int j) { return gather_args(W[j], kRelaxNoise, nullptr, states[j].latents, states[j].m_lat, states[j].v_lat, H[j], states[j].step); },
                      [&](int j) { return scaled(gather_ctas(W[j]), sc.other); });
+    b->gather_next = fill([&](int j) { return gather_args(W[j], kRelaxNoise, nullptr, states[j].latents, states[j].m_lat, states[j].v_lat, H[j], states[j].step, true); },
+                          [&](int j) { return scaled(gather_ctas(W[j]), sc.other); });
     b->reduce = fill([&](int j) { return reduce_args(W[j], states[j].params, states[j].m_par, states[j].v_par, nullptr, 1.f, H[j], states[j].step); },
                      [&](int) { return reduce_ctas(); });
     b->finish = fill([&](int j) {
@@ -215,6 +218,7 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
     for (int st = 1; st < kL; ++st) place(b->upa[st], base);
     place(b->ifce, base);
     place(b->gather, base);
+    place(b->gather_next, base);
     place(b->reduce, base);
     place(b->finish, base);
     b->rd = rd_capacity > 0 ? reinterpret_cast<double*>(base + rd_off) : nullptr;
@@ -235,7 +239,7 @@ int coolchic_batch_step(cc_batch_t* b, int32_t n_iters, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     if (b->rd) launch_mark_base_b(b->finish, s);
     for (int it = 0; it < n_iters; ++it) {
-        launch_relax_b(b->relax, s);
+        if (it == 0) launch_relax_b(b->relax, s);  // later iterations: relaxed by the previous Adam update
         launch_arm_b(b->arm, PASS_FWD_BWD, s);
         for (int m = kL - 2; m >= 1; --m) launch_up_fwd_b(b->upf[m], s);
         launch_syn_fwd_b(b->synf, s);
@@ -243,7 +247,7 @@ int coolchic_batch_step(cc_batch_t* b, int32_t n_iters, void* stream) {
         launch_syn_bwd_b(b->synb, s);
         for (int st = 1; st < kL; ++st) launch_up_adj_b(b->upa[st], b->upa_wt[st], s);
         launch_ifce_b(b->ifce, s);
-        launch_gather_b(b->gather, s);
+        launch_gather_b(it + 1 < n_iters ? b->gather_next : b->gather, s);
         launch_reduce_b(b->reduce, s);
         launch_finish_b(b->finish, s);
     }

@@ -119,6 +119,15 @@ __device__ __forceinline__ LapOut laplace_mass(float y, float mu, float logb) {
     return o;
 }
 
+// Adam bias corrections 1 - beta^t (Sec. IV-B) as -expm1(t log(beta)) with log(beta) =
+// log1p(beta - 1): FP32 with a relative error of a few 1e-7 at every t, where 1 - powf(beta, t)
+// would lose most digits to cancellation at small t.
+__device__ __forceinline__ void adam_bias_corrections(int64_t t, float beta1, float beta2, float& bc1, float& bc2) {
+    const float tf = (float)t;
+    bc1 = -expm1f(tf * log1pf(beta1 - 1.f));
+    bc2 = -expm1f(tf * log1pf(beta2 - 1.f));
+}
+
 // ---------------------------------------------------------------------------------------------
 // Reductions
 // ---------------------------------------------------------------------------------------------

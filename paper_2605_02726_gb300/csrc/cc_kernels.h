@@ -194,6 +194,7 @@ struct GatherArgs {
     float* m;
     float* v;
     const int64_t* step_dev;
+    float* yt_next;   // non-null (with Adam): also write y~ = y + u(hp.seed, step + 1) for the next step
     Hp hp;
     int zero_grad, pad_;
 };
@@ -241,8 +242,11 @@ void launch_syn_backward(const Work& w, const float* params, int pass, cudaStrea
 // a8: upsampling adjoint, stages 1..6.
 void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s);
 // a9 gather + a11: latent gradient assembly, then either Adam on the latents or a copy-out.
+// relax_next: the Adam update also writes the next step's relaxed latents (y~ of step + 1), so
+// that the next iteration needs no relaxation launch.
 void launch_gather(const Work& w, const float* params, int relax, float* grad_out, float* y,
-                   float* m, float* v, const Hp& hp, const int64_t* step_dev, cudaStream_t s);
+                   float* m, float* v, const Hp& hp, const int64_t* step_dev, cudaStream_t s,
+                   bool relax_next = false);
 // a10 + a11: fixed-order reduction of the per-CTA parameter gradients, then Adam or a copy-out.
 void launch_param_reduce(const Work& w, float* params, float* m, float* v, float* grad_out,
                          float out_scale, const Hp& hp, const int64_t* step_dev, cudaStream_t s);
@@ -271,7 +275,7 @@ ConvArgs conv_args(const Work& w, const float* params, const float* image, float
 UpAdjArgs up_adj_args(const Work& w, const float* params, int st);
 IfceArgs ifce_args(const Work& w);
 GatherArgs gather_args(const Work& w, int relax, float* grad_out, float* y, float* m, float* v, const Hp& hp,
-                       const int64_t* step_dev);
+                       const int64_t* step_dev, bool relax_next = false);
 ReduceArgs reduce_args(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,
                        const Hp& hp, const int64_t* step_dev);
 FinishArgs finish_args(const Work& w, const Hp& hp, int have_arm, int have_conv, double* rd, int rd_stride,

@@ -79,17 +79,11 @@ __global__ void k_ifce_cells_b(Batch<IfceArgs> b) {
 // parameter of a single-job launch; the grid tables are read from a shared copy.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int ncta) {
-    __shared__ float s_bc[2];
     __shared__ Geom g;  // shared copy: the grid tables are indexed with a runtime grid number
-    if (threadIdx.x == 0) {
-        g = a.g;
-        if (!a.grad_out) {
-            const double t = (double)(*a.step_dev + 1);
-            s_bc[0] = (float)(1.0 - pow((double)a.hp.beta1, t));
-            s_bc[1] = (float)(1.0 - pow((double)a.hp.beta2, t));
-        }
-    }
+    if (threadIdx.x == 0) g = a.g;
     __syncthreads();
+    float bc1 = 1.f, bc2 = 1.f;
+    if (!a.grad_out) adam_bias_corrections(*a.step_dev + 1, a.hp.beta1, a.hp.beta2, bc1, bc2);
     const int64_t N = g.off[kL];
     const float* __restrict__ dS = a.dS;
     for (int64_t i = cta * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)ncta * blockDim.x) {
@@ -135,7 +129,9 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
             const float vi = a.hp.beta2 * a.v[i] + (1.f - a.hp.beta2) * acc * acc;
             a.m[i] = mi;
             a.v[i] = vi;
-            a.y[i] -= a.hp.lr * (mi / s_bc[0]) / (sqrtf(vi / s_bc[1]) + a.hp.eps);
+            const float yn = a.y[i] - a.hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
+            a.y[i] = yn;
+            if (a.yt_next) a.yt_next[i] = yn + counter_uniform(a.hp.seed, *a.step_dev + 1, i);
         }
     }
 }
@@ -153,14 +149,15 @@ __global__ void k_gather_b(Batch<GatherArgs> b) {
 
 // ---------------------------------------------------------------------------------------------
 // Fixed-order sum of the per-CTA partial parameter gradients, then Adam or a scaled copy.
-// A CTA owns 32 consecutive parameters (one per lane); its 8 warps take interleaved slices of the
-// partial rows (coalesced across lanes) and their sums are added in warp order.  A job has
-// kReduceCtas CTAs.
+// A CTA owns 32 consecutive parameters (one per lane); its 32 warps take interleaved rows of the
+// partials (coalesced across lanes, four independent loads in flight per step) and their sums
+// are added in warp order.  A job has kReduceCtas CTAs.
 // ---------------------------------------------------------------------------------------------
 constexpr int kReduceCtas = (po::total + 31) / 32;
+constexpr int kReduceThreads = 1024, kReduceWarps = kReduceThreads / 32;
 
 __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
-    __shared__ float red[8][33];
+    __shared__ float red[kReduceWarps][33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int p = cta * 32 + lane;
     float a0 = 0.f, a1 = 0.f;
@@ -186,38 +183,42 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
             stride = po::conv_block;
             cnt = a.n_conv;
         }
+        // rows wid, wid + 32, ...
+        constexpr int RW = kReduceWarps;
         int q = wid;
-        for (; q + 8 < cnt; q += 16) {
-            a0 += __ldg(base + (int64_t)q * stride);
-            a1 += __ldg(base + (int64_t)(q + 8) * stride);
+        for (; q + 3 * RW < cnt; q += 4 * RW) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldg(base + (int64_t)(q + RW * u) * stride);
+            a0 += v[0] + v[1];
+            a1 += v[2] + v[3];
         }
-        if (q < cnt) a0 += __ldg(base + (int64_t)q * stride);
+        for (; q < cnt; q += RW) a0 += __ldg(base + (int64_t)q * stride);
     }
     red[wid][lane] = a0 + a1;
     __syncthreads();
     if (wid != 0 || p >= po::total) return;
     float gsum = 0.f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) gsum += red[w][lane];
+    for (int w = 0; w < kReduceWarps; ++w) gsum += red[w][lane];
     if (a.grad_out) {
         a.grad_out[p] = gsum * a.out_scale;
         return;
     }
-    const double t = (double)(*a.step_dev + 1);
-    const float bc1 = (float)(1.0 - pow((double)a.hp.beta1, t));
-    const float bc2 = (float)(1.0 - pow((double)a.hp.beta2, t));
+    float bc1, bc2;
+    adam_bias_corrections(*a.step_dev + 1, a.hp.beta1, a.hp.beta2, bc1, bc2);
     const float mi = a.hp.beta1 * a.m[p] + (1.f - a.hp.beta1) * gsum;
     const float vi = a.hp.beta2 * a.v[p] + (1.f - a.hp.beta2) * gsum * gsum;
     a.m[p] = mi;
     a.v[p] = vi;
     a.params[p] -= a.hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
 }
-__global__ void __launch_bounds__(256) k_param_reduce(ReduceArgs a) {
+__global__ void __launch_bounds__(kReduceThreads) k_param_reduce(ReduceArgs a) {
     __shared__ ReduceArgs sa;
     param_fetch(a, sa);
     reduce_body(sa, blockIdx.x);
 }
-__global__ void __launch_bounds__(256) k_param_reduce_b(Batch<ReduceArgs> b) {
+__global__ void __launch_bounds__(kReduceThreads) k_param_reduce_b(Batch<ReduceArgs> b) {
     __shared__ ReduceArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
@@ -308,7 +309,7 @@ IfceArgs ifce_args(const Work& w) {
     return a;
 }
 GatherArgs gather_args(const Work& w, int relax, float* grad_out, float* y, float* m, float* v, const Hp& hp,
-                       const int64_t* step_dev) {
+                       const int64_t* step_dev, bool relax_next) {
     GatherArgs a;
     a.g = w.g;
     a.dYd = w.dYd;
@@ -322,6 +323,7 @@ GatherArgs gather_args(const Work& w, int relax, float* grad_out, float* y, floa
     a.m = m;
     a.v = v;
     a.step_dev = step_dev;
+    a.yt_next = (relax_next && !grad_out) ? w.yt : nullptr;
     a.hp = hp;
     a.zero_grad = relax == kRelaxHard ? 1 : 0;
     a.pad_ = 0;
@@ -379,15 +381,15 @@ void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_
 }
 
 void launch_gather(const Work& w, const float* params, int relax, float* grad_out, float* y, float* m, float* v,
-                   const Hp& hp, const int64_t* step_dev, cudaStream_t s) {
+                   const Hp& hp, const int64_t* step_dev, cudaStream_t s, bool relax_next) {
     (void)params;
     k_ifce_cells<<<ifce_ctas(w), 128, 0, s>>>(ifce_args(w));
-    k_gather<<<gather_ctas(w), 256, 0, s>>>(gather_args(w, relax, grad_out, y, m, v, hp, step_dev));
+    k_gather<<<gather_ctas(w), 256, 0, s>>>(gather_args(w, relax, grad_out, y, m, v, hp, step_dev, relax_next));
 }
 
 void launch_param_reduce(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,
                          const Hp& hp, const int64_t* step_dev, cudaStream_t s) {
-    k_param_reduce<<<kReduceCtas, 256, 0, s>>>(reduce_args(w, params, m, v, grad_out, out_scale, hp, step_dev));
+    k_param_reduce<<<kReduceCtas, kReduceThreads, 0, s>>>(reduce_args(w, params, m, v, grad_out, out_scale, hp, step_dev));
 }
 
 void launch_finish(const Work& w, const Hp& hp, int have_arm, int have_conv, double* rd_out, int64_t* step_dev,
@@ -403,7 +405,9 @@ void launch_mark_base(const Work& w, const int64_t* step_dev, cudaStream_t s) {
 void launch_relax_b(const Batch<RelaxArgs>& b, cudaStream_t s) { k_relax_b<<<b.total_ctas, 256, 0, s>>>(b); }
 void launch_ifce_b(const Batch<IfceArgs>& b, cudaStream_t s) { k_ifce_cells_b<<<b.total_ctas, 128, 0, s>>>(b); }
 void launch_gather_b(const Batch<GatherArgs>& b, cudaStream_t s) { k_gather_b<<<b.total_ctas, 256, 0, s>>>(b); }
-void launch_reduce_b(const Batch<ReduceArgs>& b, cudaStream_t s) { k_param_reduce_b<<<b.total_ctas, 256, 0, s>>>(b); }
+void launch_reduce_b(const Batch<ReduceArgs>& b, cudaStream_t s) {
+    k_param_reduce_b<<<b.total_ctas, kReduceThreads, 0, s>>>(b);
+}
 void launch_finish_b(const Batch<FinishArgs>& b, cudaStream_t s) { k_finish_b<<<b.njobs, 256, 0, s>>>(b); }
 void launch_mark_base_b(const Batch<FinishArgs>& b, cudaStream_t s) { k_mark_base_b<<<b.njobs, 32, 0, s>>>(b); }
 

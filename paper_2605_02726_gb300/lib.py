@@ -66,7 +66,7 @@ def _load():
         "coolchic_param_count": (i64, [P(Arch)]),
         "coolchic_param_block": (i32, [i32, P(ctypes.c_char_p), P(i32), P(i32)]),
         "coolchic_workspace_bytes": (sz, [P(Arch), i32]),
-        "coolchic_kernels_per_iteration": (i32, [P(Arch)]),
+        "coolchic_kernel_launches": (i64, [P(Arch), i32]),
         "coolchic_encode_step": (i32, [P(Arch), P(HParams), vp, P(State), i32, vp, vp, sz, vp]),
         "coolchic_forward": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, i32, vp, vp, vp, sz, vp]),
         "coolchic_backward": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, i32, f32, vp, vp, vp, sz, vp]),
@@ -93,7 +93,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count", "coolchic_param_block",
-            "coolchic_workspace_bytes", "coolchic_kernels_per_iteration", "coolchic_encode_step", "coolchic_forward", "coolchic_backward",
+            "coolchic_workspace_bytes", "coolchic_kernel_launches", "coolchic_encode_step", "coolchic_forward", "coolchic_backward",
             "coolchic_rate_distortion", "coolchic_decode_image", "coolchic_timing_enable", "coolchic_timing_collect",
             "coolchic_timing_disable", "coolchic_last_error", "coolchic_version",
             "coolchic_rate_distortion_noalloc", "coolchic_batch_table_bytes", "coolchic_batch_create",
@@ -155,9 +155,9 @@ def latent_count(H: int, W: int) -> int:
     return int(_lib.coolchic_latent_count(ctypes.byref(arch(H, W))))
 
 
-def kernels_per_iteration(H: int, W: int) -> int:
-    """Kernel launches one encoder iteration makes for an H x W image."""
-    return int(_lib.coolchic_kernels_per_iteration(ctypes.byref(arch(H, W))))
+def kernel_launches(H: int, W: int, n_iters: int) -> int:
+    """Kernel launches of one encode_step call of n_iters iterations on an H x W image."""
+    return int(_lib.coolchic_kernel_launches(ctypes.byref(arch(H, W)), int(n_iters)))
 
 
 def param_blocks():

@@ -42,9 +42,14 @@ ARM_MAC_PER_LATENT = 3 * 648
 IFCE_NIN = (6, 5, 4)
 # Peak of the FP32 pipe: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (maximum SM clock).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# DRAM bytes per launch of the entropy-model kernel from the last ncu capture of this kernel
-# (None until taken for the current code).
-ARM_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per launch of the entropy-model kernel, from the ncu capture of the
+# current kernel in profiles/encode_step_kernels_512x768_full.md (cold caches: 2.16 MB read,
+# 1.81 MB written; the context-gradient planes it writes stay in L2).
+ARM_TRAFFIC_BYTES = 3.97e6
+# Algorithmic work of one whole encoder iteration per pixel: 1522 forward MAC per pixel (ARM 864,
+# IFCE 30, upsampling 45, synthesis 1x1 421, 3x3 convs 162), the adjoint and the parameter
+# gradients twice that again, 2 FLOP per MAC.
+STEP_FLOP_PER_PIXEL = 3 * 1522 * 2
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -256,7 +261,10 @@ def main():
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                 "traffic": ARM_TRAFFIC_BYTES, "launch_ms": arm_avg_s * 1e3,
                 "share_of_step": (arm_ms / max(arm_n, 1)) / ms_per_step,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 FLOP x 2070 MHz"}
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 FLOP x 2070 MHz",
+                "step": {"flop_per_pixel": STEP_FLOP_PER_PIXEL,
+                         "achieved": value * 1e6 * STEP_FLOP_PER_PIXEL / 1e12,
+                         "frac": value * 1e6 * STEP_FLOP_PER_PIXEL / 1e12 / FP32_PEAK_TFLOPS}}
 
     if rank == 0:
         cpu = None

@@ -17,8 +17,10 @@
 //
 // Parameter gradients are sums over latents of outer products, i.e. GEMMs with K = latents: each
 // warp transposes its 16 latents' factors into a private [feature][latent] shared tile and runs
-// 12 m16n8 output tiles over K = 16 per work unit, accumulating in registers for the whole kernel.
-// The 4 warps' accumulators are added in a fixed order at the end: one partial gradient per CTA.
+// the 6 dense m16n8 output tiles (W1 and b1, W2, the IFCE weights) over K = 16 per work unit,
+// accumulating in registers for the whole kernel.  The thin ones (b2, W3, Ws, b3 = bs: one or two
+// gradient rows) are per-lane FMAs on values the lane already holds.  The 4 warps' accumulators
+// are added in a fixed order at the end: one partial gradient per CTA.
 #include "cc_kernels.h"
 #include "cc_mma.cuh"
 
@@ -30,7 +32,7 @@ constexpr int kT = kWarps * 32;
 constexpr int kSld = 20;  // staging row stride: 16 latents + 4 (conflict-free fragment reads)
 // staging rows: U (gradient side) then V (activation side)
 constexpr int U_DA1 = 0, U_DA2 = 16, U_O = 32;
-constexpr int V_C = 48, V_H1 = 72, V_H2 = 88, V_R = 104, S_ROWS = 112;
+constexpr int V_C = 48, V_H1 = 72, V_R = 88, S_ROWS = 96;
 constexpr int kStage = S_ROWS * kSld;  // floats per warp
 // B-fragment table (per fragment, per lane: b0 hi, b1 hi, b0 lo, b1 lo)
 constexpr int FR_W1 = 0, FR_W2 = 6, FR_W3 = 10, FR_WS = 12, FR_BW2 = 15, FR_BW1 = 19, FR_N = 25;
@@ -117,27 +119,14 @@ __device__ __forceinline__ float ifce_out(const float* sIf, int k, int o, const 
     return acc;
 }
 
-// Parameter index of weight-gradient tile T, row, column (-1: padding); *second for b3/bs.
-__device__ int wgrad_index(int T, int row, int col, int* second) {
-    *second = -1;
+// Parameter index of weight-gradient tile T, row, column (-1: padding).
+__device__ int wgrad_index(int T, int row, int col) {
     if (T <= 2) {
         const int f = T * 8 + col;
         return f < 20 ? po::arm_w1 + row * 20 + f : (f == 20 ? po::arm_b1 + row : -1);
     }
     if (T <= 4) return po::arm_w2 + row * 16 + (T - 3) * 8 + col;
-    if (T == 5) return col == 4 ? po::arm_b2 + row : -1;
-    if (T <= 7) return row < 2 ? po::arm_w3 + row * 16 + (T - 6) * 8 + col : -1;
-    if (T <= 10) {
-        if (row >= 2) return -1;
-        const int f = (T - 8) * 8 + col;
-        if (f < 20) return po::arm_ws + row * 20 + f;
-        if (f == 20) {
-            *second = po::arm_bs + row;
-            return po::arm_b3 + row;
-        }
-        return -1;
-    }
-    if (row < 2 || row >= 14) return -1;
+    if (row < 2 || row >= 14) return -1;  // T == 5: IFCE output gradients x IFCE inputs
     const int k = (row - 2) >> 2, o = (row - 2) & 3, nin = ifce_nin(k);
     if (col < nin) return ifce_w_off(k) + o * nin + col;
     if (col == 6) return ifce_b_off(k) + o;
@@ -196,7 +185,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     const float s_b = a.params[po::arm_b3 + 1] + a.params[po::arm_bs + 1];
 
     float* st = sStage + wid * kStage;
-    if (BWD) {  // constant staging rows: C one (20) and zeros (21-23), R one (6) and zero (7), U_O zeros (14, 15)
+    if (BWD) {  // constant staging rows: C one (20) and zeros (21-23), R one (6) and zero (7), U_O zeros (0, 1, 14, 15)
         for (int j = lane; j < kSld; j += 32) {
             st[(V_C + 20) * kSld + j] = 1.f;
             st[(V_C + 21) * kSld + j] = 0.f;
@@ -204,16 +193,29 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             st[(V_C + 23) * kSld + j] = 0.f;
             st[(V_R + 6) * kSld + j] = 1.f;
             st[(V_R + 7) * kSld + j] = 0.f;
+            st[(U_O + 0) * kSld + j] = 0.f;
+            st[(U_O + 1) * kSld + j] = 0.f;
             st[(U_O + 14) * kSld + j] = 0.f;
             st[(U_O + 15) * kSld + j] = 0.f;
         }
         __syncwarp();
     }
-    float acc[12][4];
+    float acc[6][4];
 #pragma unroll
-    for (int T = 0; T < 12; ++T)
+    for (int T = 0; T < 6; ++T)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[T][q] = 0.f;
+    // per-lane sums: b2 of units 2t+cc (+8nt); W3[o][2t+cc (+8nt)]; Ws[o][t + 4q] (q = 5, t = 0: b3 = bs)
+    float sb2[2][2], sw3[2][2][2], sws[6][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            sb2[nt][cc] = 0.f;
+            sw3[nt][cc][0] = sw3[nt][cc][1] = 0.f;
+        }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sws[q][0] = sws[q][1] = 0.f;
     float rate_acc = 0.f;
 
     const int64_t N = a.N;
@@ -459,32 +461,31 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 st[(U_DA2 + uu) * kSld + gq + 8] = da2[nt][2 + cc] * mB;
                 st[(V_H1 + uu) * kSld + gq] = fmaxf(d1[nt][cc], 0.f);
                 st[(V_H1 + uu) * kSld + gq + 8] = fmaxf(d1[nt][2 + cc], 0.f);
-                st[(V_H2 + uu) * kSld + gq] = fmaxf(d2[nt][cc], 0.f);
-                st[(V_H2 + uu) * kSld + gq + 8] = fmaxf(d2[nt][2 + cc], 0.f);
+                // thin parameter gradients (d mu, d log b are zero for latents past the end)
+                const float hA = fmaxf(d2[nt][cc], 0.f), hB = fmaxf(d2[nt][2 + cc], 0.f);
+                sb2[nt][cc] += da2[nt][cc] * mA + da2[nt][2 + cc] * mB;
+                sw3[nt][cc][0] = fmaf(dmuA, hA, fmaf(dmuB, hB, sw3[nt][cc][0]));
+                sw3[nt][cc][1] = fmaf(dsA, hA, fmaf(dsB, hB, sw3[nt][cc][1]));
             }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            sws[q][0] = fmaf(dmuA, cA[q], fmaf(dmuB, cB[q], sws[q][0]));
+            sws[q][1] = fmaf(dsA, cA[q], fmaf(dsB, cB[q], sws[q][1]));
+        }
         {
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
                 st[(V_C + tq + 4 * q) * kSld + gq] = cA[q];
                 st[(V_C + tq + 4 * q) * kSld + gq + 8] = cB[q];
             }
-            // U_O rows t, t+4, t+8, t+12: 0 dmu, 1 ds, 2..13 df of grid (row-2)/4, 14..15 zero (preset)
+            // U_O rows t, t+4, t+8, t+12: 2..13 df of grid (row-2)/4; 0, 1, 14, 15 zero (preset)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int row = tq + 4 * q;
-                if (row >= 14) continue;
-                float vA, vB;
-                if (row == 0) {
-                    vA = dmuA;
-                    vB = dmuB;
-                } else if (row == 1) {
-                    vA = dsA;
-                    vB = dsB;
-                } else {
-                    const int kk = (row - 2) >> 2, o = (row - 2) & 3;
-                    vA = pA.k == kk ? sel(dfA, o) : 0.f;
-                    vB = pB.k == kk ? sel(dfB, o) : 0.f;
-                }
+                if (row < 2 || row >= 14) continue;
+                const int kk = (row - 2) >> 2, o = (row - 2) & 3;
+                const float vA = pA.k == kk ? sel(dfA, o) : 0.f;
+                const float vB = pB.k == kk ? sel(dfB, o) : 0.f;
                 st[(U_O + row) * kSld + gq] = vA * mA;
                 st[(U_O + row) * kSld + gq + 8] = vB * mB;
             }
@@ -514,20 +515,13 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             const AFrag UA1 = afrag(U_DA1), UA2 = afrag(U_DA2), UO = afrag(U_O);
             const AFrag VC0 = bfrag(V_C), VC1 = bfrag(V_C + 8), VC2 = bfrag(V_C + 16);
             const AFrag VH10 = bfrag(V_H1), VH11 = bfrag(V_H1 + 8);
-            const AFrag VH20 = bfrag(V_H2), VH21 = bfrag(V_H2 + 8);
             const AFrag VR = bfrag(V_R);
             mma3b(acc[0], UA1, VC0);
             mma3b(acc[1], UA1, VC1);
             mma3b(acc[2], UA1, VC2);
             mma3b(acc[3], UA2, VH10);
             mma3b(acc[4], UA2, VH11);
-            mma3b(acc[5], UA2, VC2);
-            mma3b(acc[6], UO, VH20);
-            mma3b(acc[7], UO, VH21);
-            mma3b(acc[8], UO, VC0);
-            mma3b(acc[9], UO, VC1);
-            mma3b(acc[10], UO, VC2);
-            mma3b(acc[11], UO, VR);
+            mma3b(acc[5], UO, VR);
         }
         __syncwarp();
     }
@@ -539,27 +533,69 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         block_sum<1>(v, scratch);
         if (tid == 0) a.rate_part[cta] = (double)v[0];
     }
-    if (!BWD) return;
-    // the 4 warps' gradient tiles, added in warp order
+    if constexpr (BWD) {
+    // the 4 warps' gradient tiles and per-lane sums, added in warp order
+    float simt[24];  // sb2 (4), sw3 (8), sws (12), each summed over the 8 lanes of the same t
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            simt[nt * 2 + cc] = sb2[nt][cc];
+            simt[4 + (nt * 2 + cc) * 2] = sw3[nt][cc][0];
+            simt[4 + (nt * 2 + cc) * 2 + 1] = sw3[nt][cc][1];
+        }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        simt[12 + 2 * q] = sws[q][0];
+        simt[12 + 2 * q + 1] = sws[q][1];
+    }
+#pragma unroll
+    for (int j = 0; j < 24; ++j) {
+        simt[j] += __shfl_xor_sync(0xffffffffu, simt[j], 4);
+        simt[j] += __shfl_xor_sync(0xffffffffu, simt[j], 8);
+        simt[j] += __shfl_xor_sync(0xffffffffu, simt[j], 16);
+    }
     __syncthreads();
-    float* sAcc = sStage;  // [warp][T][lane][4]
+    float* sAcc = sStage;                         // [warp][T][lane][4]
+    float* sSimt = sStage + kWarps * 6 * 32 * 4;  // [warp][t][24]
 #pragma unroll
-    for (int T = 0; T < 12; ++T)
+    for (int T = 0; T < 6; ++T)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) sAcc[((wid * 12 + T) * 32 + lane) * 4 + q] = acc[T][q];
+        for (int q = 0; q < 4; ++q) sAcc[((wid * 6 + T) * 32 + lane) * 4 + q] = acc[T][q];
+    if (lane < 4)
+#pragma unroll
+        for (int j = 0; j < 24; ++j) sSimt[(wid * 4 + lane) * 24 + j] = simt[j];
     __syncthreads();
     float* gp = a.gpart + (int64_t)cta * po::arm_block;
-    for (int e = tid; e < 12 * 32 * 4; e += kT) {
+    for (int e = tid; e < 6 * 32 * 4; e += kT) {
         const int T = e >> 7, l = (e >> 2) & 31, q = e & 3;
         const int row = (l >> 2) + (q >= 2 ? 8 : 0), col = 2 * (l & 3) + (q & 1);
-        int second;
-        const int idx = wgrad_index(T, row, col, &second);
+        const int idx = wgrad_index(T, row, col);
         if (idx < 0) continue;
         float s = 0.f;
-        for (int w = 0; w < kWarps; ++w) s += sAcc[((w * 12 + T) * 32 + l) * 4 + q];
+        for (int w = 0; w < kWarps; ++w) s += sAcc[((w * 6 + T) * 32 + l) * 4 + q];
         gp[idx] = s;
-        if (second >= 0) gp[second] = s;
     }
+    if (tid < 4 * 24) {
+        const int t = tid / 24, j = tid - t * 24;
+        float s = 0.f;
+        for (int w = 0; w < kWarps; ++w) s += sSimt[(w * 4 + t) * 24 + j];
+        if (j < 4) {
+            gp[po::arm_b2 + (j >> 1) * 8 + 2 * t + (j & 1)] = s;
+        } else if (j < 12) {
+            const int jj = j - 4, u = (jj >> 2) * 8 + 2 * t + ((jj >> 1) & 1), o = jj & 1;
+            gp[po::arm_w3 + o * 16 + u] = s;
+        } else {
+            const int q = (j - 12) >> 1, o = (j - 12) & 1, f = t + 4 * q;
+            if (q < 5) {
+                gp[po::arm_ws + o * 20 + f] = s;
+            } else if (t == 0) {
+                gp[po::arm_b3 + o] = s;
+                gp[po::arm_bs + o] = s;
+            }
+        }
+    }
+    }  // BWD
 }
 
 template <int PASS>

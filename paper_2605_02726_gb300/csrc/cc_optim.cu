@@ -48,17 +48,43 @@ __device__ __forceinline__ float block_sum_clipped(const float* __restrict__ pla
     return acc;
 }
 
+// one row of a B-wide block, clipped to the plane
+template <int B>
+__device__ __forceinline__ float row_sum_clipped(const float* __restrict__ plane, int h, int w, int r, int c0) {
+    float acc = 0.f;
+    if (r < h)
+#pragma unroll
+        for (int cc = 0; cc < B; ++cc)
+            if (c0 + cc < w) acc += __ldg(plane + (int64_t)r * w + c0 + cc);
+    return acc;
+}
+
+// Eight consecutive threads per (g, cell): thread p sums row p of the 8x8 block of dR0, row p of
+// the 4x4 block of dR1 (p < 4) and row p of the 2x2 block of dR2 (p < 2); the eight partial sums
+// are added by shuffles in a fixed order.
 __device__ __forceinline__ void ifce_body(const IfceArgs& a, int cta, int ncta) {
     const Geom& g = a.g;
     const int n3 = g.h[3] * g.w[3];
     const int64_t n0 = (int64_t)g.h[0] * g.w[0], n1 = (int64_t)g.h[1] * g.w[1], n2 = (int64_t)g.h[2] * g.w[2];
-    for (int64_t e = cta * (int64_t)blockDim.x + threadIdx.x; e < 4 * (int64_t)n3; e += (int64_t)ncta * blockDim.x) {
-        const int gg = 3 + (int)(e / n3), cell = (int)(e % n3);
+    const int64_t total = 4 * (int64_t)n3 * 8;  // a multiple of 8: the 8 threads of a task share a warp
+    // the loop runs while any lane of the warp has a task, so that every lane takes part in the shuffles
+    for (int64_t e = cta * (int64_t)blockDim.x + threadIdx.x; e - (int)(threadIdx.x & 31) < total;
+         e += (int64_t)ncta * blockDim.x) {
+        const bool live = e < total;
+        const int64_t task = live ? e >> 3 : 0;
+        const int p = (int)(e & 7);
+        const int gg = 3 + (int)(task / n3), cell = (int)(task % n3);
         const int r3 = cell / g.w[3], c3 = cell - r3 * g.w[3];
-        float acc = block_sum_clipped<8>(a.dR0 + (gg - 1) * n0, g.h[0], g.w[0], 8 * r3, 8 * c3);
-        acc += block_sum_clipped<4>(a.dR1 + (gg - 2) * n1, g.h[1], g.w[1], 4 * r3, 4 * c3);
-        acc += block_sum_clipped<2>(a.dR2 + (gg - 3) * n2, g.h[2], g.w[2], 2 * r3, 2 * c3);
-        a.Q[e] = acc;
+        float acc = 0.f;
+        if (live) {
+            acc = row_sum_clipped<8>(a.dR0 + (gg - 1) * n0, g.h[0], g.w[0], 8 * r3 + p, 8 * c3);
+            if (p < 4) acc += row_sum_clipped<4>(a.dR1 + (gg - 2) * n1, g.h[1], g.w[1], 4 * r3 + p, 4 * c3);
+            if (p < 2) acc += row_sum_clipped<2>(a.dR2 + (gg - 3) * n2, g.h[2], g.w[2], 2 * r3 + p, 2 * c3);
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (live && p == 0) a.Q[task] = acc;
     }
 }
 __global__ void k_ifce_cells(IfceArgs a) {
@@ -370,7 +396,7 @@ FinishArgs finish_args(const Work& w, const Hp& hp, int have_arm, int have_conv,
 }
 
 int relax_ctas(const Work& w) { return grid_for(w.N, 256, 8); }
-int ifce_ctas(const Work& w) { return grid_for(4 * (int64_t)w.g.h[kNIfce] * w.g.w[kNIfce], 128, 8); }
+int ifce_ctas(const Work& w) { return grid_for(32 * (int64_t)w.g.h[kNIfce] * w.g.w[kNIfce], 128, 16); }
 int gather_ctas(const Work& w) { return grid_for(w.N, 256, 8); }
 int reduce_ctas() { return kReduceCtas; }
 

@@ -650,20 +650,20 @@ void launch_arm(const Work& w, const float* params, int pass, float grad_scale, 
     const size_t sm = arm_smem_bytes(pass);
     const int grid = w.n_cta_arm;
     switch (pass) {
-        case PASS_FWD: k_arm<PASS_FWD><<<grid, kT, sm, s>>>(a); break;
-        case PASS_FWD_STORE: k_arm<PASS_FWD_STORE><<<grid, kT, sm, s>>>(a); break;
-        case PASS_FWD_BWD: k_arm<PASS_FWD_BWD><<<grid, kT, sm, s>>>(a); break;
-        default: k_arm<PASS_BWD_LOAD><<<grid, kT, sm, s>>>(a); break;
+        case PASS_FWD: launch_pdl(k_arm<PASS_FWD>, grid, kT, sm, s, a); break;
+        case PASS_FWD_STORE: launch_pdl(k_arm<PASS_FWD_STORE>, grid, kT, sm, s, a); break;
+        case PASS_FWD_BWD: launch_pdl(k_arm<PASS_FWD_BWD>, grid, kT, sm, s, a); break;
+        default: launch_pdl(k_arm<PASS_BWD_LOAD>, grid, kT, sm, s, a); break;
     }
 }
 
 void launch_arm_b(const Batch<ArmArgs>& b, int pass, cudaStream_t s) {
     const size_t sm = arm_smem_bytes(pass);
     switch (pass) {
-        case PASS_FWD: k_arm_b<PASS_FWD><<<b.total_ctas, kT, sm, s>>>(b); break;
-        case PASS_FWD_STORE: k_arm_b<PASS_FWD_STORE><<<b.total_ctas, kT, sm, s>>>(b); break;
-        case PASS_FWD_BWD: k_arm_b<PASS_FWD_BWD><<<b.total_ctas, kT, sm, s>>>(b); break;
-        default: k_arm_b<PASS_BWD_LOAD><<<b.total_ctas, kT, sm, s>>>(b); break;
+        case PASS_FWD: launch_pdl(k_arm_b<PASS_FWD>, b.total_ctas, kT, sm, s, b); break;
+        case PASS_FWD_STORE: launch_pdl(k_arm_b<PASS_FWD_STORE>, b.total_ctas, kT, sm, s, b); break;
+        case PASS_FWD_BWD: launch_pdl(k_arm_b<PASS_FWD_BWD>, b.total_ctas, kT, sm, s, b); break;
+        default: launch_pdl(k_arm_b<PASS_BWD_LOAD>, b.total_ctas, kT, sm, s, b); break;
     }
 }
 

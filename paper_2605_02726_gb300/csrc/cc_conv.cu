@@ -411,11 +411,11 @@ void launch_conv(const Work& w, const float* params, const float* image, int pas
                  float* xhat_out, cudaStream_t s) {
     const ConvArgs a = conv_args(w, params, image, grad_scale, xhat_out);
     if (pass_bwd(pass))
-        k_conv<PASS_FWD_BWD><<<w.n_cta_conv, kThreads, 0, s>>>(a);
+        launch_pdl(k_conv<PASS_FWD_BWD>, w.n_cta_conv, kThreads, 0, s, a);
     else
-        k_conv<PASS_FWD><<<w.n_cta_conv, kThreads, 0, s>>>(a);
+        launch_pdl(k_conv<PASS_FWD>, w.n_cta_conv, kThreads, 0, s, a);
 }
 
-void launch_conv_b(const Batch<ConvArgs>& b, cudaStream_t s) { k_conv_b<PASS_FWD_BWD><<<b.total_ctas, kThreads, 0, s>>>(b); }
+void launch_conv_b(const Batch<ConvArgs>& b, cudaStream_t s) { launch_pdl(k_conv_b<PASS_FWD_BWD>, b.total_ctas, kThreads, 0, s, b); }
 
 }  // namespace cc

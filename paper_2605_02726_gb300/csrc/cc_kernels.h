@@ -78,14 +78,42 @@ __device__ __forceinline__ int batch_job(const int* __restrict__ cb, int nj) {
     return j;
 }
 
-// Copies job j's arguments into shared memory (all threads), then synchronises.
+// Programmatic dependent launch: the kernels of an iteration are launched with programmatic stream
+// serialization, so a kernel's CTAs may be scheduled while its predecessor in the stream finishes.
+// Every such kernel lets its own successor start as soon as all of its CTAs are running
+// (launch_dependents) and reads nothing that earlier kernels wrote before griddepcontrol.wait,
+// which returns once the predecessor has completed and its writes are visible.  Both happen in
+// the argument fetches below; only kernel parameters and the static argument tables are read
+// before the wait.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline void launch_pdl(void (*kern)(P...), int grid, int block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Copies job j's arguments into shared memory (all threads), then synchronises and waits for the
+// predecessor kernel.
 template <typename A>
 __device__ __forceinline__ void batch_fetch(const A* __restrict__ args, int j, A& sa) {
     static_assert(sizeof(A) % 4 == 0, "argument structs are copied as 32-bit words");
+    pdl_trigger();
     const int* src = reinterpret_cast<const int*>(args + j);
     int* dst = reinterpret_cast<int*>(&sa);
     for (int i = threadIdx.x; i < (int)(sizeof(A) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
     __syncthreads();
+    pdl_wait();
 }
 
 // Copies a single-job launch's arguments into shared memory, so that the kernel body runs on
@@ -97,11 +125,13 @@ __device__ __forceinline__ void param_fetch(const A& a, A& sa) {
     constexpr int NW = (int)(sizeof(A) / 4);
     const int* src = reinterpret_cast<const int*>(&a);
     int* dst = reinterpret_cast<int*>(&sa);
+    pdl_trigger();
     // word w goes through lane w % 32 of the first warp; constant indices keep `a` in param space
 #pragma unroll
     for (int w = 0; w < NW; ++w)
         if ((int)threadIdx.x == (w & 31)) dst[w] = src[w];
     __syncthreads();
+    pdl_wait();
 }
 
 // Argument structs of the kernels (filled by the launchers and by the batch planner).

@@ -403,24 +403,24 @@ int reduce_ctas() { return kReduceCtas; }
 // ---- single-job launches
 void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, uint64_t seed,
                   int relax, cudaStream_t s) {
-    k_relax<<<relax_ctas(w), 256, 0, s>>>(relax_args(w, y, step_dev, step_host, seed, relax));
+    launch_pdl(k_relax, relax_ctas(w), 256, 0, s, relax_args(w, y, step_dev, step_host, seed, relax));
 }
 
 void launch_gather(const Work& w, const float* params, int relax, float* grad_out, float* y, float* m, float* v,
                    const Hp& hp, const int64_t* step_dev, cudaStream_t s, bool relax_next) {
     (void)params;
-    k_ifce_cells<<<ifce_ctas(w), 128, 0, s>>>(ifce_args(w));
-    k_gather<<<gather_ctas(w), 256, 0, s>>>(gather_args(w, relax, grad_out, y, m, v, hp, step_dev, relax_next));
+    launch_pdl(k_ifce_cells, ifce_ctas(w), 128, 0, s, ifce_args(w));
+    launch_pdl(k_gather, gather_ctas(w), 256, 0, s, gather_args(w, relax, grad_out, y, m, v, hp, step_dev, relax_next));
 }
 
 void launch_param_reduce(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,
                          const Hp& hp, const int64_t* step_dev, cudaStream_t s) {
-    k_param_reduce<<<kReduceCtas, kReduceThreads, 0, s>>>(reduce_args(w, params, m, v, grad_out, out_scale, hp, step_dev));
+    launch_pdl(k_param_reduce, kReduceCtas, kReduceThreads, 0, s, reduce_args(w, params, m, v, grad_out, out_scale, hp, step_dev));
 }
 
 void launch_finish(const Work& w, const Hp& hp, int have_arm, int have_conv, double* rd_out, int64_t* step_dev,
                    int mark_base, int increment, cudaStream_t s) {
-    k_finish<<<1, 256, 0, s>>>(finish_args(w, hp, have_arm, have_conv, rd_out, 3, step_dev, mark_base, increment));
+    launch_pdl(k_finish, 1, 256, 0, s, finish_args(w, hp, have_arm, have_conv, rd_out, 3, step_dev, mark_base, increment));
 }
 
 void launch_mark_base(const Work& w, const int64_t* step_dev, cudaStream_t s) {
@@ -428,13 +428,13 @@ void launch_mark_base(const Work& w, const int64_t* step_dev, cudaStream_t s) {
 }
 
 // ---- multi-job launches
-void launch_relax_b(const Batch<RelaxArgs>& b, cudaStream_t s) { k_relax_b<<<b.total_ctas, 256, 0, s>>>(b); }
-void launch_ifce_b(const Batch<IfceArgs>& b, cudaStream_t s) { k_ifce_cells_b<<<b.total_ctas, 128, 0, s>>>(b); }
-void launch_gather_b(const Batch<GatherArgs>& b, cudaStream_t s) { k_gather_b<<<b.total_ctas, 256, 0, s>>>(b); }
+void launch_relax_b(const Batch<RelaxArgs>& b, cudaStream_t s) { launch_pdl(k_relax_b, b.total_ctas, 256, 0, s, b); }
+void launch_ifce_b(const Batch<IfceArgs>& b, cudaStream_t s) { launch_pdl(k_ifce_cells_b, b.total_ctas, 128, 0, s, b); }
+void launch_gather_b(const Batch<GatherArgs>& b, cudaStream_t s) { launch_pdl(k_gather_b, b.total_ctas, 256, 0, s, b); }
 void launch_reduce_b(const Batch<ReduceArgs>& b, cudaStream_t s) {
-    k_param_reduce_b<<<b.total_ctas, kReduceThreads, 0, s>>>(b);
+    launch_pdl(k_param_reduce_b, b.total_ctas, kReduceThreads, 0, s, b);
 }
-void launch_finish_b(const Batch<FinishArgs>& b, cudaStream_t s) { k_finish_b<<<b.njobs, 256, 0, s>>>(b); }
+void launch_finish_b(const Batch<FinishArgs>& b, cudaStream_t s) { launch_pdl(k_finish_b, b.njobs, 256, 0, s, b); }
 void launch_mark_base_b(const Batch<FinishArgs>& b, cudaStream_t s) { k_mark_base_b<<<b.njobs, 32, 0, s>>>(b); }
 
 }  // namespace cc

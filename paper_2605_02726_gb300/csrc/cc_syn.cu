@@ -426,24 +426,24 @@ int syn_fwd_ctas(const Work& w) {
 void launch_syn_forward(const Work& w, const float* params, int pass, cudaStream_t s) {
     const SynArgs a = syn_args(w, params);
     if (pass == PASS_FWD_STORE)
-        k_syn_fwd<PASS_FWD_STORE><<<syn_fwd_ctas(w), kSynThreads, 0, s>>>(a);
+        launch_pdl(k_syn_fwd<PASS_FWD_STORE>, syn_fwd_ctas(w), kSynThreads, 0, s, a);
     else
-        k_syn_fwd<PASS_FWD><<<syn_fwd_ctas(w), kSynThreads, 0, s>>>(a);
+        launch_pdl(k_syn_fwd<PASS_FWD>, syn_fwd_ctas(w), kSynThreads, 0, s, a);
 }
 
 void launch_syn_backward(const Work& w, const float* params, int pass, cudaStream_t s) {
     const SynArgs a = syn_args(w, params);
     if (pass == PASS_BWD_LOAD)
-        k_syn_bwd<PASS_BWD_LOAD><<<w.n_cta_syn, kSynThreads, syn_bwd_smem(), s>>>(a);
+        launch_pdl(k_syn_bwd<PASS_BWD_LOAD>, w.n_cta_syn, kSynThreads, syn_bwd_smem(), s, a);
     else
-        k_syn_bwd<PASS_FWD_BWD><<<w.n_cta_syn, kSynThreads, syn_bwd_smem(), s>>>(a);
+        launch_pdl(k_syn_bwd<PASS_FWD_BWD>, w.n_cta_syn, kSynThreads, syn_bwd_smem(), s, a);
 }
 
 void launch_syn_fwd_b(const Batch<SynArgs>& b, cudaStream_t s) {
-    k_syn_fwd_b<PASS_FWD><<<b.total_ctas, kSynThreads, 0, s>>>(b);
+    launch_pdl(k_syn_fwd_b<PASS_FWD>, b.total_ctas, kSynThreads, 0, s, b);
 }
 void launch_syn_bwd_b(const Batch<SynArgs>& b, cudaStream_t s) {
-    k_syn_bwd_b<PASS_FWD_BWD><<<b.total_ctas, kSynThreads, syn_bwd_smem(), s>>>(b);
+    launch_pdl(k_syn_bwd_b<PASS_FWD_BWD>, b.total_ctas, kSynThreads, syn_bwd_smem(), s, b);
 }
 
 }  // namespace cc

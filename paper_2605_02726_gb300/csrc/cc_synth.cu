@@ -199,18 +199,18 @@ UpAdjArgs up_adj_args(const Work& w, const float* params, int st) {  // stage st
 
 // ---- single-job launches
 void launch_up_forward(const Work& w, const float* params, cudaStream_t s) {
-    for (int m = kL - 2; m >= 1; --m) k_up_fwd<<<up_fwd_ctas(w, m), kUpThreads, 0, s>>>(up_fwd_args(w, params, m));
+    for (int m = kL - 2; m >= 1; --m) launch_pdl(k_up_fwd, up_fwd_ctas(w, m), kUpThreads, 0, s, up_fwd_args(w, params, m));
 }
 
 void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
     for (int st = 1; st < kL; ++st)
-        k_up_adj<<<w.n_cta_up[st], kUpThreads, (size_t)w.g.w[st - 1] * sizeof(float), s>>>(up_adj_args(w, params, st));
+        launch_pdl(k_up_adj, w.n_cta_up[st], kUpThreads, (size_t)w.g.w[st - 1] * sizeof(float), s, up_adj_args(w, params, st));
 }
 
 // ---- multi-job launches (max_wt: the widest row any job's stage reads, for the shared row buffer)
-void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s) { k_up_fwd_b<<<b.total_ctas, kUpThreads, 0, s>>>(b); }
+void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s) { launch_pdl(k_up_fwd_b, b.total_ctas, kUpThreads, 0, s, b); }
 void launch_up_adj_b(const Batch<UpAdjArgs>& b, int max_wt, cudaStream_t s) {
-    k_up_adj_b<<<b.total_ctas, kUpThreads, (size_t)max_wt * sizeof(float), s>>>(b);
+    launch_pdl(k_up_adj_b, b.total_ctas, kUpThreads, (size_t)max_wt * sizeof(float), s, b);
 }
 
 }  // namespace cc

@@ -24,7 +24,7 @@ _lib = None
 
 N_GRIDS = 7
 N_PARAMS = 1415
-MODE_NOISE, MODE_HARD, MODE_IDENTITY = 0, 1, 2
+MODE_NOISE, MODE_HARD, MODE_IDENTITY, MODE_SOFTROUND = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -59,14 +59,19 @@ def _load():
             "orc_context_offsets": (None, [ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
             "orc_splitmix64_mix": (u64, [u64]),
             "orc_noise": (dbl, [u64, i64, i64]),
+            "orc_gauss": (dbl, [u64, i64, i64]),
+            "orc_softround": (dbl, [dbl, dbl, D]),
             "orc_laplace_prob": (dbl, [dbl, dbl, dbl, D, D]),
             "orc_upsample": (None, [c_int, c_int, c_int, c_int, D, D, D]),
             "orc_conv3x3_res": (None, [c_int, c_int, D, D, D, D]),
-            "orc_forward": (dbl, [c_int, c_int, D, D, D, c_int, u64, i64, dbl, D, D, D, D, D, D]),
-            "orc_loss_grad": (dbl, [c_int, c_int, D, D, D, c_int, u64, i64, dbl, D, D, D, D]),
+            "orc_forward": (dbl, [c_int, c_int, D, D, D, c_int, u64, i64, dbl, dbl, dbl, D, D, D, D, D, D]),
+            "orc_loss_grad": (dbl, [c_int, c_int, D, D, D, c_int, u64, i64, dbl, dbl, dbl, D, D, D, D]),
             "orc_adam": (None, [i64, D, D, D, D, i64, dbl, dbl, dbl, dbl]),
             "orc_encode": (None, [c_int, c_int, D, D, D, D, D, D, D, ctypes.POINTER(i64), c_int, u64,
                                   dbl, dbl, dbl, dbl, dbl, D, D, D]),
+            "orc_encode_schedule": (None, [c_int, c_int, D, D, D, D, D, D, D, ctypes.POINTER(i64), c_int,
+                                           u64, dbl, dbl, dbl, dbl, dbl, dbl, dbl, i64, dbl, dbl, dbl, D,
+                                           D, D]),
             "orc_cdf_q16": (i64, [ctypes.c_int32, i64]),
             "orc_table_entry": (i64, [c_int, c_int]),
             "orc_decode_probs": (None, [c_int, c_int, I32, F32, I32, I32, U32]),
@@ -128,6 +133,19 @@ def noise(seed: int, t: int, n: int) -> np.ndarray:
     return np.array([lib.orc_noise(seed, t, i) for i in range(n)], dtype=np.float64)
 
 
+def gauss(seed: int, t: int, n: int) -> np.ndarray:
+    """Box-Muller standard normals of latents 0..n-1 at step t (the soft-round proxy's noise)."""
+    lib = _load()
+    return np.array([lib.orc_gauss(seed, t, i) for i in range(n)], dtype=np.float64)
+
+
+def softround(x: float, T: float):
+    """(s_T(x), s_T'(x)), Eq. 13."""
+    d = ctypes.c_double()
+    v = _load().orc_softround(float(x), float(T), ctypes.byref(d))
+    return v, d.value
+
+
 def laplace_prob(y: float, mu: float, b: float):
     dy, dlb = ctypes.c_double(), ctypes.c_double()
     p = _load().orc_laplace_prob(y, mu, b, ctypes.byref(dy), ctypes.byref(dlb))
@@ -155,8 +173,10 @@ def conv3x3_res(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------------------------
 # whole step
 # ---------------------------------------------------------------------------------------------
-def forward(image, latents, params, *, lam, mode=MODE_NOISE, seed=0, step=0, per_latent=False):
-    """Returns dict(loss, rate_bits, mse[, mu, logb, bits, xhat])."""
+def forward(image, latents, params, *, lam, mode=MODE_NOISE, seed=0, step=0, sigma=0.0, temp=1.0,
+            per_latent=False):
+    """Returns dict(loss, rate_bits, mse[, mu, logb, bits, xhat]); sigma and temp are used by
+    MODE_SOFTROUND (Eq. 12)."""
     image, latents, params = _f64(image), _f64(latents), _f64(params)
     _, H, W = image.shape
     N = latent_count(H, W)
@@ -165,7 +185,7 @@ def forward(image, latents, params, *, lam, mode=MODE_NOISE, seed=0, step=0, per
     if per_latent:
         mu, logb, bits = (np.zeros(N) for _ in range(3))
         xhat = np.zeros_like(image)
-    loss = _load().orc_forward(H, W, _d(image), _d(latents), _d(params), mode, seed, step, lam,
+    loss = _load().orc_forward(H, W, _d(image), _d(latents), _d(params), mode, seed, step, sigma, temp, lam,
                                ctypes.byref(rate), ctypes.byref(mse), _d(mu), _d(logb), _d(bits),
                                _d(xhat))
     out = dict(loss=loss, rate_bits=rate.value, mse=mse.value)
@@ -174,15 +194,15 @@ def forward(image, latents, params, *, lam, mode=MODE_NOISE, seed=0, step=0, per
     return out
 
 
-def loss_grad(image, latents, params, *, lam, mode=MODE_NOISE, seed=0, step=0):
+def loss_grad(image, latents, params, *, lam, mode=MODE_NOISE, seed=0, step=0, sigma=0.0, temp=1.0):
     """Returns dict(loss, rate_bits, mse, grad_latents, grad_params)."""
     image, latents, params = _f64(image), _f64(latents), _f64(params)
     _, H, W = image.shape
     gy = np.zeros(latents.shape[0])
     gp = np.zeros(N_PARAMS)
     rate, mse = ctypes.c_double(), ctypes.c_double()
-    loss = _load().orc_loss_grad(H, W, _d(image), _d(latents), _d(params), mode, seed, step, lam,
-                                 ctypes.byref(rate), ctypes.byref(mse), _d(gy), _d(gp))
+    loss = _load().orc_loss_grad(H, W, _d(image), _d(latents), _d(params), mode, seed, step, sigma, temp,
+                                 lam, ctypes.byref(rate), ctypes.byref(mse), _d(gy), _d(gp))
     return dict(loss=loss, rate_bits=rate.value, mse=mse.value, grad_latents=gy, grad_params=gp)
 
 
@@ -213,6 +233,23 @@ def encode(image, state: State, n_iters, *, lam, seed, lr=1e-2, b1=0.9, b2=0.999
     _load().orc_encode(H, W, _d(image), _d(state.latents), _d(state.params), _d(state.m_lat),
                        _d(state.v_lat), _d(state.m_par), _d(state.v_par), ctypes.byref(step), n_iters,
                        seed, lam, lr, b1, b2, eps, _d(loss), _d(rate), _d(mse))
+    state.step = step.value
+    return dict(loss=loss, rate_bits=rate, mse=mse)
+
+
+def encode_schedule(image, state: State, n_iters, *, lam, seed, n_main, lr_max=1e-2, lr_min=1e-5,
+                    sigma0=0.22, sigma1=0.15, temp0=0.35, temp1=0.08, b1=0.9, b2=0.999, eps=1e-8):
+    """The paper's encoder schedule (Sec. IV-C/D, Table I) for n_iters iterations from state.step:
+    soft-round + Gaussian proxy with linear sigma / T and cosine learning rate over the main stage
+    (steps < n_main), then the hard-round stage (latents frozen, parameters at lr_min)."""
+    image = _f64(image)
+    _, H, W = image.shape
+    loss, rate, mse = (np.zeros(n_iters) for _ in range(3))
+    step = ctypes.c_int64(state.step)
+    _load().orc_encode_schedule(H, W, _d(image), _d(state.latents), _d(state.params), _d(state.m_lat),
+                                _d(state.v_lat), _d(state.m_par), _d(state.v_par), ctypes.byref(step), n_iters,
+                                seed, lam, lr_max, lr_min, sigma0, sigma1, temp0, temp1, int(n_main), b1, b2, eps,
+                                _d(loss), _d(rate), _d(mse))
     state.step = step.value
     return dict(loss=loss, rate_bits=rate, mse=mse)
 

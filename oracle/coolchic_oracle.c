@@ -9,8 +9,11 @@
  *
  * What it computes (paper section / equation in brackets):
  *   - latent grids  y^(k), k = 0..L-1, shape ceil(H/2^k) x ceil(W/2^k)      [Sec. III-A1, Eq. 1]
- *   - noise relaxation  y~ = y + u, u ~ U(-1/2, 1/2) from a counter hash    [Sec. IV-C; Eq. 13 is
- *     the paper's own proxy, replaced here by the additive uniform proxy]
+ *   - noise relaxation  y~ = y + u, u ~ U(-1/2, 1/2) from a counter hash    [Sec. IV-C; the workload's
+ *     additive uniform proxy]
+ *   - the paper's proxy  y~ = s_T(s_T(y) + sigma n), n ~ N(0, 1) by Box-Muller  [Sec. IV-C, Eq. 12-13]
+ *     from the same counter hash, with the linear sigma / T and cosine learning-rate schedules of
+ *     the main stage and the hard-round stage with frozen latents            [Sec. IV-D, Table I]
  *   - causal spatial context s_i and inter-feature context f_i = IFCE_k(r_i)  [Sec. III-A1/A2, Eqs. 4-5]
  *   - ARM MLP + linear stabilizer -> (mu, log b)                             [Eq. 4, Eq. 9, Sec. III-C]
  *   - Laplace interval probability and rate  -log2 p                         [Eq. 3, Eq. 11]
@@ -32,6 +35,9 @@
  * independent rows; every reduction goes through per-row partial arrays summed serially,
  * so results do not depend on the thread count.
  */
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -118,10 +124,32 @@ uint64_t orc_splitmix64_mix(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-double orc_noise(uint64_t seed, int64_t t, int64_t i) {
+static uint64_t counter_hash(uint64_t seed, int64_t t, int64_t i) {
     uint64_t ctr = ((uint64_t)t << 32) + (uint64_t)i;
-    uint64_t h = orc_splitmix64_mix(seed ^ (ctr * 0x9E3779B97F4A7C15ULL));
-    return (double)(h >> 40) * (1.0 / 16777216.0) - 0.5;
+    return orc_splitmix64_mix(seed ^ (ctr * 0x9E3779B97F4A7C15ULL));
+}
+
+double orc_noise(uint64_t seed, int64_t t, int64_t i) {
+    return (double)(counter_hash(seed, t, i) >> 40) * (1.0 / 16777216.0) - 0.5;
+}
+
+/* Standard normal n from the same hash by the Box-Muller transform (Box and Muller, 1958):
+ * u1 = (bits 40..63 + 1/2) / 2^24 in (0, 1), u2 = bits 16..39 / 2^24 in [0, 1),
+ * n = sqrt(-2 ln u1) cos(2 pi u2). */
+double orc_gauss(uint64_t seed, int64_t t, int64_t i) {
+    uint64_t h = counter_hash(seed, t, i);
+    double u1 = ((double)(h >> 40) + 0.5) * (1.0 / 16777216.0);
+    double u2 = (double)((h >> 16) & 0xFFFFFFULL) * (1.0 / 16777216.0);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+/* Soft rounding, Eq. 13 (after Agustsson and Theis):
+ *   s_T(x) = floor(x) + 1/2 + tanh(D / T) / (2 tanh(1 / (2T))),  D = x - floor(x) - 1/2,
+ * and its derivative (1 - tanh^2(D / T)) / (2 T tanh(1 / (2T))). */
+double orc_softround(double x, double T, double* deriv) {
+    double fl = floor(x), d = x - fl - 0.5, th = tanh(d / T), den = 2.0 * tanh(0.5 / T);
+    if (deriv) *deriv = (1.0 - th * th) / (T * den);
+    return fl + 0.5 + th / den;
 }
 
 /* ----------------------------------------------------------------------------------------
@@ -408,7 +436,15 @@ static void synth_pixel(const double* P, const double* z, double* a, double* t) 
 /* ----------------------------------------------------------------------------------------
  * Whole forward and adjoint.
  * ---------------------------------------------------------------------------------------- */
-enum { MODE_NOISE = 0, MODE_HARD = 1, MODE_IDENTITY = 2 };
+enum { MODE_NOISE = 0, MODE_HARD = 1, MODE_IDENTITY = 2, MODE_SOFTROUND = 3 };
+
+/* How the latents are relaxed: MODE_SOFTROUND uses sigma and temp (Eq. 12). */
+typedef struct {
+    int mode;
+    uint64_t seed;
+    int64_t t;
+    double sigma, temp;
+} relax_t;
 
 typedef struct {
     geom_t g;
@@ -441,9 +477,28 @@ static const double* stage_channel(const fwd_t* F, int m, int j) {
     return F->up[m] + (int64_t)(j - 1) * F->g.h[m] * F->g.w[m];
 }
 
-static double run_forward(int H, int W, const double* img, const double* y, const double* P, int mode,
-                          uint64_t seed, int64_t t, double lambda, fwd_t* F, double* rate_out,
-                          double* mse_out) {
+/* y~ of latent i and, when jac is non-null, dy~/dy */
+static double relax_one(const relax_t* R, double y, int64_t i, double* jac) {
+    double j = 1.0, v;
+    if (R->mode == MODE_NOISE) {
+        v = y + orc_noise(R->seed, R->t, i);
+    } else if (R->mode == MODE_HARD) {
+        v = rint(y);
+        j = 0.0;
+    } else if (R->mode == MODE_SOFTROUND) {
+        double d1, d2;
+        double s1 = orc_softround(y, R->temp, &d1);
+        v = orc_softround(s1 + R->sigma * orc_gauss(R->seed, R->t, i), R->temp, &d2);
+        j = d2 * d1;
+    } else {
+        v = y;
+    }
+    if (jac) *jac = j;
+    return v;
+}
+
+static double run_forward(int H, int W, const double* img, const double* y, const double* P,
+                          const relax_t* R, double lambda, fwd_t* F, double* rate_out, double* mse_out) {
     geom_init(&F->g, H, W);
     const geom_t* g = &F->g;
     int64_t N = g->off[NG], HW = (int64_t)H * W;
@@ -451,14 +506,7 @@ static double run_forward(int H, int W, const double* img, const double* y, cons
     F->mu = (double*)malloc(sizeof(double) * N);
     F->logb = (double*)malloc(sizeof(double) * N);
     F->bits = (double*)malloc(sizeof(double) * N);
-    for (int64_t i = 0; i < N; ++i) {
-        if (mode == MODE_NOISE)
-            F->yt[i] = y[i] + orc_noise(seed, t, i);
-        else if (mode == MODE_HARD)
-            F->yt[i] = rint(y[i]);
-        else
-            F->yt[i] = y[i];
-    }
+    for (int64_t i = 0; i < N; ++i) F->yt[i] = relax_one(R, y[i], i, NULL);
     /* entropy model: Eqs. 2-5, 9, 11 */
     for (int k = 0; k < NG; ++k) {
 #pragma omp parallel for schedule(static)
@@ -515,11 +563,12 @@ static double run_forward(int H, int W, const double* img, const double* y, cons
 }
 
 double orc_forward(int H, int W, const double* img, const double* y, const double* P, int mode,
-                   uint64_t seed, int64_t t, double lambda, double* rate_out, double* mse_out,
-                   double* mu_out, double* logb_out, double* bits_out, double* xhat_out) {
+                   uint64_t seed, int64_t t, double sigma, double temp, double lambda, double* rate_out,
+                   double* mse_out, double* mu_out, double* logb_out, double* bits_out, double* xhat_out) {
     fwd_t F;
     memset(&F, 0, sizeof(F));
-    double loss = run_forward(H, W, img, y, P, mode, seed, t, lambda, &F, rate_out, mse_out);
+    relax_t R = {mode, seed, t, sigma, temp};
+    double loss = run_forward(H, W, img, y, P, &R, lambda, &F, rate_out, mse_out);
     int64_t N = F.g.off[NG], HW = (int64_t)H * W;
     if (mu_out) memcpy(mu_out, F.mu, sizeof(double) * N);
     if (logb_out) memcpy(logb_out, F.logb, sizeof(double) * N);
@@ -529,14 +578,16 @@ double orc_forward(int H, int W, const double* img, const double* y, const doubl
     return loss;
 }
 
-/* Loss and its gradient with respect to the continuous latents y and the parameters.
- * With the additive noise proxy, dL/dy = dL/dy~. */
+/* Loss and its gradient with respect to the continuous latents y and the parameters:
+ * dL/dy = dL/dy~ * dy~/dy (1 for the additive proxy, 0 under hard rounding, the product of the
+ * two soft-rounding derivatives for Eq. 12). */
 double orc_loss_grad(int H, int W, const double* img, const double* y, const double* P, int mode,
-                     uint64_t seed, int64_t t, double lambda, double* rate_out, double* mse_out,
-                     double* gy, double* gP) {
+                     uint64_t seed, int64_t t, double sigma, double temp, double lambda, double* rate_out,
+                     double* mse_out, double* gy, double* gP) {
     fwd_t F;
     memset(&F, 0, sizeof(F));
-    double loss = run_forward(H, W, img, y, P, mode, seed, t, lambda, &F, rate_out, mse_out);
+    relax_t R = {mode, seed, t, sigma, temp};
+    double loss = run_forward(H, W, img, y, P, &R, lambda, &F, rate_out, mse_out);
     const geom_t* g = &F.g;
     int64_t N = g->off[NG], HW = (int64_t)H * W;
     double* gyt = (double*)calloc(N, sizeof(double));
@@ -669,8 +720,12 @@ double orc_loss_grad(int H, int W, const double* img, const double* y, const dou
         free(ddir);
         free(rowa);
     }
-    /* y~ = y + u (or y): identity Jacobian; under hard rounding the gradient is zero */
-    for (int64_t i = 0; i < N; ++i) gy[i] = (mode == MODE_HARD) ? 0.0 : gyt[i];
+    /* chain rule through the relaxation */
+    for (int64_t i = 0; i < N; ++i) {
+        double jac;
+        relax_one(&R, y[i], i, &jac);
+        gy[i] = gyt[i] * jac;
+    }
     free(gyt);
     free(dxh);
     free(dx1);
@@ -704,12 +759,46 @@ void orc_encode(int H, int W, const double* img, double* y, double* P, double* m
     double gP[N_PARAMS];
     for (int it = 0; it < n_iters; ++it) {
         double rate, mse;
-        double loss = orc_loss_grad(H, W, img, y, P, MODE_NOISE, seed, *step, lambda, &rate, &mse, gy, gP);
+        double loss = orc_loss_grad(H, W, img, y, P, MODE_NOISE, seed, *step, 0.0, 1.0, lambda, &rate, &mse, gy, gP);
         if (loss_out) loss_out[it] = loss;
         if (rate_out) rate_out[it] = rate;
         if (mse_out) mse_out[it] = mse;
         *step += 1;
         orc_adam(N, y, gy, m_y, v_y, *step, lr, b1, b2, eps);
+        orc_adam(N_PARAMS, P, gP, m_p, v_p, *step, lr, b1, b2, eps);
+    }
+    free(gy);
+}
+
+/* The paper's encoder schedule (Sec. IV-C/D, Table I), n_iters iterations from *step:
+ *   main stage, steps t < n_main, with f = t / n_main:  y~ = s_T(s_T(y) + sigma n),
+ *     sigma = sigma0 + (sigma1 - sigma0) f,  T = temp0 + (temp1 - temp0) f,
+ *     lr = lr_min + (lr_max - lr_min) (1 + cos(pi f)) / 2,  Adam on latents and parameters;
+ *   hard-round stage, t >= n_main:  y~ = rint(y), latents frozen (no update, moments kept),
+ *     Adam on the parameters at lr_min.
+ * The Adam step count is t + 1 in both stages. */
+void orc_encode_schedule(int H, int W, const double* img, double* y, double* P, double* m_y, double* v_y,
+                         double* m_p, double* v_p, int64_t* step, int n_iters, uint64_t seed, double lambda,
+                         double lr_max, double lr_min, double sigma0, double sigma1, double temp0, double temp1,
+                         int64_t n_main, double b1, double b2, double eps, double* loss_out, double* rate_out,
+                         double* mse_out) {
+    int64_t N = orc_latent_count(H, W);
+    double* gy = (double*)malloc(sizeof(double) * N);
+    double gP[N_PARAMS];
+    for (int it = 0; it < n_iters; ++it) {
+        const int64_t t = *step;
+        const int main_stage = t < n_main;
+        const double f = main_stage ? (double)t / (double)n_main : 1.0;
+        const double sigma = sigma0 + (sigma1 - sigma0) * f, temp = temp0 + (temp1 - temp0) * f;
+        const double lr = main_stage ? lr_min + 0.5 * (lr_max - lr_min) * (1.0 + cos(M_PI * f)) : lr_min;
+        double rate, mse;
+        double loss = orc_loss_grad(H, W, img, y, P, main_stage ? MODE_SOFTROUND : MODE_HARD, seed, t, sigma,
+                                    temp, lambda, &rate, &mse, gy, gP);
+        if (loss_out) loss_out[it] = loss;
+        if (rate_out) rate_out[it] = rate;
+        if (mse_out) mse_out[it] = mse;
+        *step += 1;
+        if (main_stage) orc_adam(N, y, gy, m_y, v_y, *step, lr, b1, b2, eps);
         orc_adam(N_PARAMS, P, gP, m_p, v_p, *step, lr, b1, b2, eps);
     }
     free(gy);
@@ -844,7 +933,8 @@ void orc_decode_image(int H, int W, const int32_t* q, const float* Pf, double* i
     double* zero = (double*)calloc(NCH * HW, sizeof(double));
     fwd_t F;
     memset(&F, 0, sizeof(F));
-    run_forward(H, W, zero, y, P, MODE_IDENTITY, 0, 0, 0.0, &F, &rate, &mse);
+    relax_t R = {MODE_IDENTITY, 0, 0, 0.0, 1.0};
+    run_forward(H, W, zero, y, P, &R, 0.0, &F, &rate, &mse);
     for (int64_t q2 = 0; q2 < NCH * HW; ++q2) img_out[q2] = fmin(fmax(F.xh[q2], 0.0), 1.0);
     fwd_free(&F);
     free(zero);

@@ -67,11 +67,23 @@ typedef struct {
 } cc_arch_t;
 
 /* Encoder hyper-parameters.  lambda weighs the rate in bits per pixel (Eq. 10 with R divided by
- * H*W); Adam (Sec. IV-B) uses lr, beta1, beta2, eps for latents and parameters alike. */
+ * H*W); Adam (Sec. IV-B) uses lr, beta1, beta2, eps for latents and parameters alike.
+ * noise_mode selects the training proxy of the latents at step t:
+ *   CC_NOISE_UNIFORM:   y~ = y + u, u ~ U[-1/2, 1/2) from a counter hash of (seed, t, i); lr fixed.
+ *   CC_NOISE_SOFTROUND: the paper's proxy and schedule (Sec. IV-C/D, Eq. 12-13, Table I): for
+ *     t < n_main, y~ = s_T(s_T(y) + sigma n) with n ~ N(0, 1) (Box-Muller on the same hash),
+ *     sigma and T linear from (sigma0, temp0) to (sigma1, temp1) over the n_main steps and the
+ *     learning rate cosine from lr to lr_min; for t >= n_main (hard-round stage) y~ = rint(y),
+ *     the latents are frozen and the parameters use lr_min.  temp0, temp1 > 0. */
+#define CC_NOISE_UNIFORM 0
+#define CC_NOISE_SOFTROUND 1
 typedef struct {
     float lambda, lr, beta1, beta2, eps;
-    int32_t noise_mode; /* 0: y~ = y + u, u ~ U[-1/2, 1/2) from a counter hash of (seed, step, i) */
+    int32_t noise_mode;
     uint64_t seed;
+    float sigma0, sigma1, temp0, temp1, lr_min; /* CC_NOISE_SOFTROUND only */
+    int32_t reserved;                           /* 0 */
+    int64_t n_main;                             /* CC_NOISE_SOFTROUND only */
 } cc_hparams_t;
 
 /* Encoder state, all [device], caller-owned: latents, params and their Adam moments (same
@@ -155,7 +167,8 @@ const cc_rd_t* coolchic_batch_records(const cc_batch_t* batch);
 int coolchic_batch_destroy(cc_batch_t* batch);
 
 /* Forward pass only (Eq. 10): rate of the relaxed latents (Eq. 3, Eq. 11), reconstruction and
- * distortion.  relax = CC_RELAX_*; `step` keys the noise for CC_RELAX_NOISE.
+ * distortion.  relax = CC_RELAX_*; CC_RELAX_NOISE applies the training proxy of hp->noise_mode at
+ * `step` (the noise, and for CC_NOISE_SOFTROUND the schedule's sigma, T and stage).
  *   latents, params [device];  rd_out [device, nullable] one record;
  *   xhat_out [device, nullable] reconstructed CHW image (not clamped);
  *   store_activations: 1 keeps the activations the adjoint needs in the workspace (workspace
@@ -166,7 +179,8 @@ int coolchic_forward(const cc_arch_t* arch, const cc_hparams_t* hp, const float*
                      size_t workspace_bytes, void* stream);
 
 /* Adjoint of coolchic_forward: gradients of the loss with respect to the latents and the
- * parameters, scaled by grad_scale (dLoss/dOutput of a caller's graph).
+ * parameters, scaled by grad_scale (dLoss/dOutput of a caller's graph); under CC_RELAX_NOISE the
+ * latent gradient includes dy~/dy of the training proxy (1, or the soft-rounding derivatives).
  *   use_stored: 1 reads the activations a preceding coolchic_forward(store_activations = 1) left
  *   in the same workspace with the same inputs; 0 recomputes them per tile.
  *   grad_latents [device] N floats, grad_params [device] 1415 floats, both overwritten.

@@ -72,20 +72,17 @@ int check_hp(const cc_hparams_t* hp) {
     if (!std::isfinite(hp->lr) || !std::isfinite(hp->eps) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) ||
         !(hp->beta2 >= 0.f && hp->beta2 < 1.f))
         return fail(CC_ERR_ARG, "invalid Adam hyper-parameters");
-    if (hp->noise_mode != 0) return fail(CC_ERR_UNSUPPORTED, "only noise_mode 0 (additive uniform) is built");
+    if (hp->noise_mode != CC_NOISE_UNIFORM && hp->noise_mode != CC_NOISE_SOFTROUND)
+        return fail(CC_ERR_UNSUPPORTED, "noise_mode must be CC_NOISE_UNIFORM or CC_NOISE_SOFTROUND");
+    if (hp->noise_mode == CC_NOISE_SOFTROUND &&
+        !(hp->temp0 > 0.f && hp->temp1 > 0.f && std::isfinite(hp->temp0) && std::isfinite(hp->temp1) &&
+          hp->sigma0 >= 0.f && hp->sigma1 >= 0.f && std::isfinite(hp->sigma0) && std::isfinite(hp->sigma1) &&
+          std::isfinite(hp->lr_min) && hp->n_main >= 0))
+        return fail(CC_ERR_ARG, "soft-round schedule: temperatures > 0, sigmas >= 0, finite lr_min, n_main >= 0");
     return CC_OK;
 }
 
-Hp to_hp(const cc_hparams_t* h) {
-    Hp o;
-    o.lambda = h->lambda;
-    o.lr = h->lr;
-    o.beta1 = h->beta1;
-    o.beta2 = h->beta2;
-    o.eps = h->eps;
-    o.seed = h->seed;
-    return o;
-}
+Hp to_hp(const cc_hparams_t* h) { return hp_from(h); }
 
 struct Layout {
     size_t total = 0;
@@ -248,10 +245,10 @@ int num_sms() {
 
 // Forward sequence shared by the entry points: relax, entropy model, upsampling, synthesis, convs.
 static void run_forward(const Work& w, const float* image, const float* latents, const float* params,
-                        const int64_t* step_dev, int64_t step_host, uint64_t seed, int relax, int arm_pass,
+                        const int64_t* step_dev, int64_t step_host, const Hp& hp, int relax, int arm_pass,
                         int syn_pass, int conv_pass, float arm_gscale, float conv_gscale, float* xhat, cudaStream_t s,
                         bool relaxed_already = false) {
-    if (!relaxed_already) launch_relax(w, latents, step_dev, step_host, seed, relax, s);
+    if (!relaxed_already) launch_relax(w, latents, step_dev, step_host, hp, relax, s);
     tbeg(CC_KERNEL_ARM, s);
     launch_arm(w, params, arm_pass, arm_gscale, s);
     tend(CC_KERNEL_ARM, s);
@@ -262,6 +259,26 @@ static void run_forward(const Work& w, const float* image, const float* latents,
     tbeg(CC_KERNEL_CONV, s);
     launch_conv(w, params, image, conv_pass, conv_gscale, xhat, s);
     tend(CC_KERNEL_CONV, s);
+}
+
+int validate_hparams(const cc_hparams_t* h) { return check_hp(h); }
+
+Hp hp_from(const cc_hparams_t* h) {
+    Hp o;
+    o.lambda = h->lambda;
+    o.lr = h->lr;
+    o.beta1 = h->beta1;
+    o.beta2 = h->beta2;
+    o.eps = h->eps;
+    o.seed = h->seed;
+    o.noise_mode = h->noise_mode;
+    o.sigma0 = h->sigma0;
+    o.sigma1 = h->sigma1;
+    o.temp0 = h->temp0;
+    o.temp1 = h->temp1;
+    o.lr_min = h->lr_min;
+    o.n_main = h->n_main;
+    return o;
 }
 
 static void syn_backward_timed(const Work& w, const float* params, int pass, cudaStream_t s) {
@@ -358,11 +375,11 @@ int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const fl
     if (rd_per_iter) launch_mark_base(w, st->step, s);
     for (int it = 0; it < n_iters; ++it) {
         // the relaxed latents of iterations after the first come from the previous Adam update
-        run_forward(w, image, st->latents, st->params, st->step, 0, h.seed, kRelaxNoise, PASS_FWD_BWD, PASS_FWD,
+        run_forward(w, image, st->latents, st->params, st->step, 0, h, kRelaxNoise, PASS_FWD_BWD, PASS_FWD,
                     PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s, it > 0);
         syn_backward_timed(w, st->params, PASS_FWD_BWD, s);
         launch_up_adjoint(w, st->params, s);
-        launch_gather(w, st->params, kRelaxNoise, nullptr, st->latents, st->m_lat, st->v_lat, h, st->step, s,
+        launch_gather(w, st->params, kRelaxNoise, nullptr, st->latents, st->m_lat, st->v_lat, h, st->step, 0, s,
                       it + 1 < n_iters);
         launch_param_reduce(w, st->params, st->m_par, st->v_par, nullptr, 1.f, h, st->step, s);
         launch_finish(w, h, 1, 1, (double*)rd_per_iter, st->step, 0, 1, s);
@@ -384,7 +401,7 @@ int coolchic_forward(const cc_arch_t* arch, const cc_hparams_t* hp, const float*
     cudaStream_t s = (cudaStream_t)stream;
     const Hp h = to_hp(hp);
     const int ap = store ? PASS_FWD_STORE : PASS_FWD;
-    run_forward(w, image, latents, params, nullptr, step, h.seed, relax, ap, ap, PASS_FWD, 0.f, 0.f, xhat, s);
+    run_forward(w, image, latents, params, nullptr, step, h, relax, ap, ap, PASS_FWD, 0.f, 0.f, xhat, s);
     launch_finish(w, h, 1, 1, (double*)rd_out, nullptr, 0, 0, s);
     return launched("forward");
 }
@@ -415,12 +432,13 @@ int coolchic_backward(const cc_arch_t* arch, const cc_hparams_t* hp, const float
         tend(CC_KERNEL_CONV, s);
         syn_backward_timed(w, params, PASS_BWD_LOAD, s);
     } else {
-        run_forward(w, image, latents, params, nullptr, step, h.seed, relax, PASS_FWD_BWD, PASS_FWD, PASS_FWD_BWD,
+        run_forward(w, image, latents, params, nullptr, step, h, relax, PASS_FWD_BWD, PASS_FWD, PASS_FWD_BWD,
                     arm_gs, conv_gs, nullptr, s);
         syn_backward_timed(w, params, PASS_FWD_BWD, s);
     }
     launch_up_adjoint(w, params, s);
-    launch_gather(w, params, relax, grad_latents, nullptr, nullptr, nullptr, h, nullptr, s);
+    // the latents are read (never written) for the chain rule through the training proxy
+    launch_gather(w, params, relax, grad_latents, const_cast<float*>(latents), nullptr, nullptr, h, nullptr, step, s);
     launch_param_reduce(w, nullptr, nullptr, nullptr, grad_params, 1.f, h, nullptr, s);
     return launched("backward");
 }
@@ -438,7 +456,7 @@ int coolchic_rate_distortion(const cc_arch_t* arch, const cc_hparams_t* hp, cons
     cudaStream_t s = (cudaStream_t)stream;
     const Hp h = to_hp(hp);
     double* rd_dev = (double*)w.grad_params;  // 3 doubles of scratch
-    run_forward(w, image, latents, params, nullptr, step, h.seed, relax, PASS_FWD, PASS_FWD, PASS_FWD, 0.f, 0.f,
+    run_forward(w, image, latents, params, nullptr, step, h, relax, PASS_FWD, PASS_FWD, PASS_FWD, 0.f, 0.f,
                 nullptr, s);
     launch_finish(w, h, 1, 1, rd_dev, nullptr, 0, 0, s);
     if ((rc = launched("rate_distortion"))) return rc;

@@ -115,8 +115,7 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
         if (std::memcmp(&ref, &archs[j], sizeof(ref)) != 0)
             return set_error(CC_ERR_UNSUPPORTED, "batch_create: job %d has an unsupported architecture", j);
         const cc_hparams_t& h = hps[j];
-        if (!std::isfinite(h.lambda) || h.lambda < 0.f || h.noise_mode != 0)
-            return set_error(CC_ERR_ARG, "batch_create: job %d has invalid hyper-parameters", j);
+        if (const int rc = validate_hparams(&h)) return rc;
         const cc_state_t& st = states[j];
         if (!images[j] || !st.latents || !st.params || !st.m_lat || !st.v_lat || !st.m_par || !st.v_par || !st.step)
             return set_error(CC_ERR_ARG, "batch_create: job %d has a NULL image or state pointer", j);
@@ -126,12 +125,7 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
         if (ws_bytes[j] < need)
             return set_error(CC_ERR_WORKSPACE, "batch_create: job %d workspace has %zu bytes, needs %zu", j, ws_bytes[j], need);
         layout_job(&archs[j], 0, (char*)workspaces[j], &W[j]);
-        H[j].lambda = h.lambda;
-        H[j].lr = h.lr;
-        H[j].beta1 = h.beta1;
-        H[j].beta2 = h.beta2;
-        H[j].eps = h.eps;
-        H[j].seed = h.seed;
+        H[j] = hp_from(&h);
     }
     // largest jobs first in the CTA space
     std::vector<int> order(n);
@@ -162,7 +156,7 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
         w.n_cta_conv = scaled(w.n_cta_conv, sc.conv);
         for (int st = 1; st < kL; ++st) w.n_cta_up[st] = scaled(w.n_cta_up[st], sc.other);
     }
-    b->relax = fill([&](int j) { return relax_args(W[j], states[j].latents, states[j].step, 0, H[j].seed, kRelaxNoise); },
+    b->relax = fill([&](int j) { return relax_args(W[j], states[j].latents, states[j].step, 0, H[j], kRelaxNoise); },
                     [&](int j) { return scaled(relax_ctas(W[j]), sc.other); });
     b->arm = fill([&](int j) { return arm_args(W[j], states[j].params, H[j].lambda / (float)W[j].HW); },
                   [&](int j) { return W[j].n_cta_arm; });
@@ -182,9 +176,9 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
         b->upa_wt[st] = wt;
     }
     b->ifce = fill([&](int j) { return ifce_args(W[j]); }, [&](int j) { return scaled(ifce_ctas(W[j]), sc.other); });
-    b->gather = fill([&](int j) { return gather_args(W[j], kRelaxNoise, nullptr, states[j].latents, states[j].m_lat, states[j].v_lat, H[j], states[j].step); },
+    b->gather = fill([&](int j) { return gather_args(W[j], kRelaxNoise, nullptr, states[j].latents, states[j].m_lat, states[j].v_lat, H[j], states[j].step, 0); },
                      [&](int j) { return scaled(gather_ctas(W[j]), sc.other); });
-    b->gather_next = fill([&](int j) { return gather_args(W[j], kRelaxNoise, nullptr, states[j].latents, states[j].m_lat, states[j].v_lat, H[j], states[j].step, true); },
+    b->gather_next = fill([&](int j) { return gather_args(W[j], kRelaxNoise, nullptr, states[j].latents, states[j].m_lat, states[j].v_lat, H[j], states[j].step, 0, true); },
                           [&](int j) { return scaled(gather_ctas(W[j]), sc.other); });
     b->reduce = fill([&](int j) { return reduce_args(W[j], states[j].params, states[j].m_par, states[j].v_par, nullptr, 1.f, H[j], states[j].step); },
                      [&](int) { return reduce_ctas(); });

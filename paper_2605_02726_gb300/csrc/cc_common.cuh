@@ -82,12 +82,29 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // Counter noise: SplitMix64 output function (Steele, Lea, Flood 2014) of
 // seed ^ ((step << 32) + i) * 0x9E3779B97F4A7C15; top 24 bits -> u in [-1/2, 1/2), exact in FP32.
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ float counter_uniform(uint64_t seed, int64_t step, int64_t i) {
+__device__ __forceinline__ uint64_t counter_hash(uint64_t seed, int64_t step, int64_t i) {
     uint64_t z = seed ^ ((((uint64_t)step << 32) + (uint64_t)i) * 0x9E3779B97F4A7C15ull);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return (float)(uint32_t)(z >> 40) * (1.f / 16777216.f) - 0.5f;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ float counter_uniform(uint64_t seed, int64_t step, int64_t i) {
+    return (float)(uint32_t)(counter_hash(seed, step, i) >> 40) * (1.f / 16777216.f) - 0.5f;
+}
+// Standard normal from the same hash by the Box-Muller transform (Box and Muller, 1958):
+// u1 = (bits 40..63 + 1/2) / 2^24 in (0, 1), u2 = bits 16..39 / 2^24, n = sqrt(-2 ln u1) cos(2 pi u2).
+__device__ __forceinline__ float counter_gauss(uint64_t seed, int64_t step, int64_t i) {
+    const uint64_t z = counter_hash(seed, step, i);
+    const float u1 = ((float)(uint32_t)(z >> 40) + 0.5f) * (1.f / 16777216.f);
+    const float u2 = (float)(uint32_t)((z >> 16) & 0xFFFFFFull) * (1.f / 16777216.f);
+    return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
+// Soft rounding, Eq. 13 (after Agustsson and Theis): s_T(x) = floor(x) + 1/2 + tanh(D / T) /
+// (2 tanh(1 / (2T))), D = x - floor(x) - 1/2; d = s_T'(x) = (1 - tanh^2(D / T)) / (2 T tanh(1 / (2T))).
+__device__ __forceinline__ float softround(float x, float T, float& d) {
+    const float fl = floorf(x), D = x - fl - 0.5f, th = tanhf(D / T), den = 2.f * tanhf(0.5f / T);
+    d = (1.f - th * th) / (T * den);
+    return fl + 0.5f + th / den;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -19,7 +19,48 @@ constexpr int kRelaxNoise = 0, kRelaxHard = 1, kRelaxIdentity = 2;
 struct Hp {
     float lambda, lr, beta1, beta2, eps;
     uint64_t seed;
+    int noise_mode;                              // 0 additive uniform, 1 soft-round schedule
+    float sigma0, sigma1, temp0, temp1, lr_min;  // mode 1
+    int64_t n_main;                              // mode 1: first step of the hard-round stage
 };
+Hp hp_from(const cc_hparams_t* h);
+int validate_hparams(const cc_hparams_t* h);  // CC_OK or an error code with the message set
+
+// Training proxy at step t (Sec. IV-C/D, Table I): noise scale, temperature, learning rate and
+// whether t is in the hard-round stage (mode 1 only).
+struct ProxyAt {
+    float sigma, temp, lr;
+    bool hard;
+};
+__device__ __forceinline__ ProxyAt proxy_at(const Hp& hp, int64_t t) {
+    ProxyAt p{0.f, 1.f, hp.lr, false};
+    if (hp.noise_mode == 1) {
+        p.hard = t >= hp.n_main;
+        const float f = p.hard ? 1.f : (float)t / (float)hp.n_main;
+        p.sigma = hp.sigma0 + (hp.sigma1 - hp.sigma0) * f;
+        p.temp = hp.temp0 + (hp.temp1 - hp.temp0) * f;
+        p.lr = p.hard ? hp.lr_min : hp.lr_min + 0.5f * (hp.lr - hp.lr_min) * (1.f + cospif(f));
+    }
+    return p;
+}
+// y~ of latent i at step t under the training proxy, and dy~/dy: the additive uniform proxy
+// (mode 0), Eq. 12 (mode 1, main stage), rint (mode 1, hard-round stage)
+__device__ __forceinline__ float relax_latent(const Hp& hp, const ProxyAt& p, float y, int64_t t, int64_t i,
+                                              float& jac) {
+    if (hp.noise_mode == 0) {
+        jac = 1.f;
+        return y + counter_uniform(hp.seed, t, i);
+    }
+    if (p.hard) {
+        jac = 0.f;
+        return rintf(y);
+    }
+    float d1, d2;
+    const float s1 = softround(y, p.temp, d1);
+    const float v = softround(fmaf(p.sigma, counter_gauss(hp.seed, t, i), s1), p.temp, d2);
+    jac = d2 * d1;
+    return v;
+}
 
 constexpr int kArmThreads = 128;   // latents per ARM round
 constexpr int kSynThreads = 128;   // pixels per synthesis round
@@ -139,9 +180,9 @@ struct RelaxArgs {
     const float* y;
     float* yt;
     int64_t N;
-    uint64_t seed;
     const int64_t* step_dev;  // step from here when non-null, else step_host
     int64_t step_host;
+    Hp hp;                    // seed and training proxy
     int relax;
     int pad_;
 };
@@ -223,10 +264,12 @@ struct GatherArgs {
     float* y;
     float* m;
     float* v;
-    const int64_t* step_dev;
-    float* yt_next;   // non-null (with Adam): also write y~ = y + u(hp.seed, step + 1) for the next step
+    const int64_t* step_dev;  // step from here when non-null, else step_host
+    int64_t step_host;
+    float* yt_next;   // non-null (with Adam): also write the next step's relaxed latents
     Hp hp;
-    int zero_grad, pad_;
+    int zero_grad;    // hard rounding: no latent gradient
+    int proxy;        // latents relaxed by the training proxy: chain rule through dy~/dy
 };
 struct ReduceArgs {
     const float* garm;
@@ -259,7 +302,7 @@ int set_error(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3
 
 // a1 relaxation: yt = y + u(seed, step, i) | rint(y) | y.  step from step_dev when non-null.
 void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host,
-                  uint64_t seed, int relax, cudaStream_t s);
+                  const Hp& hp, int relax, cudaStream_t s);
 // a2-a3 and a9: entropy model over all latents.
 void launch_arm(const Work& w, const float* params, int pass, float grad_scale, cudaStream_t s);
 // a4: upsampling stages 6..2 (stage 1 is fused into the synthesis kernels).
@@ -275,8 +318,8 @@ void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s);
 // relax_next: the Adam update also writes the next step's relaxed latents (y~ of step + 1), so
 // that the next iteration needs no relaxation launch.
 void launch_gather(const Work& w, const float* params, int relax, float* grad_out, float* y,
-                   float* m, float* v, const Hp& hp, const int64_t* step_dev, cudaStream_t s,
-                   bool relax_next = false);
+                   float* m, float* v, const Hp& hp, const int64_t* step_dev, int64_t step_host,
+                   cudaStream_t s, bool relax_next = false);
 // a10 + a11: fixed-order reduction of the per-CTA parameter gradients, then Adam or a copy-out.
 void launch_param_reduce(const Work& w, float* params, float* m, float* v, float* grad_out,
                          float out_scale, const Hp& hp, const int64_t* step_dev, cudaStream_t s);
@@ -296,7 +339,7 @@ void synth_init_attributes();
 void syn_init_attributes();
 
 // argument builders, CTA counts and multi-job launches (batched encode)
-RelaxArgs relax_args(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, uint64_t seed,
+RelaxArgs relax_args(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, const Hp& hp,
                      int relax);
 ArmArgs arm_args(const Work& w, const float* params, float grad_scale);
 UpFwdArgs up_fwd_args(const Work& w, const float* params, int m);
@@ -305,7 +348,7 @@ ConvArgs conv_args(const Work& w, const float* params, const float* image, float
 UpAdjArgs up_adj_args(const Work& w, const float* params, int st);
 IfceArgs ifce_args(const Work& w);
 GatherArgs gather_args(const Work& w, int relax, float* grad_out, float* y, float* m, float* v, const Hp& hp,
-                       const int64_t* step_dev, bool relax_next = false);
+                       const int64_t* step_dev, int64_t step_host, bool relax_next = false);
 ReduceArgs reduce_args(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,
                        const Hp& hp, const int64_t* step_dev);
 FinishArgs finish_args(const Work& w, const Hp& hp, int have_arm, int have_conv, double* rd, int rd_stride,

@@ -86,7 +86,7 @@ extern "C" int coolchic_rate_distortion_noalloc(const cc_arch_t* arch, const cc_
         return set_error(CC_ERR_UNSUPPORTED, "rate_distortion_noalloc: only the architecture of coolchic_arch_init is built");
     if (!hp || !std::isfinite(hp->lambda) || hp->lambda < 0.f)
         return set_error(CC_ERR_ARG, "rate_distortion_noalloc: hparams NULL or lambda not finite and >= 0");
-    if (hp->noise_mode != 0) return set_error(CC_ERR_UNSUPPORTED, "rate_distortion_noalloc: only noise_mode 0 is built");
+    if (const int rc = validate_hparams(hp)) return rc;
     if (!image || !latents || !params || !rd_out)
         return set_error(CC_ERR_ARG, "rate_distortion_noalloc: NULL image, latents, params or rd_out");
     if (relax < 0 || relax > 2) return set_error(CC_ERR_ARG, "rate_distortion_noalloc: relax must be 0, 1 or 2");
@@ -117,14 +117,9 @@ extern "C" int coolchic_rate_distortion_noalloc(const cc_arch_t* arch, const cc_
     layout(arch, (char*)base, &w);
     cudaStream_t s = (cudaStream_t)stream;
     Hp h;
-    h.lambda = hp->lambda;
-    h.lr = hp->lr;
-    h.beta1 = hp->beta1;
-    h.beta2 = hp->beta2;
-    h.eps = hp->eps;
-    h.seed = hp->seed;
+    h = hp_from(hp);
     double* rd_dev = (double*)w.grad_params;
-    launch_relax(w, latents, nullptr, step, h.seed, relax, s);
+    launch_relax(w, latents, nullptr, step, h, relax, s);
     launch_arm(w, params, PASS_FWD, 0.f, s);
     launch_up_forward(w, params, s);
     launch_syn_forward(w, params, PASS_FWD, s);

@@ -12,9 +12,12 @@ namespace {
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void relax_body(const RelaxArgs& a, int cta, int ncta) {
     const int64_t step = a.step_dev ? *a.step_dev : a.step_host;
+    const ProxyAt px = proxy_at(a.hp, step);
     for (int64_t i = cta * (int64_t)blockDim.x + threadIdx.x; i < a.N; i += (int64_t)ncta * blockDim.x) {
         const float v = a.y[i];
-        a.yt[i] = a.relax == kRelaxNoise ? v + counter_uniform(a.seed, step, i) : (a.relax == kRelaxHard ? rintf(v) : v);
+        float jac;
+        a.yt[i] = a.relax == kRelaxNoise ? relax_latent(a.hp, px, v, step, i, jac)
+                                         : (a.relax == kRelaxHard ? rintf(v) : v);
     }
 }
 __global__ void k_relax(RelaxArgs a) {
@@ -109,7 +112,9 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
     if (threadIdx.x == 0) g = a.g;
     __syncthreads();
     float bc1 = 1.f, bc2 = 1.f;
-    if (!a.grad_out) adam_bias_corrections(*a.step_dev + 1, a.hp.beta1, a.hp.beta2, bc1, bc2);
+    const int64_t step = a.step_dev ? *a.step_dev : a.step_host;
+    if (!a.grad_out) adam_bias_corrections(step + 1, a.hp.beta1, a.hp.beta2, bc1, bc2);
+    const ProxyAt px = proxy_at(a.hp, step), px_next = proxy_at(a.hp, step + 1);
     const int64_t N = g.off[kL];
     const float* __restrict__ dS = a.dS;
     for (int64_t i = cta * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)ncta * blockDim.x) {
@@ -148,16 +153,28 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
                 for (int cc = 0; cc < bw; ++cc) acc += plane[(int64_t)(r0 + rr) * w3 + c0 + cc];
         }
         if (a.zero_grad) acc = 0.f;
+        const float yi = a.y[i];
+        if (a.proxy && a.hp.noise_mode != 0) {  // chain rule through y~ = Q_train(y)
+            float jac;
+            relax_latent(a.hp, px, yi, step, i, jac);
+            acc *= jac;
+        }
         if (a.grad_out) {
             a.grad_out[i] = acc;
         } else {
-            const float mi = a.hp.beta1 * a.m[i] + (1.f - a.hp.beta1) * acc;
-            const float vi = a.hp.beta2 * a.v[i] + (1.f - a.hp.beta2) * acc * acc;
-            a.m[i] = mi;
-            a.v[i] = vi;
-            const float yn = a.y[i] - a.hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
-            a.y[i] = yn;
-            if (a.yt_next) a.yt_next[i] = yn + counter_uniform(a.hp.seed, *a.step_dev + 1, i);
+            float yn = yi;
+            if (!px.hard) {  // the hard-round stage leaves the latents (and their moments) alone
+                const float mi = a.hp.beta1 * a.m[i] + (1.f - a.hp.beta1) * acc;
+                const float vi = a.hp.beta2 * a.v[i] + (1.f - a.hp.beta2) * acc * acc;
+                a.m[i] = mi;
+                a.v[i] = vi;
+                yn = yi - px.lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
+                a.y[i] = yn;
+            }
+            if (a.yt_next) {
+                float jac;
+                a.yt_next[i] = relax_latent(a.hp, px_next, yn, step + 1, i, jac);
+            }
         }
     }
 }
@@ -232,12 +249,14 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
         return;
     }
     float bc1, bc2;
-    adam_bias_corrections(*a.step_dev + 1, a.hp.beta1, a.hp.beta2, bc1, bc2);
+    const int64_t step = *a.step_dev;
+    adam_bias_corrections(step + 1, a.hp.beta1, a.hp.beta2, bc1, bc2);
+    const float lr = proxy_at(a.hp, step).lr;
     const float mi = a.hp.beta1 * a.m[p] + (1.f - a.hp.beta1) * gsum;
     const float vi = a.hp.beta2 * a.v[p] + (1.f - a.hp.beta2) * gsum * gsum;
     a.m[p] = mi;
     a.v[p] = vi;
-    a.params[p] -= a.hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
+    a.params[p] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
 }
 __global__ void __launch_bounds__(kReduceThreads) k_param_reduce(ReduceArgs a) {
     __shared__ ReduceArgs sa;
@@ -312,15 +331,15 @@ int grid_for(int64_t n, int threads, int per_sm) {
 }
 
 // ---- argument builders
-RelaxArgs relax_args(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, uint64_t seed,
+RelaxArgs relax_args(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, const Hp& hp,
                      int relax) {
     RelaxArgs a;
     a.y = y;
     a.yt = w.yt;
     a.N = w.N;
-    a.seed = seed;
     a.step_dev = step_dev;
     a.step_host = step_host;
+    a.hp = hp;
     a.relax = relax;
     a.pad_ = 0;
     return a;
@@ -335,7 +354,7 @@ IfceArgs ifce_args(const Work& w) {
     return a;
 }
 GatherArgs gather_args(const Work& w, int relax, float* grad_out, float* y, float* m, float* v, const Hp& hp,
-                       const int64_t* step_dev, bool relax_next) {
+                       const int64_t* step_dev, int64_t step_host, bool relax_next) {
     GatherArgs a;
     a.g = w.g;
     a.dYd = w.dYd;
@@ -349,10 +368,11 @@ GatherArgs gather_args(const Work& w, int relax, float* grad_out, float* y, floa
     a.m = m;
     a.v = v;
     a.step_dev = step_dev;
+    a.step_host = step_host;
     a.yt_next = (relax_next && !grad_out) ? w.yt : nullptr;
     a.hp = hp;
     a.zero_grad = relax == kRelaxHard ? 1 : 0;
-    a.pad_ = 0;
+    a.proxy = relax == kRelaxNoise ? 1 : 0;
     return a;
 }
 ReduceArgs reduce_args(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,
@@ -401,16 +421,17 @@ int gather_ctas(const Work& w) { return grid_for(w.N, 256, 8); }
 int reduce_ctas() { return kReduceCtas; }
 
 // ---- single-job launches
-void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, uint64_t seed,
+void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, const Hp& hp,
                   int relax, cudaStream_t s) {
-    launch_pdl(k_relax, relax_ctas(w), 256, 0, s, relax_args(w, y, step_dev, step_host, seed, relax));
+    launch_pdl(k_relax, relax_ctas(w), 256, 0, s, relax_args(w, y, step_dev, step_host, hp, relax));
 }
 
 void launch_gather(const Work& w, const float* params, int relax, float* grad_out, float* y, float* m, float* v,
-                   const Hp& hp, const int64_t* step_dev, cudaStream_t s, bool relax_next) {
+                   const Hp& hp, const int64_t* step_dev, int64_t step_host, cudaStream_t s, bool relax_next) {
     (void)params;
     launch_pdl(k_ifce_cells, ifce_ctas(w), 128, 0, s, ifce_args(w));
-    launch_pdl(k_gather, gather_ctas(w), 256, 0, s, gather_args(w, relax, grad_out, y, m, v, hp, step_dev, relax_next));
+    launch_pdl(k_gather, gather_ctas(w), 256, 0, s,
+               gather_args(w, relax, grad_out, y, m, v, hp, step_dev, step_host, relax_next));
 }
 
 void launch_param_reduce(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,

@@ -29,7 +29,9 @@ class Arch(ctypes.Structure):
 class HParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_float), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("noise_mode", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("sigma0", ctypes.c_float), ("sigma1", ctypes.c_float),
+                ("temp0", ctypes.c_float), ("temp1", ctypes.c_float), ("lr_min", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("n_main", ctypes.c_int64)]
 
 
 class State(ctypes.Structure):
@@ -147,8 +149,20 @@ def arch(H: int, W: int) -> Arch:
     return a
 
 
+CC_NOISE_UNIFORM, CC_NOISE_SOFTROUND = 0, 1
+
+
 def hparams(lam=1e-3, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, seed=0) -> HParams:
-    return HParams(lam, lr, beta1, beta2, eps, 0, seed)
+    """Additive uniform proxy, constant learning rate."""
+    return HParams(lam, lr, beta1, beta2, eps, CC_NOISE_UNIFORM, seed, 0.0, 0.0, 1.0, 1.0, lr, 0, 0)
+
+
+def hparams_schedule(lam=1e-3, n_main=1000, lr=1e-2, lr_min=1e-5, sigma0=0.22, sigma1=0.15, temp0=0.35,
+                     temp1=0.08, beta1=0.9, beta2=0.999, eps=1e-8, seed=0) -> HParams:
+    """The paper's soft-round proxy and schedule (Table I defaults): main stage for steps < n_main,
+    then the hard-round stage."""
+    return HParams(lam, lr, beta1, beta2, eps, CC_NOISE_SOFTROUND, seed, sigma0, sigma1, temp0, temp1, lr_min,
+                   0, int(n_main))
 
 
 def latent_count(H: int, W: int) -> int:

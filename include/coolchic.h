@@ -100,7 +100,7 @@ typedef struct {
 } cc_rd_t;
 
 /* Relaxation of the latents used by a forward pass (Sec. IV-C). */
-#define CC_RELAX_NOISE 0    /* y + u(seed, step, i)                 */
+#define CC_RELAX_NOISE 0    /* the training proxy of hp->noise_mode at step */
 #define CC_RELAX_HARD 1     /* rint(y), round half to even (Eq. 12) */
 #define CC_RELAX_IDENTITY 2 /* y as given                           */
 

@@ -84,6 +84,8 @@ struct Work {
     float* t;          // synthesis output before the residual convs [3][HW]
     float* dt;         // its adjoint [3][HW]
     float* dz;         // adjoint of the dense latents of grids 1..6 at full resolution [6][HW]
+    float* zden;       // dense latents of grids 1..6 at full resolution [6][HW], written by the
+                       // synthesis forward for its adjoint (null: not kept)
     float* tmp;        // upsampling-adjoint intermediate (largest stage)
     float* act_arm;    // stored ARM activations [34][N] (optional)
     float* act_syn;    // stored synthesis pre-activations [40][HW] (optional)
@@ -220,6 +222,7 @@ struct SynArgs {
     float* act;       // [40][HW]
     float* dYsyn0;    // grid-0 part of dYsyn [HW]
     float* dz;        // [6][HW]
+    float* zden;      // [6][HW] dense latents of grids 1..6: written by the forward, read by the adjoint
     float* gpart;     // [n_cta][467]
 };
 struct ConvArgs {

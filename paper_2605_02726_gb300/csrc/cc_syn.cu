@@ -1,10 +1,11 @@
 // Synthesis of the encoder step: the last upsampling stage (Sec. III-B, Eq. 7) fused with the 1x1
 // MLP 7 -> 40 (GELU) -> 3 and its linear stabilizer 7 -> 3 (Eq. 8, Eq. 9), forward and adjoint.
 //
-// The forward runs one thread per pixel.  The adjoint runs on tensor cores, one warp per unit of
-// 16 consecutive pixels (the M dimension of mma.sync.m16n8k8): lane (g, t) owns pixels g and g + 8
-// of the unit and computes the dense-latent channels t and t + 4 of both (channel 7 is the constant
-// 1 that carries the first-layer bias), i.e. exactly its A fragment.  Products run as TF32 MMAs
+// The forward runs one thread per pixel and keeps the 6 upsampled dense-latent channels for the
+// adjoint.  The adjoint runs on tensor cores, one warp per unit of 16 consecutive pixels (the M
+// dimension of mma.sync.m16n8k8): lane (g, t) owns pixels g and g + 8 of the unit and loads the
+// dense-latent channels t and t + 4 of both (channel 7 is the constant 1 that carries the
+// first-layer bias), i.e. exactly its A fragment.  Products run as TF32 MMAs
 // with the hi/lo split of cc_mma.cuh (FP32-level accuracy), accumulator fragments feed the next
 // product through the K permutation, weight fragments are pre-split per lane in shared memory.
 // Parameter gradients are MMAs over the pixel dimension from a warp-private transposed tile,
@@ -138,6 +139,9 @@ __device__ __forceinline__ void syn_fwd_body(const SynArgs& a, int cta, int ncta
         float z[7];
 #pragma unroll
         for (int j = 0; j < 7; ++j) z[j] = dense_ch(a, sp, j, n1);
+        if (a.zden)  // kept for the adjoint
+#pragma unroll
+            for (int j = 1; j < 7; ++j) a.zden[(int64_t)(j - 1) * a.HW + p] = z[j];
         float t0 = sW[ss_ws + 7], t1 = sW[ss_ws + 15], t2 = sW[ss_ws + 23];
 #pragma unroll
         for (int i = 0; i < 7; ++i) {
@@ -216,24 +220,24 @@ __device__ __forceinline__ void syn_bwd_body(const SynArgs& a, int cta, int ncta
         sW2[j] = v;
     }
     __syncthreads();
-    const float tp[4] = {a.params[po::up], a.params[po::up + 1], a.params[po::up + 2], a.params[po::up + 3]};
     float acc[8][4];
 #pragma unroll
     for (int T = 0; T < 8; ++T)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[T][q] = 0.f;
 
-    const float rcpW = 1.f / (float)a.g.W;
-    const int64_t HW = a.HW, n1 = (int64_t)a.g.h[1] * a.g.w[1];
+    const int64_t HW = a.HW;
     const int64_t n_units = (HW + 15) / 16;
     for (int64_t u = (int64_t)cta * kWarps + wid; u < n_units; u += (int64_t)ncta * kWarps) {
         const int64_t pA = u * 16 + gq, pB = pA + 8;
         const bool vA = pA < HW, vB = pB < HW;
         const int64_t qA = vA ? pA : HW - 1, qB = vB ? pB : HW - 1;
-        const Samp sA = sample_at(a.g, rcpW, tp, qA);
-        const Samp sB = sample_at(a.g, rcpW, tp, qB);
-        const float zA0 = dense_ch(a, sA, tq, n1), zB0 = dense_ch(a, sB, tq, n1);
-        const float zA1 = dense_ch(a, sA, tq + 4, n1), zB1 = dense_ch(a, sB, tq + 4, n1);
+        // dense-latent channels t and t + 4 (0: y~ of grid 0, 1..6: kept by the forward, 7: one)
+        auto zval = [&](int j, int64_t q) {
+            return j == 0 ? __ldg(a.yt + q) : (j >= 7 ? 1.f : __ldg(a.zden + (int64_t)(j - 1) * HW + q));
+        };
+        const float zA0 = zval(tq, qA), zB0 = zval(tq, qB);
+        const float zA1 = zval(tq + 4, qA), zB1 = zval(tq + 4, qB);
         const AFrag Z = make_a(zA0, zB0, zA1, zB1);
         const float mA = vA ? 1.f : 0.f, mB = vB ? 1.f : 0.f;
         float dtA[3], dtB[3];
@@ -414,6 +418,7 @@ SynArgs syn_args(const Work& w, const float* params) {
     a.act = w.act_syn;
     a.dYsyn0 = w.dYsyn;
     a.dz = w.dz;
+    a.zden = w.zden;
     a.gpart = w.gpart_syn;
     return a;
 }

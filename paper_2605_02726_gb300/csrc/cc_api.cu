@@ -111,7 +111,7 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     }
     for (int st = 1; st < kL; ++st) {
         const int nch = kL - st;
-        W.n_cta_up[st] = up_adj_grid((int64_t)nch * g.h[st]);
+        W.n_cta_up[st] = up_adj_ctas(nch, g.h[st], g.w[st]);
     }
     Layout L;
     const size_t F = sizeof(float);
@@ -254,7 +254,9 @@ static void run_forward(const Work& w, const float* image, const float* latents,
     tbeg(CC_KERNEL_ARM, s);
     launch_arm(w, params, arm_pass, arm_gscale, s);
     tend(CC_KERNEL_ARM, s);
+    tbeg(CC_KERNEL_UP_FWD, s);
     launch_up_forward(w, params, s);
+    tend(CC_KERNEL_UP_FWD, s);
     tbeg(CC_KERNEL_SYN_FWD, s);
     launch_syn_forward(w, params, syn_pass, s);
     tend(CC_KERNEL_SYN_FWD, s);
@@ -287,6 +289,11 @@ static void syn_backward_timed(const Work& w, const float* params, int pass, cud
     tbeg(CC_KERNEL_SYN_BWD, s);
     launch_syn_backward(w, params, pass, s);
     tend(CC_KERNEL_SYN_BWD, s);
+}
+static void up_adjoint_timed(const Work& w, const float* params, cudaStream_t s) {
+    tbeg(CC_KERNEL_UP_ADJ, s);
+    launch_up_adjoint(w, params, s);
+    tend(CC_KERNEL_UP_ADJ, s);
 }
 
 }  // namespace cc
@@ -380,9 +387,11 @@ int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const fl
         run_forward(w, image, st->latents, st->params, st->step, 0, h, kRelaxNoise, PASS_FWD_BWD, PASS_FWD,
                     PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s, it > 0);
         syn_backward_timed(w, st->params, PASS_FWD_BWD, s);
-        launch_up_adjoint(w, st->params, s);
+        up_adjoint_timed(w, st->params, s);
+        tbeg(CC_KERNEL_GATHER, s);
         launch_gather(w, st->params, kRelaxNoise, nullptr, st->latents, st->m_lat, st->v_lat, h, st->step, 0, s,
                       it + 1 < n_iters);
+        tend(CC_KERNEL_GATHER, s);
         launch_param_reduce(w, st->params, st->m_par, st->v_par, nullptr, 1.f, h, st->step, s);
         launch_finish(w, h, 1, 1, (double*)rd_per_iter, st->step, 0, 1, s);
         if ((rc = launched("encode_step"))) return rc;
@@ -438,7 +447,7 @@ int coolchic_backward(const cc_arch_t* arch, const cc_hparams_t* hp, const float
                     arm_gs, conv_gs, nullptr, s);
         syn_backward_timed(w, params, PASS_FWD_BWD, s);
     }
-    launch_up_adjoint(w, params, s);
+    up_adjoint_timed(w, params, s);
     // the latents are read (never written) for the chain rule through the training proxy
     launch_gather(w, params, relax, grad_latents, const_cast<float*>(latents), nullptr, nullptr, h, nullptr, step, s);
     launch_param_reduce(w, nullptr, nullptr, nullptr, grad_params, 1.f, h, nullptr, s);
@@ -490,7 +499,7 @@ int coolchic_decode_image(const cc_arch_t* arch, const int32_t* q, const float* 
 }
 
 int coolchic_timing_enable(int32_t kernel_id, int32_t max_launches) {
-    if (kernel_id < CC_KERNEL_ARM || kernel_id > CC_KERNEL_SYN_FWD) return fail(CC_ERR_ARG, "unknown kernel id %d", kernel_id);
+    if (kernel_id < CC_KERNEL_ARM || kernel_id > CC_KERNEL_GATHER) return fail(CC_ERR_ARG, "unknown kernel id %d", kernel_id);
     if (max_launches < 1 || max_launches > (1 << 20)) return fail(CC_ERR_ARG, "max_launches outside 1..2^20");
     coolchic_timing_disable();
     std::lock_guard<std::mutex> lk(g_tm_mu);

@@ -25,7 +25,6 @@ struct cc_batch {
     cc::Batch<cc::SynArgs> synf, synb;
     cc::Batch<cc::ConvArgs> conv;
     cc::Batch<cc::UpAdjArgs> upa[cc::kL];  // stage 1..6
-    int upa_wt[cc::kL];
     cc::Batch<cc::IfceArgs> ifce;
     cc::Batch<cc::GatherArgs> gather;       // last iteration of a call: Adam only
     cc::Batch<cc::GatherArgs> gather_next;  // other iterations: Adam + next step's relaxed latents
@@ -171,9 +170,6 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
     for (int st = 1; st < kL; ++st) {
         b->upa[st] = fill([&](int j) { return up_adj_args(W[j], states[j].params, st); },
                           [&](int j) { return W[j].n_cta_up[st]; });
-        int wt = 1;
-        for (int j = 0; j < n; ++j) wt = std::max(wt, W[j].g.w[st - 1]);
-        b->upa_wt[st] = wt;
     }
     b->ifce = fill([&](int j) { return ifce_args(W[j]); }, [&](int j) { return scaled(ifce_ctas(W[j]), sc.other); });
     b->gather = fill([&](int j) { return gather_args(W[j], kRelaxNoise, nullptr, states[j].latents, states[j].m_lat, states[j].v_lat, H[j], states[j].step, 0); },
@@ -239,7 +235,7 @@ int coolchic_batch_step(cc_batch_t* b, int32_t n_iters, void* stream) {
         launch_syn_fwd_b(b->synf, s);
         launch_conv_b(b->conv, s);
         launch_syn_bwd_b(b->synb, s);
-        for (int st = 1; st < kL; ++st) launch_up_adj_b(b->upa[st], b->upa_wt[st], s);
+        for (int st = 1; st < kL; ++st) launch_up_adj_b(b->upa[st], s);
         launch_ifce_b(b->ifce, s);
         launch_gather_b(it + 1 < n_iters ? b->gather_next : b->gather, s);
         launch_reduce_b(b->reduce, s);

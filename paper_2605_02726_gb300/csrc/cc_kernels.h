@@ -67,6 +67,8 @@ constexpr int kSynThreads = 128;   // pixels per synthesis round
 constexpr int kConvTH = 16, kConvTW = 32;  // conv tile (pixels)
 constexpr int kUpThreads = 256;
 constexpr int kUpMaxCta = 1024;    // per-stage cap on CTAs of an upsampling-adjoint pass
+constexpr int kUpTX = 64;          // input columns of an upsampling-adjoint tile
+constexpr int kUpTYMax = 16;       // tallest upsampling-adjoint tile (input rows)
 
 // Per-job device buffers carved from the caller's workspace (layout in cc_api.cu).
 struct Work {
@@ -246,7 +248,8 @@ struct UpAdjArgs {
     float* outup;        // dup[s]
     float* gpart;        // [n_cta][4]
     const float* taps;
-    int hs, ws, ht, wt, nch, pad_;
+    int hs, ws, ht, wt, nch;
+    int ty;              // tile height in input rows (2..kUpTYMax)
 };
 struct IfceArgs {
     Geom g;
@@ -336,7 +339,7 @@ void launch_mark_base(const Work& w, const int64_t* step_dev, cudaStream_t s);
 size_t arm_smem_bytes(int pass);
 int arm_grid(int64_t N);
 int conv_tiles(int H, int W);
-int up_adj_grid(int64_t pairs);
+int up_adj_ctas(int nch, int hs, int ws);
 void arm_init_attributes();
 void synth_init_attributes();
 void syn_init_attributes();
@@ -368,7 +371,7 @@ void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s);
 void launch_syn_fwd_b(const Batch<SynArgs>& b, cudaStream_t s);
 void launch_conv_b(const Batch<ConvArgs>& b, cudaStream_t s);
 void launch_syn_bwd_b(const Batch<SynArgs>& b, cudaStream_t s);
-void launch_up_adj_b(const Batch<UpAdjArgs>& b, int max_wt, cudaStream_t s);
+void launch_up_adj_b(const Batch<UpAdjArgs>& b, cudaStream_t s);
 void launch_ifce_b(const Batch<IfceArgs>& b, cudaStream_t s);
 void launch_gather_b(const Batch<GatherArgs>& b, cudaStream_t s);
 void launch_reduce_b(const Batch<ReduceArgs>& b, cudaStream_t s);

@@ -11,12 +11,18 @@ namespace {
 // a1: y~ = y + u(seed, step, i) | rint(y) | y
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void relax_body(const RelaxArgs& a, int cta, int ncta) {
-    const int64_t step = a.step_dev ? *a.step_dev : a.step_host;
-    const ProxyAt px = proxy_at(a.hp, step);
+    __shared__ ProxyAt s_px;  // the proxy at this step, once per CTA
+    __shared__ int64_t s_step;
+    if (threadIdx.x == 0) {
+        s_step = a.step_dev ? *a.step_dev : a.step_host;
+        s_px = proxy_at(a.hp, s_step);
+    }
+    __syncthreads();
+    const int64_t step = s_step;
     for (int64_t i = cta * (int64_t)blockDim.x + threadIdx.x; i < a.N; i += (int64_t)ncta * blockDim.x) {
         const float v = a.y[i];
         float jac;
-        a.yt[i] = a.relax == kRelaxNoise ? relax_latent(a.hp, px, v, step, i, jac)
+        a.yt[i] = a.relax == kRelaxNoise ? relax_latent(a.hp, s_px, v, step, i, jac)
                                          : (a.relax == kRelaxHard ? rintf(v) : v);
     }
 }
@@ -105,30 +111,76 @@ __global__ void k_ifce_cells_b(Batch<IfceArgs> b) {
 // ---------------------------------------------------------------------------------------------
 // Latent gradient: direct rate term + the 16 context users + IFCE users + upsampling/synthesis,
 // then Adam on (y, m, v) or a copy to grad_out.  `a` must be in shared memory or be the kernel
-// parameter of a single-job launch; the grid tables are read from a shared copy.
+// parameter of a single-job launch.  The per-launch scalars (grid tables, 1/w of every grid, the
+// Adam bias corrections, the proxy at this step and the next) are computed once per CTA; a latent
+// finds its row by a float reciprocal corrected to the exact quotient, and latents whose 16
+// context users all lie inside the grid load them without bounds tests.
 // ---------------------------------------------------------------------------------------------
+struct GatherScalars {
+    Geom g;
+    float invw[kL];
+    float bc1, bc2;
+    ProxyAt px, px_next;
+    int64_t step;
+};
+
+// r = li / w, c = li % w for 0 <= li < 2^22: the float estimate is within one of the quotient
+// there, and one correction makes it exact; larger indices take the integer division.
+__device__ __forceinline__ void row_col(int li, int w, float invw, int& r, int& c) {
+    if (li < (1 << 22)) {
+        r = (int)((float)li * invw);
+        c = li - r * w;
+        if (c < 0) {
+            --r;
+            c += w;
+        } else if (c >= w) {
+            ++r;
+            c -= w;
+        }
+    } else {
+        r = li / w;
+        c = li - r * w;
+    }
+}
+
 __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int ncta) {
-    __shared__ Geom g;  // shared copy: the grid tables are indexed with a runtime grid number
-    if (threadIdx.x == 0) g = a.g;
+    __shared__ GatherScalars sc;
+    if (threadIdx.x == 0) {
+        sc.g = a.g;
+        for (int k = 0; k < kL; ++k) sc.invw[k] = 1.f / (float)a.g.w[k];
+        sc.step = a.step_dev ? *a.step_dev : a.step_host;
+        sc.bc1 = sc.bc2 = 1.f;
+        if (!a.grad_out) adam_bias_corrections(sc.step + 1, a.hp.beta1, a.hp.beta2, sc.bc1, sc.bc2);
+        sc.px = proxy_at(a.hp, sc.step);
+        sc.px_next = proxy_at(a.hp, sc.step + 1);
+    }
     __syncthreads();
-    float bc1 = 1.f, bc2 = 1.f;
-    const int64_t step = a.step_dev ? *a.step_dev : a.step_host;
-    if (!a.grad_out) adam_bias_corrections(step + 1, a.hp.beta1, a.hp.beta2, bc1, bc2);
-    const ProxyAt px = proxy_at(a.hp, step), px_next = proxy_at(a.hp, step + 1);
+    const Geom& g = sc.g;
+    const int64_t step = sc.step;
     const int64_t N = g.off[kL];
     const float* __restrict__ dS = a.dS;
     for (int64_t i = cta * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)ncta * blockDim.x) {
         const int k = grid_of(g, i);
         const int hk = g.h[k], wk = g.w[k];
         const int li = (int)(i - g.off[k]);
-        const int r = li / wk, c = li - r * wk;
-        float acc = a.dYd[i] + a.dYsyn[i];
-        const float* dSk = dS + g.off[k];
+        int r, c;
+        row_col(li, wk, sc.invw[k], r, c);
+        // latent i is slot n of the latent at (r - dy_n, c - dx_n): plane n at li - dy_n*wk - dx_n
+        const float* p0 = dS + g.off[k] + li;
+        float v[kNCtx];
+        if (r + 3 < hk && c >= 3 && c + 3 < wk) {
 #pragma unroll
-        for (int n = 0; n < kNCtx; ++n) {
-            const int rr = r - ctx_dy(n), cc = c - ctx_dx(n);  // the latent that reads i via slot n
-            if (rr < hk && cc >= 0 && cc < wk) acc += __ldg(dSk + (int64_t)n * N + rr * wk + cc);
+            for (int n = 0; n < kNCtx; ++n) v[n] = __ldg(p0 + (int64_t)n * N - ctx_dy(n) * wk - ctx_dx(n));
+        } else {
+#pragma unroll
+            for (int n = 0; n < kNCtx; ++n) {
+                const int rr = r - ctx_dy(n), cc = c - ctx_dx(n);
+                v[n] = (rr < hk && cc >= 0 && cc < wk) ? __ldg(p0 + (int64_t)n * N - ctx_dy(n) * wk - ctx_dx(n)) : 0.f;
+            }
         }
+        float acc = a.dYd[i] + a.dYsyn[i];
+#pragma unroll
+        for (int n = 0; n < kNCtx; ++n) acc += v[n];
         if (k == 1 || k == 2) {
             // grid 1: 2x2 block of dR0 channel 0; grid 2: 4x4 block of dR0 channel 1, 2x2 of dR1 channel 0
             for (int kp = 0; kp < k; ++kp) {
@@ -156,34 +208,34 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
         const float yi = a.y[i];
         if (a.proxy && a.hp.noise_mode != 0) {  // chain rule through y~ = Q_train(y)
             float jac;
-            relax_latent(a.hp, px, yi, step, i, jac);
+            relax_latent(a.hp, sc.px, yi, step, i, jac);
             acc *= jac;
         }
         if (a.grad_out) {
             a.grad_out[i] = acc;
         } else {
             float yn = yi;
-            if (!px.hard) {  // the hard-round stage leaves the latents (and their moments) alone
+            if (!sc.px.hard) {  // the hard-round stage leaves the latents (and their moments) alone
                 const float mi = a.hp.beta1 * a.m[i] + (1.f - a.hp.beta1) * acc;
                 const float vi = a.hp.beta2 * a.v[i] + (1.f - a.hp.beta2) * acc * acc;
                 a.m[i] = mi;
                 a.v[i] = vi;
-                yn = yi - px.lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
+                yn = yi - sc.px.lr * (mi / sc.bc1) / (sqrtf(vi / sc.bc2) + a.hp.eps);
                 a.y[i] = yn;
             }
             if (a.yt_next) {
                 float jac;
-                a.yt_next[i] = relax_latent(a.hp, px_next, yn, step + 1, i, jac);
+                a.yt_next[i] = relax_latent(a.hp, sc.px_next, yn, step + 1, i, jac);
             }
         }
     }
 }
-__global__ void k_gather(GatherArgs a) {
+__global__ void __launch_bounds__(256, 4) k_gather(GatherArgs a) {
     __shared__ GatherArgs sa;
     param_fetch(a, sa);
     gather_body(sa, blockIdx.x, gridDim.x);
 }
-__global__ void k_gather_b(Batch<GatherArgs> b) {
+__global__ void __launch_bounds__(256, 4) k_gather_b(Batch<GatherArgs> b) {
     __shared__ GatherArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
@@ -417,7 +469,7 @@ FinishArgs finish_args(const Work& w, const Hp& hp, int have_arm, int have_conv,
 
 int relax_ctas(const Work& w) { return grid_for(w.N, 256, 8); }
 int ifce_ctas(const Work& w) { return grid_for(32 * (int64_t)w.g.h[kNIfce] * w.g.w[kNIfce], 128, 16); }
-int gather_ctas(const Work& w) { return grid_for(w.N, 256, 8); }
+int gather_ctas(const Work& w) { return grid_for(w.N, 256, 4); }  // one wave at 4 CTAs per SM
 int reduce_ctas() { return kReduceCtas; }
 
 // ---- single-job launches

@@ -54,76 +54,118 @@ __global__ void k_up_fwd_b(Batch<UpFwdArgs> b) {
 //   output rows oy that read input row py through tap tau; dh_tau += G_tau * R[j][py][ox] with R
 //   the forward row-pass value.
 // Pass B (rows): dS[j][py][px] = sum_tau h_tau G'_tau over T; dh_tau += G'_tau * S[j][py][px].
+//
+// Output o reads inputs poly_first(o) .. poly_first(o)+3 (clamped), so input p is read only by
+// outputs 2p-3 .. 2p+4.  A CTA owns a tile of ty input rows by kUpTX input columns of one
+// channel and stages in shared memory the D block those outputs span (zero outside the grid),
+// the T block pass B needs and the clamped S columns of the row pass: every D element is read
+// from L2 about (2ty+6)/(2ty) times instead of four times.
 // ---------------------------------------------------------------------------------------------
+constexpr int kUpDC = 2 * kUpTX + 6;  // D and T columns: outputs 2*px0-3 .. 2*px0+2*kUpTX+2
+constexpr int kUpSC = kUpTX + 4;      // S columns px0-2 .. px0+kUpTX+1 (clamped)
+constexpr int kUpSmemFloats = (2 * kUpTYMax + 6) * kUpDC + kUpTYMax * kUpDC + kUpTYMax * kUpSC;
 
-// G[tau] for input index p along an axis with n_in inputs and n_out (cropped) outputs, reading
-// the output-side values through `get(o)`.
+// G[tau] for input p (of n_in) from the eight outputs 2p-3+q, q = 0..7, whose values are v(q)
+// (zero for outputs outside the grid).  Away from the borders output 2p-3+q reads p through tap
+// a b c d d c b a; at the borders the replicate clamp decides which taps read p.
 template <typename F>
-__device__ __forceinline__ void gather_taps(int p, int n_in, int n_out, F get, float (&G)[4]) {
+__device__ __forceinline__ void taps_of_input(int p, int n_in, F v, float (&G)[4]) {
     G[0] = G[1] = G[2] = G[3] = 0.f;
     if (p >= 2 && p <= n_in - 3) {
-        const int o0 = 2 * p - 3;  // outputs 2p-3 .. 2p+4 use taps a b c d d c b a
-        const int tt[8] = {0, 1, 2, 3, 3, 2, 1, 0};
+        G[0] = v(0) + v(7);
+        G[1] = v(1) + v(6);
+        G[2] = v(2) + v(5);
+        G[3] = v(3) + v(4);
+    } else {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int o = o0 + q;
-            if (o < n_out) G[tt[q]] += get(o);
-        }
-    } else {
-        const int lo = max(0, 2 * p - 7), hi = min(n_out - 1, 2 * p + 8);
-        for (int o = lo; o <= hi; ++o) {
+            const int o = 2 * p - 3 + q;
             const int f = poly_first(o);
-            const float v = get(o);
+            const float u = v(q);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float u = clampi(f + q, 0, n_in - 1) == p ? v : 0.f;
-                const int t = poly_tap(o, q);
-                G[0] += t == 0 ? u : 0.f;
-                G[1] += t == 1 ? u : 0.f;
-                G[2] += t == 2 ? u : 0.f;
-                G[3] += t == 3 ? u : 0.f;
+            for (int k = 0; k < 4; ++k) {
+                const float x = clampi(f + k, 0, n_in - 1) == p ? u : 0.f;
+                const int t = poly_tap(o, k);
+                G[0] += t == 0 ? x : 0.f;
+                G[1] += t == 1 ? x : 0.f;
+                G[2] += t == 2 ? x : 0.f;
+                G[3] += t == 3 ? x : 0.f;
             }
         }
     }
 }
 
-// One CTA per (channel j, input row py) pair (grid-stride): pass A builds the row T[j][py][.]
-// in shared memory from the <= 8 output rows that read input row py, pass B gathers it along x.
 __device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int ncta) {
-    extern __shared__ float sTrow[];  // wt floats
+    extern __shared__ float smem_up[];
+    float* sD = smem_up;                                // [2ty+6][kUpDC]
+    float* sT = sD + (2 * kUpTYMax + 6) * kUpDC;        // [ty][kUpDC]
+    float* sS = sT + kUpTYMax * kUpDC;                  // [ty][kUpSC]
     const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
     float dh[4] = {0.f, 0.f, 0.f, 0.f};
-    const int npairs = a.nch * a.hs;
-    for (int pair = cta; pair < npairs; pair += ncta) {
-        const int j = pair / a.hs, py = pair - j * a.hs;
+    const int ty = a.ty;
+    const int nty = (a.hs + ty - 1) / ty, ntx = (a.ws + kUpTX - 1) / kUpTX;
+    const int tiles = a.nch * nty * ntx;
+    for (int tile = cta; tile < tiles; tile += ncta) {
+        const int j = tile / (nty * ntx);
+        const int rem = tile - j * nty * ntx;
+        const int py0 = (rem / ntx) * ty, px0 = (rem - (rem / ntx) * ntx) * kUpTX;
+        const int r0 = 2 * py0 - 3, c0 = 2 * px0 - 3;
         const float* Dj = a.D + (int64_t)j * a.ht * a.wt;
-        const float* S = (j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws) + (int64_t)py * a.ws;
-        for (int ox = threadIdx.x; ox < a.wt; ox += blockDim.x) {
-            float G[4];
-            gather_taps(py, a.hs, a.ht, [&](int oy) { return __ldg(Dj + (int64_t)oy * a.wt + ox); }, G);
-            sTrow[ox] = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
-            const int fx = poly_first(ox);
-            float wx[4];
-            poly_w(ox, tp, wx);
-            float R = 0.f;  // forward row-pass value at (py, ox)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) R = fmaf(wx[q], __ldg(S + clampi(fx + q, 0, a.ws - 1)), R);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], R, dh[q]);
+        const float* S = j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws;
+        const int nd = (2 * ty + 6) * kUpDC;
+        for (int e = threadIdx.x; e < nd; e += blockDim.x) {
+            const int r = e / kUpDC, c = e - r * kUpDC;
+            const int gr = r0 + r, gc = c0 + c;
+            sD[e] = (gr >= 0 && gr < a.ht && gc >= 0 && gc < a.wt) ? __ldg(Dj + (int64_t)gr * a.wt + gc) : 0.f;
+        }
+        for (int e = threadIdx.x; e < ty * kUpSC; e += blockDim.x) {
+            const int r = e / kUpSC, c = e - r * kUpSC;
+            const int py = py0 + r;
+            sS[e] = py < a.hs ? __ldg(S + (int64_t)py * a.ws + clampi(px0 - 2 + c, 0, a.ws - 1)) : 0.f;
         }
         __syncthreads();
-        for (int px = threadIdx.x; px < a.ws; px += blockDim.x) {
-            float G[4];
-            gather_taps(px, a.ws, a.wt, [&](int ox) { return sTrow[ox]; }, G);
-            const float d = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
-            const float sv = __ldg(S + px);
+        // pass A: T over output columns c0 .. c0+kUpDC-1 of the tile's input rows
+        for (int e = threadIdx.x; e < ty * kUpDC; e += blockDim.x) {
+            const int r = e / kUpDC, c = e - r * kUpDC;
+            const int py = py0 + r, ox = c0 + c;
+            float t = 0.f;
+            if (py < a.hs && ox >= 0 && ox < a.wt) {
+                float G[4];
+                const float* col = sD + 2 * r * kUpDC + c;
+                taps_of_input(py, a.hs, [&](int q) { return col[q * kUpDC]; }, G);
+                t = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
+                if (ox >= 2 * px0 && ox < 2 * px0 + 2 * kUpTX) {  // this tile owns (py, ox) for dh
+                    float wx[4];
+                    poly_w(ox, tp, wx);
+                    const float* srow = sS + r * kUpSC + (poly_first(ox) - (px0 - 2));
+                    float R = 0.f;  // forward row-pass value at (py, ox)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], sv, dh[q]);
-            const int64_t si = (int64_t)py * a.ws + px;
-            if (j == 0)
-                a.out0[si] = d;
-            else
-                a.outup[(int64_t)(j - 1) * a.hs * a.ws + si] = d;
+                    for (int q = 0; q < 4; ++q) R = fmaf(wx[q], srow[q], R);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], R, dh[q]);
+                }
+            }
+            sT[e] = t;
+        }
+        __syncthreads();
+        // pass B: the tile's inputs from T
+        for (int e = threadIdx.x; e < ty * kUpTX; e += blockDim.x) {
+            const int r = e / kUpTX, c = e - r * kUpTX;
+            const int py = py0 + r, px = px0 + c;
+            if (py < a.hs && px < a.ws) {
+                float G[4];
+                const float* row = sT + r * kUpDC + 2 * c;
+                taps_of_input(px, a.ws, [&](int q) { return row[q]; }, G);
+                const float d = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
+                const float sv = sS[r * kUpSC + c + 2];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], sv, dh[q]);
+                const int64_t si = (int64_t)py * a.ws + px;
+                if (j == 0)
+                    a.out0[si] = d;
+                else
+                    a.outup[(int64_t)(j - 1) * a.hs * a.ws + si] = d;
+            }
         }
         __syncthreads();
     }
@@ -152,11 +194,24 @@ int up_grid(int64_t total) {
 
 }  // namespace
 
-int up_adj_grid(int64_t pairs) { return (int)(pairs < kUpMaxCta ? (pairs < 1 ? 1 : pairs) : kUpMaxCta); }
+// Tile height of stage s's adjoint: the tallest of 16, 8, 4, 2 rows that still gives two CTAs per
+// SM, so the fine stages read the fewest halo rows and the coarse ones keep enough CTAs.
+int up_adj_ty(int nch, int hs, int ws) {
+    const int64_t want = 2 * (int64_t)num_sms();
+    const int64_t ntx = (ws + kUpTX - 1) / kUpTX;
+    for (int ty = kUpTYMax; ty > 2; ty /= 2)
+        if ((int64_t)nch * ((hs + ty - 1) / ty) * ntx >= want) return ty;
+    return 2;
+}
+int up_adj_ctas(int nch, int hs, int ws) {
+    const int ty = up_adj_ty(nch, hs, ws);
+    const int64_t tiles = (int64_t)nch * ((hs + ty - 1) / ty) * ((ws + kUpTX - 1) / kUpTX);
+    return (int)(tiles < kUpMaxCta ? (tiles < 1 ? 1 : tiles) : kUpMaxCta);
+}
 
 void synth_init_attributes() {
-    cudaFuncSetAttribute(k_up_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * (int)sizeof(float));
-    cudaFuncSetAttribute(k_up_adj_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * (int)sizeof(float));
+    cudaFuncSetAttribute(k_up_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpSmemFloats * (int)sizeof(float));
+    cudaFuncSetAttribute(k_up_adj_b, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpSmemFloats * (int)sizeof(float));
     syn_init_attributes();
 }
 
@@ -193,7 +248,7 @@ UpAdjArgs up_adj_args(const Work& w, const float* params, int st) {  // stage st
     a.ht = g.h[st - 1];
     a.wt = g.w[st - 1];
     a.nch = kL - st;
-    a.pad_ = 0;
+    a.ty = up_adj_ty(a.nch, a.hs, a.ws);
     return a;
 }
 
@@ -204,13 +259,13 @@ void launch_up_forward(const Work& w, const float* params, cudaStream_t s) {
 
 void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
     for (int st = 1; st < kL; ++st)
-        launch_pdl(k_up_adj, w.n_cta_up[st], kUpThreads, (size_t)w.g.w[st - 1] * sizeof(float), s, up_adj_args(w, params, st));
+        launch_pdl(k_up_adj, w.n_cta_up[st], kUpThreads, kUpSmemFloats * sizeof(float), s, up_adj_args(w, params, st));
 }
 
-// ---- multi-job launches (max_wt: the widest row any job's stage reads, for the shared row buffer)
+// ---- multi-job launches
 void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s) { launch_pdl(k_up_fwd_b, b.total_ctas, kUpThreads, 0, s, b); }
-void launch_up_adj_b(const Batch<UpAdjArgs>& b, int max_wt, cudaStream_t s) {
-    launch_pdl(k_up_adj_b, b.total_ctas, kUpThreads, (size_t)max_wt * sizeof(float), s, b);
+void launch_up_adj_b(const Batch<UpAdjArgs>& b, cudaStream_t s) {
+    launch_pdl(k_up_adj_b, b.total_ctas, kUpThreads, kUpSmemFloats * sizeof(float), s, b);
 }
 
 }  // namespace cc

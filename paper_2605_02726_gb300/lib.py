@@ -102,6 +102,7 @@ EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count
             "coolchic_batch_step", "coolchic_batch_records", "coolchic_batch_destroy"]
 
 KERNEL_ARM, KERNEL_SYN_BWD, KERNEL_CONV, KERNEL_SYN_FWD = 0, 1, 2, 3
+KERNEL_UP_FWD, KERNEL_UP_ADJ, KERNEL_GATHER = 4, 5, 6
 
 
 def timing_enable(kernel_id: int, max_launches: int):

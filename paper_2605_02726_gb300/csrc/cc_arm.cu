@@ -175,12 +175,10 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     const float2* w3c = reinterpret_cast<const float2*>(sC + 16) + tq;     // [o * 8 + nt * 4]
     const float2* wsc = reinterpret_cast<const float2*>(sC + 48) + tq;     // [o * 12 + nt * 4]
     __syncthreads();
-    int ndy[4], ndx[4];  // context slots t, t+4, t+8, t+12 of this lane
+    // context slots t, t+4, t+8, t+12 of this lane, packed 5 bits each: dy + 3 (2 bits), dx + 3 (3 bits)
+    int nd = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        ndy[q] = ctx_dy(tq + 4 * q);
-        ndx[q] = ctx_dx(tq + 4 * q);
-    }
+    for (int q = 0; q < 4; ++q) nd |= ((ctx_dy(tq + 4 * q) + 3) | ((ctx_dx(tq + 4 * q) + 3) << 2)) << (5 * q);
     const float mu_b = a.params[po::arm_b3] + a.params[po::arm_bs];
     const float s_b = a.params[po::arm_b3 + 1] + a.params[po::arm_bs + 1];
 
@@ -228,6 +226,12 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         ifce_inputs(g, a.yt, pA, rA);
         ifce_inputs(g, a.yt, pB, rB);
         float cA[6], cB[6];
+        int ndy[4], ndx[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ndy[q] = ((nd >> (5 * q)) & 3) - 3;
+            ndx[q] = ((nd >> (5 * q + 2)) & 7) - 3;
+        }
         cA[0] = neighbour(g, a.yt, pA, ndy[0], ndx[0]);
         cA[1] = neighbour(g, a.yt, pA, ndy[1], ndx[1]);
         cA[2] = neighbour(g, a.yt, pA, ndy[2], ndx[2]);
@@ -498,30 +502,52 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             }
         }
         __syncwarp();
-        // ---- parameter-gradient tiles over K = 16 latents (two k-steps of 8)
+        // ---- parameter-gradient tiles over K = 16 latents (two k-steps of 8), fragments by ldmatrix:
+        // an A fragment (16 rows) is matrices (rows 0-7, k 0-3), (8-15, 0-3), (0-7, 4-7), (8-15, 4-7);
+        // a pair of B fragments (8 rows each) is (rows of the first, k 0-3), (first, 4-7),
+        // (second, 0-3), (second, 4-7).
+        {
+            const int mi = lane >> 3, ri = lane & 7;
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            const int k0 = ks * 8;
-            auto afrag = [&](int row0) {
-                return make_a(st[(row0 + gq) * kSld + k0 + tq], st[(row0 + gq + 8) * kSld + k0 + tq],
-                              st[(row0 + gq) * kSld + k0 + tq + 4], st[(row0 + gq + 8) * kSld + k0 + tq + 4]);
-            };
-            auto bfrag = [&](int row0) {  // as an AFrag whose h[0..1], l[0..1] hold (b0, b1)
-                AFrag f;
-                split2(st[(row0 + gq) * kSld + k0 + tq], f.h[0], f.l[0]);
-                split2(st[(row0 + gq) * kSld + k0 + tq + 4], f.h[1], f.l[1]);
-                return f;
-            };
-            const AFrag UA1 = afrag(U_DA1), UA2 = afrag(U_DA2), UO = afrag(U_O);
-            const AFrag VC0 = bfrag(V_C), VC1 = bfrag(V_C + 8), VC2 = bfrag(V_C + 16);
-            const AFrag VH10 = bfrag(V_H1), VH11 = bfrag(V_H1 + 8);
-            const AFrag VR = bfrag(V_R);
-            mma3b(acc[0], UA1, VC0);
-            mma3b(acc[1], UA1, VC1);
-            mma3b(acc[2], UA1, VC2);
-            mma3b(acc[3], UA2, VH10);
-            mma3b(acc[4], UA2, VH11);
-            mma3b(acc[5], UO, VR);
+            for (int ks = 0; ks < 2; ++ks) {
+                const int k0 = ks * 8;
+                const float* arow = st + (ri + (mi & 1) * 8) * kSld + k0 + (mi >> 1) * 4;  // + row0 * kSld
+                const float* brow = st + ri * kSld + k0 + (mi & 1) * 4;                    // + first/second row0
+                auto afrag = [&](int row0) {
+                    uint32_t r[4];
+                    ldsm_x4(r, arow + row0 * kSld);
+                    AFrag f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) split_u(r[q], f.h[q], f.l[q]);
+                    return f;
+                };
+                auto bpair = [&](int row0a, int row0b, AFrag& fa, AFrag& fb) {  // (b0, b1) in h[0..1], l[0..1]
+                    uint32_t r[4];
+                    ldsm_x4(r, brow + ((mi >> 1) ? row0b : row0a) * kSld);
+                    split_u(r[0], fa.h[0], fa.l[0]);
+                    split_u(r[1], fa.h[1], fa.l[1]);
+                    split_u(r[2], fb.h[0], fb.l[0]);
+                    split_u(r[3], fb.h[1], fb.l[1]);
+                };
+                {
+                    const AFrag UA1 = afrag(U_DA1);
+                    AFrag VC0, VC1, VC2, VR;
+                    bpair(V_C, V_C + 8, VC0, VC1);
+                    mma3b(acc[0], UA1, VC0);
+                    mma3b(acc[1], UA1, VC1);
+                    bpair(V_C + 16, V_R, VC2, VR);
+                    mma3b(acc[2], UA1, VC2);
+                    const AFrag UO = afrag(U_O);
+                    mma3b(acc[5], UO, VR);
+                }
+                {
+                    const AFrag UA2 = afrag(U_DA2);
+                    AFrag VH10, VH11;
+                    bpair(V_H1, V_H1 + 8, VH10, VH11);
+                    mma3b(acc[3], UA2, VH10);
+                    mma3b(acc[4], UA2, VH11);
+                }
+            }
         }
         __syncwarp();
     }

@@ -52,6 +52,16 @@ __device__ __forceinline__ void mma3b(float (&d)[4], const AFrag& a, const AFrag
     mma1(d, a.h, b.l[0], b.l[1]);
     mma1(d, a.h, b.h[0], b.h[1]);
 }
+// ldmatrix of 32-bit values: a matrix "row" is 4 consecutive floats (16 bytes) of shared memory,
+// and lane l receives float l % 4 of row l / 4 of each 8x4 matrix.  `row` is this lane's row
+// address (16-byte aligned): lanes 8m..8m+7 address the rows of matrix m.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const float* row) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void split_u(uint32_t x, uint32_t& hi, uint32_t& lo) { split2(__uint_as_float(x), hi, lo); }
 // v[i] for a runtime i without a dynamically indexed (local-memory) array
 template <int NV>
 __device__ __forceinline__ float sel(const float (&v)[NV], int i) {

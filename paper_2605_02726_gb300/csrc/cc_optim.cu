@@ -181,18 +181,13 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
         float acc = a.dYd[i] + a.dYsyn[i];
 #pragma unroll
         for (int n = 0; n < kNCtx; ++n) acc += v[n];
-        if (k == 1 || k == 2) {
-            // grid 1: 2x2 block of dR0 channel 0; grid 2: 4x4 block of dR0 channel 1, 2x2 of dR1 channel 0
-            for (int kp = 0; kp < k; ++kp) {
-                const float* dR = kp == 0 ? a.dR0 : a.dR1;
-                const int sh = k - kp, ch = k - kp - 1;
-                const int hkp = g.h[kp], wp = g.w[kp];
-                const int r0 = r << sh, c0 = c << sh;
-                const int bh = min(1 << sh, hkp - r0), bw = min(1 << sh, wp - c0);
-                const float* plane = dR + (int64_t)ch * hkp * wp;
-                for (int rr = 0; rr < bh; ++rr)
-                    for (int cc = 0; cc < bw; ++cc) acc += __ldg(plane + (int64_t)(r0 + rr) * wp + c0 + cc);
-            }
+        // IFCE users, as blocks summed with all their loads in flight (unrolled, clipped to the grid)
+        if (k == 1) {  // 2x2 block of dR0 channel 0
+            acc += block_sum_clipped<2>(a.dR0, g.h[0], g.w[0], 2 * r, 2 * c);
+        } else if (k == 2) {  // 4x4 block of dR0 channel 1, 2x2 block of dR1 channel 0
+            const int64_t n0 = (int64_t)g.h[0] * g.w[0];
+            acc += block_sum_clipped<4>(a.dR0 + n0, g.h[0], g.w[0], 4 * r, 4 * c);
+            acc += block_sum_clipped<2>(a.dR1, g.h[1], g.w[1], 2 * r, 2 * c);
         } else if (k == kNIfce) {
             acc += a.dIf[li];
         } else if (k > kNIfce) {
@@ -200,9 +195,9 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
             const int sh = k - kNIfce, h3 = g.h[kNIfce], w3 = g.w[kNIfce];
             const float* plane = a.dIf + (int64_t)sh * h3 * w3;
             const int r0 = r << sh, c0 = c << sh;
-            const int bh = min(1 << sh, h3 - r0), bw = min(1 << sh, w3 - c0);
-            for (int rr = 0; rr < bh; ++rr)
-                for (int cc = 0; cc < bw; ++cc) acc += plane[(int64_t)(r0 + rr) * w3 + c0 + cc];
+            acc += sh == 1 ? block_sum_clipped<2>(plane, h3, w3, r0, c0)
+                 : sh == 2 ? block_sum_clipped<4>(plane, h3, w3, r0, c0)
+                           : block_sum_clipped<8>(plane, h3, w3, r0, c0);
         }
         if (a.zero_grad) acc = 0.f;
         const float yi = a.y[i];

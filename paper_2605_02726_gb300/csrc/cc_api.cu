@@ -255,7 +255,7 @@ static void run_forward(const Work& w, const float* image, const float* latents,
     launch_arm(w, params, arm_pass, arm_gscale, s);
     tend(CC_KERNEL_ARM, s);
     tbeg(CC_KERNEL_UP_FWD, s);
-    launch_up_forward(w, params, s);
+    launch_up_forward(w, params, kUpArmLo - 1, s);
     tend(CC_KERNEL_UP_FWD, s);
     tbeg(CC_KERNEL_SYN_FWD, s);
     launch_syn_forward(w, params, syn_pass, s);
@@ -356,9 +356,10 @@ int64_t coolchic_kernel_launches(const cc_arch_t* a, int32_t n_iters) {
     if (check_arch(a)) return -1;
     if (n_iters < 0) return fail(CC_ERR_ARG, "n_iters must be >= 0"), -1;
     if (n_iters == 0) return 0;
-    // per iteration: entropy model, synthesis forward, convs, synthesis adjoint, IFCE, gather,
-    // reduce, finish, forward upsampling stages 2..6 and adjoint stages 1..6; relax once per call
-    const int64_t per_iter = 8 + (kL - 2) + (kL - 1);
+    // per iteration: entropy model (with the coarse forward upsampling stages), synthesis forward,
+    // convs, synthesis adjoint, IFCE, gather, reduce, finish, forward upsampling stages 2..kUpArmLo
+    // and adjoint stages 1..6; relax once per call
+    const int64_t per_iter = 8 + (kUpArmLo - 1) + (kL - 1);
     return 1 + per_iter * n_iters;
 }
 
@@ -489,7 +490,7 @@ int coolchic_decode_image(const cc_arch_t* arch, const int32_t* q, const float* 
     cudaStream_t s = (cudaStream_t)stream;
     launch_decode(w.g, q, params, w.yt, prob_q16, mu_q, logb_q, s);
     if (image_out) {
-        launch_up_forward(w, params, s);
+        launch_up_forward(w, params, kL - 2, s);  // no entropy-model launch: every stage
         launch_syn_forward(w, params, PASS_FWD, s);
         // the residual convs of the forward pass against a dummy target; only xhat is kept
         launch_conv(w, params, w.dt, PASS_FWD, 0.f, image_out, s);

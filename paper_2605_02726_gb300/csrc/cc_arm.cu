@@ -23,6 +23,7 @@
 // are added in a fixed order at the end: one partial gradient per CTA.
 #include "cc_kernels.h"
 #include "cc_mma.cuh"
+#include "cc_upfwd.cuh"
 
 namespace cc {
 namespace {
@@ -133,6 +134,13 @@ __device__ int wgrad_index(int T, int row, int col) {
     return -1;
 }
 
+// The coarse forward upsampling stages of CTA 0, out of line: inlined, their registers would
+// shape the allocation of the latent loop.
+__device__ __noinline__ void coarse_upsampling(const ArmArgs& a, float* sm) {
+#pragma unroll 1
+    for (int q = 0; q < kUpArmStages; ++q) up_fwd_stage_cta(a.upc[q], sm, kWarps * kStage);
+}
+
 template <int PASS>
 __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     constexpr bool BWD = pass_bwd(PASS);
@@ -182,6 +190,33 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     const float mu_b = a.params[po::arm_b3] + a.params[po::arm_bs];
     const float s_b = a.params[po::arm_b3 + 1] + a.params[po::arm_bs + 1];
 
+    // CTA 0 computes the coarse forward upsampling stages (it takes no latents when there are
+    // other CTAs), staged through the weight-gradient staging area before its constant rows are
+    // set; each stage ends with a barrier, so its output is visible to the next.
+    //   Units: with W warps in all, no warp takes more than Q = ceil(units / W); the warps of CTAs
+    // 1.. take units [0, U1) round-robin (U1 = min(units, Q * their number)) and the warps of CTA 0
+    // only the rest [U1, units), so that the coarse stages do not lengthen the launch.
+    // (units < 2^31: images are at most 16384 x 16384)
+    const int64_t N = a.N;
+    const int n_units = (int)((N + 15) / 16);
+    int u_first = cta * kWarps + wid, u_step = ncta * kWarps, u_end = n_units;
+    if (a.upc_on) {
+        if (cta == 0) coarse_upsampling(a, sStage);
+        if (ncta > 1) {
+            const int w_all = ncta * kWarps, w_reg = w_all - kWarps;
+            const int q_max = (int)(((int64_t)n_units + w_all - 1) / w_all);
+            const int u1 = (int)std::min<int64_t>(n_units, (int64_t)q_max * w_reg);
+            if (cta > 0) {
+                u_first = (cta - 1) * kWarps + wid;
+                u_step = w_reg;
+                u_end = u1;
+            } else {
+                u_first = u1 + wid;
+                u_step = kWarps;
+            }
+        }
+    }
+
     float* st = sStage + wid * kStage;
     if (BWD) {  // constant staging rows: C one (20) and zeros (21-23), R one (6) and zero (7), U_O zeros (0, 1, 14, 15)
         for (int j = lane; j < kSld; j += 32) {
@@ -216,11 +251,9 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     for (int q = 0; q < 6; ++q) sws[q][0] = sws[q][1] = 0.f;
     float rate_acc = 0.f;
 
-    const int64_t N = a.N;
-    const int64_t n_units = (N + 15) / 16;
-    for (int64_t u = (int64_t)cta * kWarps + wid; u < n_units; u += (int64_t)ncta * kWarps) {
-        const LatentPos pA = locate(g, rcp_w, u * 16 + gq, N);
-        const LatentPos pB = locate(g, rcp_w, u * 16 + gq + 8, N);
+    for (int u = u_first; u < u_end; u += u_step) {
+        const LatentPos pA = locate(g, rcp_w, (int64_t)u * 16 + gq, N);
+        const LatentPos pB = locate(g, rcp_w, (int64_t)u * 16 + gq + 8, N);
         // ---- context features f in {t, t+4, 8+t, 12+t, 16+t, 20+t} of latents A (row g) and B (row g+8)
         float rA[6], rB[6];
         ifce_inputs(g, a.yt, pA, rA);
@@ -640,9 +673,9 @@ __global__ void __launch_bounds__(kT, 3) k_arm_b(Batch<ArmArgs> b) {
 
 }  // namespace
 
-size_t arm_smem_bytes(int pass) {  // the staging tiles exist only for the adjoint passes
-    return (size_t)FR_N * 32 * sizeof(float4) +
-           (size_t)(kIfceSm + (pass_bwd(pass) ? kWarps * kStage : 0)) * sizeof(float);
+size_t arm_smem_bytes(int pass) {  // staging tiles: weight-gradient factors, or the coarse upsampling in CTA 0
+    (void)pass;
+    return (size_t)FR_N * 32 * sizeof(float4) + (size_t)(kIfceSm + kWarps * kStage) * sizeof(float);
 }
 
 int arm_grid(int64_t N) {
@@ -654,6 +687,9 @@ int arm_grid(int64_t N) {
 
 ArmArgs arm_args(const Work& w, const float* params, float grad_scale) {
     ArmArgs a;
+    for (int q = 0; q < kUpArmStages; ++q) a.upc[q] = up_fwd_args(w, params, kL - 2 - q);
+    a.upc_on = 1;
+    a.pad2_ = 0;
     a.pad_ = 0;
     a.g = w.g;
     a.N = w.N;
@@ -672,7 +708,8 @@ ArmArgs arm_args(const Work& w, const float* params, float grad_scale) {
 }
 
 void launch_arm(const Work& w, const float* params, int pass, float grad_scale, cudaStream_t s) {
-    const ArmArgs a = arm_args(w, params, grad_scale);
+    ArmArgs a = arm_args(w, params, grad_scale);
+    if (pass == PASS_BWD_LOAD) a.upc_on = 0;  // the upsampled grids are still in the workspace
     const size_t sm = arm_smem_bytes(pass);
     const int grid = w.n_cta_arm;
     switch (pass) {

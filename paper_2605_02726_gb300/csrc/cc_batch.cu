@@ -49,6 +49,7 @@ struct TableWriter {
 // relative to `dev_base`, fixed up once the table is placed).
 template <typename A>
 Batch<A> put(TableWriter& tw, const std::vector<A>& args, const std::vector<int>& ctas, const std::vector<int>& order) {
+    static_assert(sizeof(A) <= 512, "table_bytes assumes argument structs of at most 512 bytes");
     const int n = (int)args.size();
     const size_t oa = tw.take(sizeof(A) * n), ob = tw.take(sizeof(int) * (n + 1));
     std::vector<int> begin(n + 1, 0);
@@ -231,7 +232,7 @@ int coolchic_batch_step(cc_batch_t* b, int32_t n_iters, void* stream) {
     for (int it = 0; it < n_iters; ++it) {
         if (it == 0) launch_relax_b(b->relax, s);  // later iterations: relaxed by the previous Adam update
         launch_arm_b(b->arm, PASS_FWD_BWD, s);
-        for (int m = kL - 2; m >= 1; --m) launch_up_fwd_b(b->upf[m], s);
+        for (int m = kUpArmLo - 1; m >= 1; --m) launch_up_fwd_b(b->upf[m], s);  // the rest in the entropy-model launch
         launch_syn_fwd_b(b->synf, s);
         launch_conv_b(b->conv, s);
         launch_syn_bwd_b(b->synb, s);

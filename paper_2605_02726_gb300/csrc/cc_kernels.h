@@ -190,7 +190,21 @@ struct RelaxArgs {
     int relax;
     int pad_;
 };
+struct UpFwdArgs {
+    const float* src0;   // y~ of grid m+1
+    const float* srcup;  // up[m+1] (channels 1..), may be null when nch == 1
+    float* dst;          // up[m]
+    const float* taps;   // 4 taps of this stage (device)
+    int hs, ws, ht, wt, nch, pad_;
+};
+// The forward upsampling outputs up[m] for m >= kUpArmLo (stages 6..4, grids of 1/16 the image
+// and smaller) are computed by the first CTA of the entropy-model launch, which needs none of
+// them and whose other CTAs take all the latents; the per-stage kernels compute the rest.
+constexpr int kUpArmLo = 3;
+constexpr int kUpArmStages = kL - 1 - kUpArmLo;  // up[5], up[4], up[3]
 struct ArmArgs {
+    UpFwdArgs upc[kUpArmStages];  // m = kL-2 down to kUpArmLo
+    int upc_on, pad2_;
     Geom g;
     int64_t N;
     const float* yt;
@@ -205,13 +219,6 @@ struct ArmArgs {
     float* act;         // [34][N]: a1 (16), a2 (16), mu, s
     float* gpart;       // [n_cta][756]
     double* rate_part;  // [n_cta]
-};
-struct UpFwdArgs {
-    const float* src0;   // y~ of grid m+1
-    const float* srcup;  // up[m+1] (channels 1..), may be null when nch == 1
-    float* dst;          // up[m]
-    const float* taps;   // 4 taps of this stage (device)
-    int hs, ws, ht, wt, nch, pad_;
 };
 struct SynArgs {
     Geom g;
@@ -311,8 +318,9 @@ void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_
                   const Hp& hp, int relax, cudaStream_t s);
 // a2-a3 and a9: entropy model over all latents.
 void launch_arm(const Work& w, const float* params, int pass, float grad_scale, cudaStream_t s);
-// a4: upsampling stages 6..2 (stage 1 is fused into the synthesis kernels).
-void launch_up_forward(const Work& w, const float* params, cudaStream_t s);
+// a4: upsampling stages m_hi+1 .. 2, output up[m_hi] .. up[1] (stage 1 is fused into the
+// synthesis kernels; after an entropy-model launch m_hi = kUpArmLo - 1, for decoding kL - 2).
+void launch_up_forward(const Work& w, const float* params, int m_hi, cudaStream_t s);
 // a5-a7: synthesis MLP, residual convs, distortion and their adjoints.
 void launch_syn_forward(const Work& w, const float* params, int pass, cudaStream_t s);
 void launch_conv(const Work& w, const float* params, const float* image, int pass, float grad_scale,

@@ -121,7 +121,7 @@ extern "C" int coolchic_rate_distortion_noalloc(const cc_arch_t* arch, const cc_
     double* rd_dev = (double*)w.grad_params;
     launch_relax(w, latents, nullptr, step, h, relax, s);
     launch_arm(w, params, PASS_FWD, 0.f, s);
-    launch_up_forward(w, params, s);
+    launch_up_forward(w, params, kUpArmLo - 1, s);
     launch_syn_forward(w, params, PASS_FWD, s);
     launch_conv(w, params, image, PASS_FWD, 0.f, nullptr, s);
     launch_finish(w, h, 1, 1, rd_dev, nullptr, 0, 0, s);

@@ -2,40 +2,11 @@
 // adjoint of every stage with the tap gradients (per-CTA partials, reduced in a fixed order).
 // Stage 1 forward is fused into the synthesis kernels (cc_syn.cu).
 #include "cc_kernels.h"
+#include "cc_upfwd.cuh"
 
 namespace cc {
 namespace {
 
-// ---------------------------------------------------------------------------------------------
-// Upsampling stage s (grid s -> grid s-1), forward, stages 6..2.  Output up[m], m = s-1, holds
-// the channels of grids m+1..6: channel 0 comes from y~^(m+1), channel j >= 1 from up[m+1][j-1].
-// Separable 4x4 polyphase taps with replicate (clamped) indices, cropped to the grid size.
-// ---------------------------------------------------------------------------------------------
-
-__device__ __forceinline__ void up_fwd_body(const UpFwdArgs& a, int cta, int ncta) {
-    const int64_t total = (int64_t)a.nch * a.ht * a.wt;
-    const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
-    for (int64_t e = cta * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)ncta * blockDim.x) {
-        const int j = (int)(e / ((int64_t)a.ht * a.wt));
-        const int rem = (int)(e - (int64_t)j * a.ht * a.wt);
-        const int y = rem / a.wt, x = rem - y * a.wt;
-        const float* S = j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws;
-        const int fy = poly_first(y), fx = poly_first(x);
-        float wy[4], wx[4];
-        poly_w(y, tp, wy);
-        poly_w(x, tp, wx);
-        float acc = 0.f;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const float* row = S + clampi(fy + p, 0, a.hs - 1) * a.ws;
-            float rs = 0.f;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) rs = fmaf(wx[q], __ldg(row + clampi(fx + q, 0, a.ws - 1)), rs);
-            acc = fmaf(wy[p], rs, acc);
-        }
-        a.dst[e] = acc;
-    }
-}
 __global__ void k_up_fwd(UpFwdArgs a) {
     __shared__ UpFwdArgs sa;
     param_fetch(a, sa);
@@ -253,8 +224,8 @@ UpAdjArgs up_adj_args(const Work& w, const float* params, int st) {  // stage st
 }
 
 // ---- single-job launches
-void launch_up_forward(const Work& w, const float* params, cudaStream_t s) {
-    for (int m = kL - 2; m >= 1; --m) launch_pdl(k_up_fwd, up_fwd_ctas(w, m), kUpThreads, 0, s, up_fwd_args(w, params, m));
+void launch_up_forward(const Work& w, const float* params, int m_hi, cudaStream_t s) {
+    for (int m = m_hi; m >= 1; --m) launch_pdl(k_up_fwd, up_fwd_ctas(w, m), kUpThreads, 0, s, up_fwd_args(w, params, m));
 }
 
 void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {

@@ -37,33 +37,37 @@ constexpr int kUpSC = kUpTX + 4;      // S columns px0-2 .. px0+kUpTX+1 (clamped
 constexpr int kUpSmemFloats = (2 * kUpTYMax + 6) * kUpDC + kUpTYMax * kUpDC + kUpTYMax * kUpSC;
 
 // G[tau] for input p (of n_in) from the eight outputs 2p-3+q, q = 0..7, whose values are v(q)
-// (zero for outputs outside the grid).  Away from the borders output 2p-3+q reads p through tap
-// a b c d d c b a; at the borders the replicate clamp decides which taps read p.
+// (zero for outputs outside the grid): output 2p-3+q reads p through tap a b c d d c b a.  The
+// replicate clamp folds the virtual inputs beyond a border onto it, so input 0 also collects the
+// outputs of virtual inputs -1 and -2 (window positions q-2, q-4) and input n_in-1 those of n_in
+// and n_in+1 (q+2, q+4); every other input is read only through its own window.
 template <typename F>
 __device__ __forceinline__ void taps_of_input(int p, int n_in, F v, float (&G)[4]) {
-    G[0] = G[1] = G[2] = G[3] = 0.f;
-    if (p >= 2 && p <= n_in - 3) {
-        G[0] = v(0) + v(7);
-        G[1] = v(1) + v(6);
-        G[2] = v(2) + v(5);
-        G[3] = v(3) + v(4);
-    } else {
+    float u[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) u[q] = v(q);
+    if (p == 0 || p == n_in - 1) {
+        float w[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int o = 2 * p - 3 + q;
-            const int f = poly_first(o);
-            const float u = v(q);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float x = clampi(f + k, 0, n_in - 1) == p ? u : 0.f;
-                const int t = poly_tap(o, k);
-                G[0] += t == 0 ? x : 0.f;
-                G[1] += t == 1 ? x : 0.f;
-                G[2] += t == 2 ? x : 0.f;
-                G[3] += t == 3 ? x : 0.f;
+            float x = u[q];
+            if (p == 0) {
+                if (q >= 2) x += u[q - 2];
+                if (q >= 4) x += u[q - 4];
             }
+            if (p == n_in - 1) {
+                if (q + 2 <= 7) x += u[q + 2];
+                if (q + 4 <= 7) x += u[q + 4];
+            }
+            w[q] = x;
         }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) u[q] = w[q];
     }
+    G[0] = u[0] + u[7];
+    G[1] = u[1] + u[6];
+    G[2] = u[2] + u[5];
+    G[3] = u[3] + u[4];
 }
 
 __device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int ncta) {

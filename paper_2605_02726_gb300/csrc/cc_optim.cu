@@ -110,14 +110,13 @@ __global__ void k_ifce_cells_b(Batch<IfceArgs> b) {
 
 // ---------------------------------------------------------------------------------------------
 // Latent gradient: direct rate term + the 16 context users + IFCE users + upsampling/synthesis,
-// then Adam on (y, m, v) or a copy to grad_out.  `a` must be in shared memory or be the kernel
-// parameter of a single-job launch.  The per-launch scalars (grid tables, 1/w of every grid, the
-// Adam bias corrections, the proxy at this step and the next) are computed once per CTA; a latent
+// then Adam on (y, m, v) or a copy to grad_out.  `a` must be in shared memory (its grid tables are
+// indexed with a runtime grid number).  The per-launch scalars (1/w of every grid, the Adam bias
+// corrections, the proxy at this step and the next) are computed once per CTA; a latent
 // finds its row by a float reciprocal corrected to the exact quotient, and latents whose 16
 // context users all lie inside the grid load them without bounds tests.
 // ---------------------------------------------------------------------------------------------
 struct GatherScalars {
-    Geom g;
     float invw[kL];
     float bc1, bc2;
     ProxyAt px, px_next;
@@ -144,18 +143,27 @@ __device__ __forceinline__ void row_col(int li, int w, float invw, int& r, int& 
 }
 
 __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int ncta) {
+    // the per-launch scalars on four warps at once (the grid tables are read from `a`)
     __shared__ GatherScalars sc;
-    if (threadIdx.x == 0) {
-        sc.g = a.g;
-        for (int k = 0; k < kL; ++k) sc.invw[k] = 1.f / (float)a.g.w[k];
-        sc.step = a.step_dev ? *a.step_dev : a.step_host;
-        sc.bc1 = sc.bc2 = 1.f;
-        if (!a.grad_out) adam_bias_corrections(sc.step + 1, a.hp.beta1, a.hp.beta2, sc.bc1, sc.bc2);
-        sc.px = proxy_at(a.hp, sc.step);
-        sc.px_next = proxy_at(a.hp, sc.step + 1);
+    {
+        const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0 && wid < 3) {
+            const int64_t step = a.step_dev ? *a.step_dev : a.step_host;
+            if (wid == 0) {
+                sc.step = step;
+                sc.bc1 = sc.bc2 = 1.f;
+                if (!a.grad_out) adam_bias_corrections(step + 1, a.hp.beta1, a.hp.beta2, sc.bc1, sc.bc2);
+            } else if (wid == 1) {
+                sc.px = proxy_at(a.hp, step);
+            } else {
+                sc.px_next = proxy_at(a.hp, step + 1);
+            }
+        } else if (wid == 3 && lane < kL) {
+            sc.invw[lane] = 1.f / (float)a.g.w[lane];
+        }
     }
     __syncthreads();
-    const Geom& g = sc.g;
+    const Geom& g = a.g;
     const int64_t step = sc.step;
     const int64_t N = g.off[kL];
     const float* __restrict__ dS = a.dS;

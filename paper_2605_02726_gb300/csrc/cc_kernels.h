@@ -69,6 +69,7 @@ constexpr int kUpThreads = 256;
 constexpr int kUpMaxCta = 1024;    // per-stage cap on CTAs of an upsampling-adjoint pass
 constexpr int kUpTX = 64;          // input columns of an upsampling-adjoint tile
 constexpr int kUpTYMax = 16;       // tallest upsampling-adjoint tile (input rows)
+constexpr int kUpAdjThreads = 288; // 2 x (2 kUpTX + 6) column tasks of the adjoint's pass A, in 9 warps
 
 // Per-job device buffers carved from the caller's workspace (layout in cc_api.cu).
 struct Work {

@@ -70,6 +70,47 @@ __device__ __forceinline__ void taps_of_input(int p, int n_in, F v, float (&G)[4
     G[3] = u[3] + u[4];
 }
 
+// Pass A of a tile of TY input rows: thread t < 2 kUpDC takes column c = t mod kUpDC of the D
+// block and half of the tile's rows (R = TY/2, group t / kUpDC), sliding a register window of the
+// 2R + 6 output rows those inputs read down the column: each D value is loaded from shared memory
+// once per thread instead of once per input row that reads it.
+template <int TY>
+__device__ __forceinline__ void up_adj_pass_a(const UpAdjArgs& a, const float* sD, float* sT, const float* sS,
+                                              int py0, int px0, int c0, const float (&tp)[4], float (&dh)[4]) {
+    constexpr int R = TY / 2;
+    const int t = threadIdx.x;
+    if (t >= 2 * kUpDC) return;
+    const int grp = t >= kUpDC ? 1 : 0, c = t - grp * kUpDC;
+    const int ox = c0 + c;
+    const bool col_ok = ox >= 0 && ox < a.wt;
+    const bool own = ox >= 2 * px0 && ox < 2 * px0 + 2 * kUpTX;  // this tile owns (py, ox) for dh
+    float win[2 * R + 6];
+#pragma unroll
+    for (int k = 0; k < 2 * R + 6; ++k) win[k] = sD[(2 * grp * R + k) * kUpDC + c];
+    float wx[4];
+    poly_w(ox, tp, wx);
+    const int so = poly_first(ox) - (px0 - 2);  // S column of the row pass (owned ox only)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int tr = grp * R + r, py = py0 + tr;
+        float T = 0.f;
+        if (col_ok && py < a.hs) {
+            float G[4];
+            taps_of_input(py, a.hs, [&](int q) { return win[2 * r + q]; }, G);
+            T = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
+            if (own) {
+                const float* srow = sS + tr * kUpSC + so;
+                float Rv = 0.f;  // forward row-pass value at (py, ox)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Rv = fmaf(wx[q], srow[q], Rv);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], Rv, dh[q]);
+            }
+        }
+        sT[tr * kUpDC + c] = T;
+    }
+}
+
 __device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int ncta) {
     extern __shared__ float smem_up[];
     float* sD = smem_up;                                // [2ty+6][kUpDC]
@@ -100,27 +141,11 @@ __device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int nct
         }
         __syncthreads();
         // pass A: T over output columns c0 .. c0+kUpDC-1 of the tile's input rows
-        for (int e = threadIdx.x; e < ty * kUpDC; e += blockDim.x) {
-            const int r = e / kUpDC, c = e - r * kUpDC;
-            const int py = py0 + r, ox = c0 + c;
-            float t = 0.f;
-            if (py < a.hs && ox >= 0 && ox < a.wt) {
-                float G[4];
-                const float* col = sD + 2 * r * kUpDC + c;
-                taps_of_input(py, a.hs, [&](int q) { return col[q * kUpDC]; }, G);
-                t = tp[0] * G[0] + tp[1] * G[1] + tp[2] * G[2] + tp[3] * G[3];
-                if (ox >= 2 * px0 && ox < 2 * px0 + 2 * kUpTX) {  // this tile owns (py, ox) for dh
-                    float wx[4];
-                    poly_w(ox, tp, wx);
-                    const float* srow = sS + r * kUpSC + (poly_first(ox) - (px0 - 2));
-                    float R = 0.f;  // forward row-pass value at (py, ox)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) R = fmaf(wx[q], srow[q], R);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) dh[q] = fmaf(G[q], R, dh[q]);
-                }
-            }
-            sT[e] = t;
+        switch (ty) {
+            case 16: up_adj_pass_a<16>(a, sD, sT, sS, py0, px0, c0, tp, dh); break;
+            case 8: up_adj_pass_a<8>(a, sD, sT, sS, py0, px0, c0, tp, dh); break;
+            case 4: up_adj_pass_a<4>(a, sD, sT, sS, py0, px0, c0, tp, dh); break;
+            default: up_adj_pass_a<2>(a, sD, sT, sS, py0, px0, c0, tp, dh); break;
         }
         __syncthreads();
         // pass B: the tile's inputs from T
@@ -144,17 +169,17 @@ __device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int nct
         }
         __syncthreads();
     }
-    __shared__ float scratch[4 * (kUpThreads / 32)];
+    __shared__ float scratch[4 * (kUpAdjThreads / 32)];
     block_sum<4>(dh, scratch);
     if (threadIdx.x == 0)
         for (int q = 0; q < 4; ++q) a.gpart[cta * 4 + q] = dh[q];
 }
-__global__ void __launch_bounds__(kUpThreads) k_up_adj(UpAdjArgs a) {
+__global__ void __launch_bounds__(kUpAdjThreads) k_up_adj(UpAdjArgs a) {
     __shared__ UpAdjArgs sa;
     param_fetch(a, sa);
     up_adj_body(sa, blockIdx.x, gridDim.x);
 }
-__global__ void __launch_bounds__(kUpThreads) k_up_adj_b(Batch<UpAdjArgs> b) {
+__global__ void __launch_bounds__(kUpAdjThreads) k_up_adj_b(Batch<UpAdjArgs> b) {
     __shared__ UpAdjArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
@@ -234,13 +259,13 @@ void launch_up_forward(const Work& w, const float* params, int m_hi, cudaStream_
 
 void launch_up_adjoint(const Work& w, const float* params, cudaStream_t s) {
     for (int st = 1; st < kL; ++st)
-        launch_pdl(k_up_adj, w.n_cta_up[st], kUpThreads, kUpSmemFloats * sizeof(float), s, up_adj_args(w, params, st));
+        launch_pdl(k_up_adj, w.n_cta_up[st], kUpAdjThreads, kUpSmemFloats * sizeof(float), s, up_adj_args(w, params, st));
 }
 
 // ---- multi-job launches
 void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s) { launch_pdl(k_up_fwd_b, b.total_ctas, kUpThreads, 0, s, b); }
 void launch_up_adj_b(const Batch<UpAdjArgs>& b, cudaStream_t s) {
-    launch_pdl(k_up_adj_b, b.total_ctas, kUpThreads, kUpSmemFloats * sizeof(float), s, b);
+    launch_pdl(k_up_adj_b, b.total_ctas, kUpAdjThreads, kUpSmemFloats * sizeof(float), s, b);
 }
 
 }  // namespace cc

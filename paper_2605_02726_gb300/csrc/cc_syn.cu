@@ -367,14 +367,16 @@ __device__ __forceinline__ void syn_bwd_body(const SynArgs& a, int cta, int ncta
     }
 }
 
+// 8 resident CTAs per SM (at most 64 registers): the forward is latency-bound, and the extra
+// warps pay for the few spilled registers.
 template <int PASS>
-__global__ void __launch_bounds__(kSynThreads) k_syn_fwd(SynArgs a) {
+__global__ void __launch_bounds__(kSynThreads, 8) k_syn_fwd(SynArgs a) {
     __shared__ SynArgs sa;
     param_fetch(a, sa);
     syn_fwd_body<PASS>(sa, blockIdx.x, gridDim.x);
 }
 template <int PASS>
-__global__ void __launch_bounds__(kSynThreads) k_syn_fwd_b(Batch<SynArgs> b) {
+__global__ void __launch_bounds__(kSynThreads, 8) k_syn_fwd_b(Batch<SynArgs> b) {
     __shared__ SynArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);

@@ -13,13 +13,13 @@ namespace {
 // Separable 4x4 polyphase taps with replicate (clamped) indices, cropped to the grid size.
 // ---------------------------------------------------------------------------------------------
 
+// (32-bit indices: a stage has at most 5 channels of half the image, < 2^31 elements)
 __device__ __forceinline__ void up_fwd_body(const UpFwdArgs& a, int cta, int ncta) {
-    const int64_t total = (int64_t)a.nch * a.ht * a.wt;
+    const int plane = a.ht * a.wt, total = a.nch * plane;
     const float tp[4] = {__ldg(a.taps), __ldg(a.taps + 1), __ldg(a.taps + 2), __ldg(a.taps + 3)};
-    for (int64_t e = cta * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)ncta * blockDim.x) {
-        const int j = (int)(e / ((int64_t)a.ht * a.wt));
-        const int rem = (int)(e - (int64_t)j * a.ht * a.wt);
-        const int y = rem / a.wt, x = rem - y * a.wt;
+    for (int e = cta * (int)blockDim.x + (int)threadIdx.x; e < total; e += ncta * (int)blockDim.x) {
+        const int row = e / a.wt, x = e - row * a.wt;  // row of the stacked channels
+        const int j = row / a.ht, y = row - j * a.ht;
         const float* S = j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws;
         const int fy = poly_first(y), fx = poly_first(x);
         float wy[4], wx[4];
@@ -28,10 +28,10 @@ __device__ __forceinline__ void up_fwd_body(const UpFwdArgs& a, int cta, int nct
         float acc = 0.f;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-            const float* row = S + clampi(fy + p, 0, a.hs - 1) * a.ws;
+            const float* srow = S + clampi(fy + p, 0, a.hs - 1) * a.ws;
             float rs = 0.f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) rs = fmaf(wx[q], __ldg(row + clampi(fx + q, 0, a.ws - 1)), rs);
+            for (int q = 0; q < 4; ++q) rs = fmaf(wx[q], __ldg(srow + clampi(fx + q, 0, a.ws - 1)), rs);
             acc = fmaf(wy[p], rs, acc);
         }
         a.dst[e] = acc;

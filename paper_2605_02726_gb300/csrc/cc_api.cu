@@ -131,7 +131,6 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     size_t o_dt = L.take(3 * W.HW * F);
     size_t o_dz = L.take(6 * W.HW * F);
     size_t o_zd = L.take(6 * W.HW * F);
-    size_t o_tmp = L.take(F);
     size_t o_ga = L.take((size_t)W.n_cta_arm * po::arm_block * F);
     size_t o_gs = L.take((size_t)W.n_cta_syn * po::syn_block * F);
     size_t o_gc = L.take((size_t)W.n_cta_conv * po::conv_block * F);
@@ -160,7 +159,6 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
         W.dt = (float*)(base + o_dt);
         W.dz = (float*)(base + o_dz);
         W.zden = (float*)(base + o_zd);
-        W.tmp = (float*)(base + o_tmp);
         W.gpart_arm = (float*)(base + o_ga);
         W.gpart_syn = (float*)(base + o_gs);
         W.gpart_conv = (float*)(base + o_gc);

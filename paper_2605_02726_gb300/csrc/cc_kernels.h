@@ -89,7 +89,6 @@ struct Work {
     float* dz;         // adjoint of the dense latents of grids 1..6 at full resolution [6][HW]
     float* zden;       // dense latents of grids 1..6 at full resolution [6][HW], written by the
                        // synthesis forward for its adjoint (null: not kept)
-    float* tmp;        // upsampling-adjoint intermediate (largest stage)
     float* act_arm;    // stored ARM activations [34][N] (optional)
     float* act_syn;    // stored synthesis pre-activations [40][HW] (optional)
     float* gpart_arm;  // per-CTA partial gradients [n_cta_arm][756]

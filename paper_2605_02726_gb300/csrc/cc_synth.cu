@@ -1,6 +1,8 @@
-// Upsampling cascade of the encoder step (Sec. III-B, Eq. 7), stages 6..2 forward, and the
-// adjoint of every stage with the tap gradients (per-CTA partials, reduced in a fixed order).
-// Stage 1 forward is fused into the synthesis kernels (cc_syn.cu).
+// Upsampling cascade of the encoder step (Sec. III-B, Eq. 7): the forward stages as per-stage
+// kernels (stages 3 and 2 in the encoder iteration, whose entropy-model launch computes stages
+// 6..4; every stage when decoding), and the adjoint of every stage with the tap gradients
+// (per-CTA partials, reduced in a fixed order).  Stage 1 forward is fused into the synthesis
+// kernels (cc_syn.cu).
 #include "cc_kernels.h"
 #include "cc_upfwd.cuh"
 

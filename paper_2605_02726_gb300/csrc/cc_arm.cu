@@ -96,28 +96,40 @@ __device__ __forceinline__ float neighbour(const Geom& g, const float* yt, const
     return (rr >= 0 && cc >= 0 && cc < w) ? __ldg(yt + g.off[p.k] + rr * w + cc) : 0.f;
 }
 
-__device__ __forceinline__ void ifce_inputs(const Geom& g, const float* yt, const LatentPos& p, float (&rv)[6]) {
+// IFCE inputs j = t and j = t + 4 of a latent (lane t of its quad; zero where j >= nin): the
+// nearest-neighbour co-located values of grids k+1+j.
+__device__ __forceinline__ void ifce_inputs(const Geom& g, const float* yt, const LatentPos& p, int t, float& r0,
+                                            float& r1) {
     const int nin = ifce_nin(p.k);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        rv[j] = 0.f;
-        if (j < nin) {
-            const int gj = p.k + 1 + j;
-            const int rr = min(p.r >> (j + 1), g.h[gj] - 1), cc = min(p.c >> (j + 1), g.w[gj] - 1);
-            rv[j] = __ldg(yt + g.off[gj] + rr * g.w[gj] + cc);
-        }
-    }
+    auto at = [&](int j) {
+        const int gj = p.k + 1 + j;
+        const int rr = min(p.r >> (j + 1), g.h[gj] - 1), cc = min(p.c >> (j + 1), g.w[gj] - 1);
+        return __ldg(yt + g.off[gj] + rr * g.w[gj] + cc);
+    };
+    r0 = t < nin ? at(t) : 0.f;
+    r1 = t + 4 < nin ? at(t + 4) : 0.f;
 }
 
-__device__ __forceinline__ float ifce_out(const float* sIf, int k, int o, const float (&rv)[6]) {
+// IFCE output t of a latent in lane t of its quad: each lane forms the products of its two inputs
+// with all four output rows, and a transposing butterfly over the quad (lanes t ^ 2, then t ^ 1)
+// leaves the sum of output t in lane t.  All 32 lanes take part in the shuffles.
+__device__ __forceinline__ float ifce_out(const float* sIf, int k, int t, float r0, float r1) {
     const int nin = ifce_nin(k);
-    if (nin == 0) return 0.f;
-    const int wo = ifce_w_off(k) - po::if_w0, bo = ifce_b_off(k) - po::if_w0;
-    float acc = sIf[bo + o];
+    const int wo = ifce_w_off(k < kNIfce ? k : 0) - po::if_w0, bo = ifce_b_off(k < kNIfce ? k : 0) - po::if_w0;
+    float part[kF];
 #pragma unroll
-    for (int j = 0; j < 6; ++j)
-        if (j < nin) acc = fmaf(sIf[wo + o * nin + j], rv[j], acc);
-    return acc;
+    for (int o = 0; o < kF; ++o) {
+        const float w0 = t < nin ? sIf[wo + o * nin + t] : 0.f;
+        const float w1 = t + 4 < nin ? sIf[wo + o * nin + t + 4] : 0.f;
+        part[o] = fmaf(w1, r1, w0 * r0);
+    }
+    const bool b1 = t & 2, b0 = t & 1;
+    float keep0 = b1 ? part[2] : part[0], keep1 = b1 ? part[3] : part[1];
+    keep0 += __shfl_xor_sync(0xffffffffu, b1 ? part[0] : part[2], 2);
+    keep1 += __shfl_xor_sync(0xffffffffu, b1 ? part[1] : part[3], 2);
+    float keep = b0 ? keep1 : keep0;
+    keep += __shfl_xor_sync(0xffffffffu, b0 ? keep0 : keep1, 1);
+    return nin > 0 ? keep + sIf[bo + t] : 0.f;
 }
 
 // Parameter index of weight-gradient tile T, row, column (-1: padding).
@@ -255,9 +267,9 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         const LatentPos pA = locate(g, rcp_w, (int64_t)u * 16 + gq, N);
         const LatentPos pB = locate(g, rcp_w, (int64_t)u * 16 + gq + 8, N);
         // ---- context features f in {t, t+4, 8+t, 12+t, 16+t, 20+t} of latents A (row g) and B (row g+8)
-        float rA[6], rB[6];
-        ifce_inputs(g, a.yt, pA, rA);
-        ifce_inputs(g, a.yt, pB, rB);
+        float rA0, rA1, rB0, rB1;  // IFCE inputs tq and tq + 4 of latents A and B
+        ifce_inputs(g, a.yt, pA, tq, rA0, rA1);
+        ifce_inputs(g, a.yt, pB, tq, rB0, rB1);
         float cA[6], cB[6];
         int ndy[4], ndx[4];
 #pragma unroll
@@ -269,13 +281,13 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         cA[1] = neighbour(g, a.yt, pA, ndy[1], ndx[1]);
         cA[2] = neighbour(g, a.yt, pA, ndy[2], ndx[2]);
         cA[3] = neighbour(g, a.yt, pA, ndy[3], ndx[3]);
-        cA[4] = ifce_out(sIf, pA.k, tq, rA);
+        cA[4] = ifce_out(sIf, pA.k, tq, rA0, rA1);
         cA[5] = tq == 0 ? 1.f : 0.f;
         cB[0] = neighbour(g, a.yt, pB, ndy[0], ndx[0]);
         cB[1] = neighbour(g, a.yt, pB, ndy[1], ndx[1]);
         cB[2] = neighbour(g, a.yt, pB, ndy[2], ndx[2]);
         cB[3] = neighbour(g, a.yt, pB, ndy[3], ndx[3]);
-        cB[4] = ifce_out(sIf, pB.k, tq, rB);
+        cB[4] = ifce_out(sIf, pB.k, tq, rB0, rB1);
         cB[5] = cA[5];
         const AFrag C0 = make_a(cA[0], cB[0], cA[1], cB[1]);
         const AFrag C1 = make_a(cA[2], cB[2], cA[3], cB[3]);
@@ -527,11 +539,11 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 st[(U_O + row) * kSld + gq + 8] = vB * mB;
             }
             // R rows t and t+4 (rows 6, 7 are the preset one and zero)
-            st[(V_R + tq) * kSld + gq] = sel(rA, tq);
-            st[(V_R + tq) * kSld + gq + 8] = sel(rB, tq);
+            st[(V_R + tq) * kSld + gq] = rA0;
+            st[(V_R + tq) * kSld + gq + 8] = rB0;
             if (tq < 2) {
-                st[(V_R + tq + 4) * kSld + gq] = tq == 0 ? rA[4] : rA[5];
-                st[(V_R + tq + 4) * kSld + gq + 8] = tq == 0 ? rB[4] : rB[5];
+                st[(V_R + tq + 4) * kSld + gq] = rA1;
+                st[(V_R + tq + 4) * kSld + gq + 8] = rB1;
             }
         }
         __syncwarp();

@@ -70,7 +70,7 @@ typedef struct {
  * H*W); Adam (Sec. IV-B) uses lr, beta1, beta2, eps for latents and parameters alike.
  * noise_mode selects the training proxy of the latents at step t:
  *   CC_NOISE_UNIFORM:   y~ = y + u, u ~ U[-1/2, 1/2) from a counter hash of (seed, t, i); lr fixed.
- *   CC_NOISE_SOFTROUND: the paper's proxy and schedule (Sec. IV-C/D, Eq. 12-13, Table I): for
+ *   CC_NOISE_SOFTROUND: the paper's proxy and schedule (Sec. IV-C/D, Eq. 13-14, Table I): for
  *     t < n_main, y~ = s_T(s_T(y) + sigma n) with n ~ N(0, 1) (Box-Muller on the same hash),
  *     sigma and T linear from (sigma0, temp0) to (sigma1, temp1) over the n_main steps and the
  *     learning rate cosine from lr to lr_min; for t >= n_main (hard-round stage) y~ = rint(y),

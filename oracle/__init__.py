@@ -140,7 +140,7 @@ def gauss(seed: int, t: int, n: int) -> np.ndarray:
 
 
 def softround(x: float, T: float):
-    """(s_T(x), s_T'(x)), Eq. 13."""
+    """(s_T(x), s_T'(x)), Eq. 14."""
     d = ctypes.c_double()
     v = _load().orc_softround(float(x), float(T), ctypes.byref(d))
     return v, d.value
@@ -176,7 +176,7 @@ def conv3x3_res(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
 def forward(image, latents, params, *, lam, mode=MODE_NOISE, seed=0, step=0, sigma=0.0, temp=1.0,
             per_latent=False):
     """Returns dict(loss, rate_bits, mse[, mu, logb, bits, xhat]); sigma and temp are used by
-    MODE_SOFTROUND (Eq. 12)."""
+    MODE_SOFTROUND (Eq. 13)."""
     image, latents, params = _f64(image), _f64(latents), _f64(params)
     _, H, W = image.shape
     N = latent_count(H, W)

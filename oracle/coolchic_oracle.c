@@ -11,7 +11,7 @@
  *   - latent grids  y^(k), k = 0..L-1, shape ceil(H/2^k) x ceil(W/2^k)      [Sec. III-A1, Eq. 1]
  *   - noise relaxation  y~ = y + u, u ~ U(-1/2, 1/2) from a counter hash    [Sec. IV-C; the workload's
  *     additive uniform proxy]
- *   - the paper's proxy  y~ = s_T(s_T(y) + sigma n), n ~ N(0, 1) by Box-Muller  [Sec. IV-C, Eq. 12-13]
+ *   - the paper's proxy  y~ = s_T(s_T(y) + sigma n), n ~ N(0, 1) by Box-Muller  [Sec. IV-C, Eq. 13-14]
  *     from the same counter hash, with the linear sigma / T and cosine learning-rate schedules of
  *     the main stage and the hard-round stage with frozen latents            [Sec. IV-D, Table I]
  *   - causal spatial context s_i and inter-feature context f_i = IFCE_k(r_i)  [Sec. III-A1/A2, Eqs. 4-5]
@@ -143,7 +143,7 @@ double orc_gauss(uint64_t seed, int64_t t, int64_t i) {
     return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
 }
 
-/* Soft rounding, Eq. 13 (after Agustsson and Theis):
+/* Soft rounding, Eq. 14 (after Agustsson and Theis):
  *   s_T(x) = floor(x) + 1/2 + tanh(D / T) / (2 tanh(1 / (2T))),  D = x - floor(x) - 1/2,
  * and its derivative (1 - tanh^2(D / T)) / (2 T tanh(1 / (2T))). */
 double orc_softround(double x, double T, double* deriv) {
@@ -438,7 +438,7 @@ static void synth_pixel(const double* P, const double* z, double* a, double* t) 
  * ---------------------------------------------------------------------------------------- */
 enum { MODE_NOISE = 0, MODE_HARD = 1, MODE_IDENTITY = 2, MODE_SOFTROUND = 3 };
 
-/* How the latents are relaxed: MODE_SOFTROUND uses sigma and temp (Eq. 12). */
+/* How the latents are relaxed: MODE_SOFTROUND uses sigma and temp (Eq. 13). */
 typedef struct {
     int mode;
     uint64_t seed;
@@ -580,7 +580,7 @@ double orc_forward(int H, int W, const double* img, const double* y, const doubl
 
 /* Loss and its gradient with respect to the continuous latents y and the parameters:
  * dL/dy = dL/dy~ * dy~/dy (1 for the additive proxy, 0 under hard rounding, the product of the
- * two soft-rounding derivatives for Eq. 12). */
+ * two soft-rounding derivatives for Eq. 13). */
 double orc_loss_grad(int H, int W, const double* img, const double* y, const double* P, int mode,
                      uint64_t seed, int64_t t, double sigma, double temp, double lambda, double* rate_out,
                      double* mse_out, double* gy, double* gP) {

@@ -99,7 +99,7 @@ __device__ __forceinline__ float counter_gauss(uint64_t seed, int64_t step, int6
     const float u2 = (float)(uint32_t)((z >> 16) & 0xFFFFFFull) * (1.f / 16777216.f);
     return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
 }
-// Soft rounding, Eq. 13 (after Agustsson and Theis): s_T(x) = floor(x) + 1/2 + tanh(D / T) /
+// Soft rounding, Eq. 14 (after Agustsson and Theis): s_T(x) = floor(x) + 1/2 + tanh(D / T) /
 // (2 tanh(1 / (2T))), D = x - floor(x) - 1/2; d = s_T'(x) = (1 - tanh^2(D / T)) / (2 T tanh(1 / (2T))).
 __device__ __forceinline__ float softround(float x, float T, float& d) {
     const float fl = floorf(x), D = x - fl - 0.5f, th = tanhf(D / T), den = 2.f * tanhf(0.5f / T);

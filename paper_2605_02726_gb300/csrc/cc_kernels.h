@@ -44,7 +44,7 @@ __device__ __forceinline__ ProxyAt proxy_at(const Hp& hp, int64_t t) {
     return p;
 }
 // y~ of latent i at step t under the training proxy, and dy~/dy: the additive uniform proxy
-// (mode 0), Eq. 12 (mode 1, main stage), rint (mode 1, hard-round stage)
+// (mode 0), Eq. 13 (mode 1, main stage), rint (mode 1, hard-round stage)
 __device__ __forceinline__ float relax_latent(const Hp& hp, const ProxyAt& p, float y, int64_t t, int64_t i,
                                               float& jac) {
     if (hp.noise_mode == 0) {

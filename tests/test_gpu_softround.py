@@ -1,4 +1,4 @@
-"""GPU parity of the paper's training proxy and schedule (Sec. IV-C/D, Eq. 12-13, Table I) against
+"""GPU parity of the paper's training proxy and schedule (Sec. IV-C/D, Eq. 13-14, Table I) against
 the FP64 oracle: y~ = s_T(s_T(y) + sigma n) in the main stage with sigma, T linear and the learning
 rate cosine over n_main steps; rounding with frozen latents in the hard-round stage.
 

@@ -1,4 +1,4 @@
-"""Pins of the oracle's soft-round proxy (Eq. 12-13) and encoder schedule (Sec. IV-C/D, Table I).
+"""Pins of the oracle's soft-round proxy (Eq. 13-14) and encoder schedule (Sec. IV-C/D, Table I).
 
 Checked against properties the paper and the mathematics fix, not against the oracle itself:
 soft rounding is exact at the integers, continuous and continuously differentiable across them,
@@ -82,7 +82,7 @@ def test_gauss_moments():
 
 
 def test_softround_proxy_reduces_to_rounding():
-    """sigma = 0 and a tiny temperature: the proxy is hard rounding (Eq. 12 -> Eq. 11 input)."""
+    """sigma = 0 and a tiny temperature: the proxy (Eq. 13) is the hard rounding of Eq. 12."""
     H, W = 12, 10
     img = inputs.image(H, W, seed=4)
     lat, par = inputs.random_state(H, W, seed=5, latent_sigma=1.3)

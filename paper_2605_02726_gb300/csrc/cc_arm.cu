@@ -21,6 +21,9 @@
 // accumulating in registers for the whole kernel.  The thin ones (b2, W3, Ws, b3 = bs: one or two
 // gradient rows) are per-lane FMAs on values the lane already holds.  The 4 warps' accumulators
 // are added in a fixed order at the end: one partial gradient per CTA.
+//
+// The first CTA also computes the coarse forward upsampling stages 6..4 (it needs none of the
+// entropy model's results, and the other CTAs take the latents), so that they cost no launch.
 #include "cc_kernels.h"
 #include "cc_mma.cuh"
 #include "cc_upfwd.cuh"

@@ -8,7 +8,7 @@ namespace cc {
 namespace {
 
 // ---------------------------------------------------------------------------------------------
-// a1: y~ = y + u(seed, step, i) | rint(y) | y
+// a1: y~ = y + u(seed, step, i) | s_T(s_T(y) + sigma n) (Eq. 13, in its schedule) | rint(y) | y
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void relax_body(const RelaxArgs& a, int cta, int ncta) {
     __shared__ ProxyAt s_px;  // the proxy at this step, once per CTA

@@ -130,17 +130,26 @@ __device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int nct
         const int r0 = 2 * py0 - 3, c0 = 2 * px0 - 3;
         const float* Dj = a.D + (int64_t)j * a.ht * a.wt;
         const float* S = j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * a.hs * a.ws;
+        // the tiles by asynchronous global -> shared copies (all of a thread's copies in flight at
+        // once); cells outside the grid are stored as zeros
         const int nd = (2 * ty + 6) * kUpDC;
         for (int e = threadIdx.x; e < nd; e += blockDim.x) {
             const int r = e / kUpDC, c = e - r * kUpDC;
             const int gr = r0 + r, gc = c0 + c;
-            sD[e] = (gr >= 0 && gr < a.ht && gc >= 0 && gc < a.wt) ? __ldg(Dj + (int64_t)gr * a.wt + gc) : 0.f;
+            if (gr >= 0 && gr < a.ht && gc >= 0 && gc < a.wt)
+                cp_async4(sD + e, Dj + (int64_t)gr * a.wt + gc);
+            else
+                sD[e] = 0.f;
         }
         for (int e = threadIdx.x; e < ty * kUpSC; e += blockDim.x) {
             const int r = e / kUpSC, c = e - r * kUpSC;
             const int py = py0 + r;
-            sS[e] = py < a.hs ? __ldg(S + (int64_t)py * a.ws + clampi(px0 - 2 + c, 0, a.ws - 1)) : 0.f;
+            if (py < a.hs)
+                cp_async4(sS + e, S + (int64_t)py * a.ws + clampi(px0 - 2 + c, 0, a.ws - 1));
+            else
+                sS[e] = 0.f;
         }
+        cp_async_wait_all();
         __syncthreads();
         // pass A: T over output columns c0 .. c0+kUpDC-1 of the tile's input rows
         switch (ty) {
@@ -176,12 +185,12 @@ __device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int nct
     if (threadIdx.x == 0)
         for (int q = 0; q < 4; ++q) a.gpart[cta * 4 + q] = dh[q];
 }
-__global__ void __launch_bounds__(kUpAdjThreads) k_up_adj(UpAdjArgs a) {
+__global__ void __launch_bounds__(kUpAdjThreads, 4) k_up_adj(UpAdjArgs a) {
     __shared__ UpAdjArgs sa;
     param_fetch(a, sa);
     up_adj_body(sa, blockIdx.x, gridDim.x);
 }
-__global__ void __launch_bounds__(kUpAdjThreads) k_up_adj_b(Batch<UpAdjArgs> b) {
+__global__ void __launch_bounds__(kUpAdjThreads, 4) k_up_adj_b(Batch<UpAdjArgs> b) {
     __shared__ UpAdjArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);

@@ -170,40 +170,42 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     __shared__ float rcp_w[kL];
     if (tid == 0) g = a.g;
     if (tid < kL) rcp_w[tid] = 1.f / (float)a.g.w[tid];
+    // the entropy-model and IFCE parameters staged in one round trip, through the staging area
+    // (free until the coarse stages and the first unit)
+    const float* P = stage_params(a.params, 0, po::arm_block, sStage);
     for (int j = tid; j < FR_N * 32; j += kT) {
         const int f = j >> 5, l = j & 31;
-        const float v0 = bfrag_value(a.params, f, l >> 2, l & 3, 0);
-        const float v1 = bfrag_value(a.params, f, l >> 2, l & 3, 1);
+        const float v0 = bfrag_value(P, f, l >> 2, l & 3, 0);
+        const float v1 = bfrag_value(P, f, l >> 2, l & 3, 1);
         uint32_t h0, l0, h1, l1;
         split2(v0, h0, l0);
         split2(v1, h1, l1);
         sFr[j] = make_float4(__uint_as_float(h0), __uint_as_float(h1), __uint_as_float(l0), __uint_as_float(l1));
     }
-    for (int j = tid; j < kIfceSm; j += kT) sIf[j] = a.params[po::if_w0 + j];
-    __syncthreads();
+    for (int j = tid; j < kIfceSm; j += kT) sIf[j] = P[po::if_w0 + j];
 
     // per-lane constants of the SIMT parts, read as float2 (units / features 2t, 2t+1 of a tile)
     __shared__ __align__(16) float sC[16 + 2 * 16 + 2 * 24];  // b2 [16], W3 [2][16], Ws [2][24] (zero-padded)
     for (int j = tid; j < 96; j += kT) {
         float v;
-        if (j < 16) v = a.params[po::arm_b2 + j];
-        else if (j < 48) v = a.params[po::arm_w3 + (j - 16)];
+        if (j < 16) v = P[po::arm_b2 + j];
+        else if (j < 48) v = P[po::arm_w3 + (j - 16)];
         else {
             const int o = (j - 48) / 24, f = (j - 48) % 24;
-            v = f < 20 ? a.params[po::arm_ws + o * 20 + f] : 0.f;
+            v = f < 20 ? P[po::arm_ws + o * 20 + f] : 0.f;
         }
         sC[j] = v;
     }
     const float2* b2c = reinterpret_cast<const float2*>(sC) + tq;          // [nt * 4]
     const float2* w3c = reinterpret_cast<const float2*>(sC + 16) + tq;     // [o * 8 + nt * 4]
     const float2* wsc = reinterpret_cast<const float2*>(sC + 48) + tq;     // [o * 12 + nt * 4]
-    __syncthreads();
+    const float mu_b = P[po::arm_b3] + P[po::arm_bs];
+    const float s_b = P[po::arm_b3 + 1] + P[po::arm_bs + 1];
+    __syncthreads();  // (the staged parameters are dead from here: the staging area is reused)
     // context slots t, t+4, t+8, t+12 of this lane, packed 5 bits each: dy + 3 (2 bits), dx + 3 (3 bits)
     int nd = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) nd |= ((ctx_dy(tq + 4 * q) + 3) | ((ctx_dx(tq + 4 * q) + 3) << 2)) << (5 * q);
-    const float mu_b = a.params[po::arm_b3] + a.params[po::arm_bs];
-    const float s_b = a.params[po::arm_b3 + 1] + a.params[po::arm_bs + 1];
 
     // CTA 0 computes the coarse forward upsampling stages (it takes no latents when there are
     // other CTAs), staged through the weight-gradient staging area before its constant rows are

@@ -164,6 +164,16 @@ __device__ __forceinline__ void batch_fetch(const A* __restrict__ args, int j, A
 // Copies a single-job launch's arguments into shared memory, so that the kernel body runs on
 // arguments in the same memory space as in a multi-job launch (one compiled body, bitwise equal
 // results whether an image runs alone or in a batch).
+// Copies params[lo, lo + n) to shared memory `sm` by asynchronous copies (every thread's copies
+// in flight at once: one round trip for the CTA instead of one per loop pass), then a barrier.
+// The result indexes the copy with absolute parameter offsets (valid for [lo, lo + n) only).
+__device__ __forceinline__ const float* stage_params(const float* P, int lo, int n, float* sm) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) cp_async4(sm + j, P + lo + j);
+    cp_async_wait_all();
+    __syncthreads();
+    return sm - lo;
+}
+
 template <typename A>
 __device__ __forceinline__ void param_fetch(const A& a, A& sa) {
     static_assert(sizeof(A) % 4 == 0, "argument structs are copied as 32-bit words");

@@ -129,7 +129,8 @@ __device__ __forceinline__ void load_syn_weights(const float* P, float* sW) {
 template <int PASS>
 __device__ __forceinline__ void syn_fwd_body(const SynArgs& a, int cta, int ncta) {
     __shared__ __align__(16) float sW[ss_total];
-    load_syn_weights(a.params, sW);
+    __shared__ float sRaw[po::syn_block];  // the synthesis parameters, staged in one round trip
+    load_syn_weights(stage_params(a.params, po::syn_w1, po::syn_block, sRaw), sW);
     const float tp[4] = {a.params[po::up], a.params[po::up + 1], a.params[po::up + 2], a.params[po::up + 3]};
     __syncthreads();
     const float rcpW = 1.f / (float)a.g.W;
@@ -201,24 +202,26 @@ __device__ __forceinline__ void syn_bwd_body(const SynArgs& a, int cta, int ncta
     extern __shared__ float4 smem4[];
     float4* sFr = smem4;
     float* sStage = reinterpret_cast<float*>(smem4 + FR_N * 32);
-    build_frags(a.params, sFr);
+    // the synthesis parameters staged in one round trip (through the staging area, free until the
+    // first unit), then the fragment table and W2 / Ws for the SIMT parts, read as float2 per lane
+    const float* P = stage_params(a.params, po::syn_w1, po::syn_block, sStage);
+    build_frags(P, sFr);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, gq = lane >> 2, tq = lane & 3;
-    float* st = sStage + wid * kStage;
-    for (int j = lane; j < kSld; j += 32)
-        for (int r = U_DT + 3; r < V_Z; ++r) st[r * kSld + j] = 0.f;
-    __syncthreads();
-    // W2 [3][40] and Ws [3][8] (column 7 zero) for the SIMT parts, read as float2 per lane
-    __shared__ __align__(16) float sW2[kC * kSH + kC * 8];
+    __shared__ __align__(16) float sW2[kC * kSH + kC * 8];  // W2 [3][40], Ws [3][8] (column 7 zero)
     for (int j = tid; j < kC * kSH + kC * 8; j += blockDim.x) {
         float v;
         if (j < kC * kSH) {
-            v = a.params[po::syn_w2 + j];
+            v = P[po::syn_w2 + j];
         } else {
             const int c = (j - kC * kSH) >> 3, ch = (j - kC * kSH) & 7;
-            v = ch < 7 ? a.params[po::syn_ws + c * 7 + ch] : 0.f;
+            v = ch < 7 ? P[po::syn_ws + c * 7 + ch] : 0.f;
         }
         sW2[j] = v;
     }
+    __syncthreads();
+    float* st = sStage + wid * kStage;
+    for (int j = lane; j < kSld; j += 32)
+        for (int r = U_DT + 3; r < V_Z; ++r) st[r * kSld + j] = 0.f;
     __syncthreads();
     float acc[8][4];
 #pragma unroll

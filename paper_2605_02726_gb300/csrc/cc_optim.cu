@@ -248,8 +248,10 @@ __global__ void __launch_bounds__(256, 4) k_gather_b(Batch<GatherArgs> b) {
 // ---------------------------------------------------------------------------------------------
 // Fixed-order sum of the per-CTA partial parameter gradients, then Adam or a scaled copy.
 // A CTA owns 32 consecutive parameters (one per lane); its 32 warps take interleaved rows of the
-// partials (coalesced across lanes, four independent loads in flight per step) and their sums
-// are added in warp order.  A job has kReduceCtas CTAs.
+// partials (coalesced across lanes, all of a warp's rows in flight at once when they number at
+// most 16, the usual case) and their sums are added in warp order.  The Adam operands (step,
+// moments, parameter) are loaded before the partials, so their round trip overlaps.  A job has
+// kReduceCtas CTAs.
 // ---------------------------------------------------------------------------------------------
 constexpr int kReduceCtas = (po::total + 31) / 32;
 constexpr int kReduceThreads = 1024, kReduceWarps = kReduceThreads / 32;
@@ -258,7 +260,16 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
     __shared__ float red[kReduceWarps][33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int p = cta * 32 + lane;
-    float a0 = 0.f, a1 = 0.f;
+    const bool adam = !a.grad_out && wid == 0 && p < po::total;
+    int64_t step = 0;
+    float m0 = 0.f, v0 = 0.f, p0 = 0.f;
+    if (adam) {
+        step = *a.step_dev;
+        m0 = a.m[p];
+        v0 = a.v[p];
+        p0 = a.params[p];
+    }
+    float acc = 0.f;
     if (p < po::total) {
         const float* base;
         int64_t stride;
@@ -281,19 +292,20 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
             stride = po::conv_block;
             cnt = a.n_conv;
         }
-        // rows wid, wid + 32, ...
-        constexpr int RW = kReduceWarps;
-        int q = wid;
-        for (; q + 3 * RW < cnt; q += 4 * RW) {
-            float v[4];
+        // rows wid, wid + 32, ..., 16 per pass, added as a fixed pairwise tree
+        constexpr int RW = kReduceWarps, kU = 16;
+        for (int q = wid; q < cnt; q += kU * RW) {
+            float v[kU];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = __ldg(base + (int64_t)(q + RW * u) * stride);
-            a0 += v[0] + v[1];
-            a1 += v[2] + v[3];
+            for (int u = 0; u < kU; ++u) v[u] = q + RW * u < cnt ? __ldg(base + (int64_t)(q + RW * u) * stride) : 0.f;
+#pragma unroll
+            for (int w = kU / 2; w > 0; w >>= 1)
+#pragma unroll
+                for (int u = 0; u < w; ++u) v[u] += v[u + w];
+            acc += v[0];
         }
-        for (; q < cnt; q += RW) a0 += __ldg(base + (int64_t)q * stride);
     }
-    red[wid][lane] = a0 + a1;
+    red[wid][lane] = acc;
     __syncthreads();
     if (wid != 0 || p >= po::total) return;
     float gsum = 0.f;
@@ -304,14 +316,13 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
         return;
     }
     float bc1, bc2;
-    const int64_t step = *a.step_dev;
     adam_bias_corrections(step + 1, a.hp.beta1, a.hp.beta2, bc1, bc2);
     const float lr = proxy_at(a.hp, step).lr;
-    const float mi = a.hp.beta1 * a.m[p] + (1.f - a.hp.beta1) * gsum;
-    const float vi = a.hp.beta2 * a.v[p] + (1.f - a.hp.beta2) * gsum * gsum;
+    const float mi = a.hp.beta1 * m0 + (1.f - a.hp.beta1) * gsum;
+    const float vi = a.hp.beta2 * v0 + (1.f - a.hp.beta2) * gsum * gsum;
     a.m[p] = mi;
     a.v[p] = vi;
-    a.params[p] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
+    a.params[p] = p0 - lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
 }
 __global__ void __launch_bounds__(kReduceThreads) k_param_reduce(ReduceArgs a) {
     __shared__ ReduceArgs sa;
@@ -331,6 +342,11 @@ __global__ void __launch_bounds__(kReduceThreads) k_param_reduce_b(Batch<ReduceA
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void finish_body(const FinishArgs& a) {
     __shared__ double sr[256], ss[256];
+    int64_t step = 0, base = 0;  // loaded up front: their round trip overlaps the partials'
+    if (threadIdx.x == 0 && a.step_dev) {
+        step = *a.step_dev;
+        if (a.base_step) base = *a.base_step;
+    }
     double r = 0.0, e = 0.0;
     for (int q = threadIdx.x; q < a.n_rate; q += blockDim.x) r += a.rate_part[q];
     for (int q = threadIdx.x; q < a.n_se; q += blockDim.x) e += a.se_part[q];
@@ -349,14 +365,14 @@ __device__ __forceinline__ void finish_body(const FinishArgs& a) {
         const double loss = mse + a.lambda * rate * a.inv_hw;
         if (a.rd) {
             int64_t slot = 0;
-            if (a.step_dev && a.base_step) slot = *a.step_dev - *a.base_step;
+            if (a.step_dev && a.base_step) slot = step - base;
             double* o = a.rd + slot * a.rd_stride;
             o[0] = loss;
             o[1] = rate;
             o[2] = mse;
         }
-        if (a.mark_base && a.step_dev && a.base_step) *a.base_step = *a.step_dev;
-        if (a.increment && a.step_dev) *a.step_dev += 1;
+        if (a.mark_base && a.step_dev && a.base_step) *a.base_step = step;
+        if (a.increment && a.step_dev) *a.step_dev = step + 1;
     }
 }
 __global__ void k_finish(FinishArgs a) {

@@ -675,7 +675,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(kT, 3) k_arm(ArmArgs a) {
+__global__ void __launch_bounds__(kT, 3) k_arm(const __grid_constant__ ArmArgs a) {
     __shared__ ArmArgs sa;
     param_fetch(a, sa);
     arm_body<PASS>(sa, blockIdx.x, gridDim.x);

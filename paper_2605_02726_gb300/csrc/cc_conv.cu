@@ -371,10 +371,9 @@ __device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) 
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs a) {
-    __shared__ ConvArgs sa;
-    param_fetch(a, sa);
-    conv_body<PASS>(sa, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kThreads, 2) k_conv(const __grid_constant__ ConvArgs a) {
+    pdl_enter();
+    conv_body<PASS>(a, blockIdx.x, gridDim.x);
 }
 template <int PASS>
 __global__ void __launch_bounds__(kThreads, 2) k_conv_b(Batch<ConvArgs> b) {

@@ -161,9 +161,29 @@ __device__ __forceinline__ void batch_fetch(const A* __restrict__ args, int j, A
     pdl_wait();
 }
 
-// Copies a single-job launch's arguments into shared memory, so that the kernel body runs on
-// arguments in the same memory space as in a multi-job launch (one compiled body, bitwise equal
-// results whether an image runs alone or in a batch).
+// Arguments of a single-job launch.  The kernel parameter is declared __grid_constant__ (taking
+// its address makes no copy).  Kernels whose bodies read it at compile-time offsets only use it
+// where it is, in the parameter space (pdl_enter); kernels that index it with a runtime grid number
+// (the grid tables) first copy it to shared memory (param_fetch: the first warp copies, the CTA
+// synchronises).  A copy in every thread of every CTA, as the predicated per-word form needs, cost
+// more than the arguments' use.
+__device__ __forceinline__ void pdl_enter() {
+    pdl_trigger();
+    pdl_wait();
+}
+template <typename A>
+__device__ __forceinline__ void param_fetch(const A& a, A& sa) {  // a: the __grid_constant__ parameter
+    static_assert(sizeof(A) % 4 == 0, "argument structs are copied as 32-bit words");
+    pdl_trigger();
+    if (threadIdx.x < 32) {
+        const int* src = reinterpret_cast<const int*>(&a);
+        int* dst = reinterpret_cast<int*>(&sa);
+        for (int w = threadIdx.x; w < (int)(sizeof(A) / 4); w += 32) dst[w] = src[w];
+    }
+    __syncthreads();
+    pdl_wait();
+}
+
 // Copies params[lo, lo + n) to shared memory `sm` by asynchronous copies (every thread's copies
 // in flight at once: one round trip for the CTA instead of one per loop pass), then a barrier.
 // The result indexes the copy with absolute parameter offsets (valid for [lo, lo + n) only).
@@ -172,21 +192,6 @@ __device__ __forceinline__ const float* stage_params(const float* P, int lo, int
     cp_async_wait_all();
     __syncthreads();
     return sm - lo;
-}
-
-template <typename A>
-__device__ __forceinline__ void param_fetch(const A& a, A& sa) {
-    static_assert(sizeof(A) % 4 == 0, "argument structs are copied as 32-bit words");
-    constexpr int NW = (int)(sizeof(A) / 4);
-    const int* src = reinterpret_cast<const int*>(&a);
-    int* dst = reinterpret_cast<int*>(&sa);
-    pdl_trigger();
-    // word w goes through lane w % 32 of the first warp; constant indices keep `a` in param space
-#pragma unroll
-    for (int w = 0; w < NW; ++w)
-        if ((int)threadIdx.x == (w & 31)) dst[w] = src[w];
-    __syncthreads();
-    pdl_wait();
 }
 
 // Argument structs of the kernels (filled by the launchers and by the batch planner).

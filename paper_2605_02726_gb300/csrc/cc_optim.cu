@@ -26,10 +26,9 @@ __device__ __forceinline__ void relax_body(const RelaxArgs& a, int cta, int ncta
                                          : (a.relax == kRelaxHard ? rintf(v) : v);
     }
 }
-__global__ void k_relax(RelaxArgs a) {
-    __shared__ RelaxArgs sa;
-    param_fetch(a, sa);
-    relax_body(sa, blockIdx.x, gridDim.x);
+__global__ void k_relax(const __grid_constant__ RelaxArgs a) {
+    pdl_enter();
+    relax_body(a, blockIdx.x, gridDim.x);
 }
 __global__ void k_relax_b(Batch<RelaxArgs> b) {
     __shared__ RelaxArgs sa;
@@ -96,10 +95,9 @@ __device__ __forceinline__ void ifce_body(const IfceArgs& a, int cta, int ncta) 
         if (live && p == 0) a.Q[task] = acc;
     }
 }
-__global__ void k_ifce_cells(IfceArgs a) {
-    __shared__ IfceArgs sa;
-    param_fetch(a, sa);
-    ifce_body(sa, blockIdx.x, gridDim.x);
+__global__ void k_ifce_cells(const __grid_constant__ IfceArgs a) {
+    pdl_enter();
+    ifce_body(a, blockIdx.x, gridDim.x);
 }
 __global__ void k_ifce_cells_b(Batch<IfceArgs> b) {
     __shared__ IfceArgs sa;
@@ -233,7 +231,7 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
         }
     }
 }
-__global__ void __launch_bounds__(256, 4) k_gather(GatherArgs a) {
+__global__ void __launch_bounds__(256, 4) k_gather(const __grid_constant__ GatherArgs a) {
     __shared__ GatherArgs sa;
     param_fetch(a, sa);
     gather_body(sa, blockIdx.x, gridDim.x);
@@ -324,7 +322,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
     a.v[p] = vi;
     a.params[p] = p0 - lr * (mi / bc1) / (sqrtf(vi / bc2) + a.hp.eps);
 }
-__global__ void __launch_bounds__(kReduceThreads) k_param_reduce(ReduceArgs a) {
+__global__ void __launch_bounds__(kReduceThreads) k_param_reduce(const __grid_constant__ ReduceArgs a) {
     __shared__ ReduceArgs sa;
     param_fetch(a, sa);
     reduce_body(sa, blockIdx.x);
@@ -375,10 +373,9 @@ __device__ __forceinline__ void finish_body(const FinishArgs& a) {
         if (a.increment && a.step_dev) *a.step_dev = step + 1;
     }
 }
-__global__ void k_finish(FinishArgs a) {
-    __shared__ FinishArgs sa;
-    param_fetch(a, sa);
-    finish_body(sa);
+__global__ void k_finish(const __grid_constant__ FinishArgs a) {
+    pdl_enter();
+    finish_body(a);
 }
 __global__ void k_finish_b(Batch<FinishArgs> b) {
     __shared__ FinishArgs sa;

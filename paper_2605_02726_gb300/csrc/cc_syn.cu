@@ -373,10 +373,9 @@ __device__ __forceinline__ void syn_bwd_body(const SynArgs& a, int cta, int ncta
 // 8 resident CTAs per SM (at most 64 registers): the forward is latency-bound, and the extra
 // warps pay for the few spilled registers.
 template <int PASS>
-__global__ void __launch_bounds__(kSynThreads, 8) k_syn_fwd(SynArgs a) {
-    __shared__ SynArgs sa;
-    param_fetch(a, sa);
-    syn_fwd_body<PASS>(sa, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kSynThreads, 8) k_syn_fwd(const __grid_constant__ SynArgs a) {
+    pdl_enter();
+    syn_fwd_body<PASS>(a, blockIdx.x, gridDim.x);
 }
 template <int PASS>
 __global__ void __launch_bounds__(kSynThreads, 8) k_syn_fwd_b(Batch<SynArgs> b) {
@@ -386,10 +385,9 @@ __global__ void __launch_bounds__(kSynThreads, 8) k_syn_fwd_b(Batch<SynArgs> b) 
     syn_fwd_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
 }
 template <int PASS>
-__global__ void __launch_bounds__(kSynThreads, 3) k_syn_bwd(SynArgs a) {
-    __shared__ SynArgs sa;
-    param_fetch(a, sa);
-    syn_bwd_body<PASS>(sa, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kSynThreads, 3) k_syn_bwd(const __grid_constant__ SynArgs a) {
+    pdl_enter();
+    syn_bwd_body<PASS>(a, blockIdx.x, gridDim.x);
 }
 template <int PASS>
 __global__ void __launch_bounds__(kSynThreads, 3) k_syn_bwd_b(Batch<SynArgs> b) {

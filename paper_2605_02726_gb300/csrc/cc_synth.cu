@@ -9,10 +9,9 @@
 namespace cc {
 namespace {
 
-__global__ void k_up_fwd(UpFwdArgs a) {
-    __shared__ UpFwdArgs sa;
-    param_fetch(a, sa);
-    up_fwd_body(sa, blockIdx.x, gridDim.x);
+__global__ void k_up_fwd(const __grid_constant__ UpFwdArgs a) {
+    pdl_enter();
+    up_fwd_body(a, blockIdx.x, gridDim.x);
 }
 __global__ void k_up_fwd_b(Batch<UpFwdArgs> b) {
     __shared__ UpFwdArgs sa;
@@ -185,10 +184,9 @@ __device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int nct
     if (threadIdx.x == 0)
         for (int q = 0; q < 4; ++q) a.gpart[cta * 4 + q] = dh[q];
 }
-__global__ void __launch_bounds__(kUpAdjThreads, 4) k_up_adj(UpAdjArgs a) {
-    __shared__ UpAdjArgs sa;
-    param_fetch(a, sa);
-    up_adj_body(sa, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kUpAdjThreads, 4) k_up_adj(const __grid_constant__ UpAdjArgs a) {
+    pdl_enter();
+    up_adj_body(a, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(kUpAdjThreads, 4) k_up_adj_b(Batch<UpAdjArgs> b) {
     __shared__ UpAdjArgs sa;

@@ -117,10 +117,23 @@ struct Batch {
     int total_ctas;
 };
 
+// The job whose CTA range [cb[j], cb[j+1]) holds this CTA: the number of job starts cb[1..nj-1] at
+// or below blockIdx.x (cb is increasing), counted by the first warp 32 starts per round trip.
+// Reads only the static table, so it may run before the dependent-launch wait.
 __device__ __forceinline__ int batch_job(const int* __restrict__ cb, int nj) {
-    int j = 0;
-    while (j + 1 < nj && (int)blockIdx.x >= __ldg(cb + j + 1)) ++j;
-    return j;
+    __shared__ int s_job;
+    if (threadIdx.x < 32) {
+        int j = 0;
+        for (int base = 1; base < nj; base += 32) {
+            const int q = base + (int)threadIdx.x;
+            const unsigned past = __ballot_sync(0xffffffffu, q < nj && (int)blockIdx.x >= __ldg(cb + q));
+            j += __popc(past);
+            if (past != 0xffffffffu) break;
+        }
+        if (threadIdx.x == 0) s_job = j;
+    }
+    __syncthreads();
+    return s_job;
 }
 
 // Programmatic dependent launch: the kernels of an iteration are launched with programmatic stream

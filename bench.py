@@ -211,7 +211,10 @@ def main():
 
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    cc.timing_enable(cc.KERNEL_ARM, K)
+    # the entropy-model kernel is timed by event pairs around its launch in the first tenth of the
+    # timed steps (those steps launch eagerly; the rest replay the library's CUDA graph of the call)
+    K_arm = max(3, K // 10)
+    cc.timing_enable(cc.KERNEL_ARM, K_arm)
     with ClockSampler(local) as clk:
         barrier()
         t_wall = time.perf_counter()
@@ -283,7 +286,8 @@ def main():
             "config": {"workload": WORKLOAD, "image": [H, W], "latents": cc.latent_count(H, W),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "flushed between timed iterations (256 MB write outside the events)",
-                       "launch": f"eager, {launches_per_step} kernels per iteration"},
+                       "launch": f"{launches_per_step} kernels per iteration, replayed from the library's CUDA "
+                                 f"graph of the call (the first {K_arm} timed steps eager, the entropy model timed)"},
             "e2e": {"value": world * H * W / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
                     "h2d_bytes_per_step": int(host_img.numel() * 4), "d2h_bytes_per_step": 24,
                     "ms_per_step": e2e_ms, "loss_readback": loss_now},

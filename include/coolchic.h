@@ -134,7 +134,11 @@ int64_t coolchic_kernel_launches(const cc_arch_t* arch, int32_t n_iters);
  *   rd_per_iter [device, nullable] n_iters records: loss, rate, mse measured before each update.
  *   workspace  [device] coolchic_workspace_bytes(arch, 0) bytes, 256-byte aligned; contents are
  *              scratch between calls.
- * Asynchronous on `stream`; may be captured in a CUDA graph. */
+ * Asynchronous on `stream`; may be captured in a CUDA graph.  A call of at most 4 iterations is
+ * captured into a CUDA graph of the library's own on its first occurrence with given arguments
+ * (all values and pointers), which later identical calls replay (at most 16 kept; not while
+ * kernel timing records or the caller's stream is capturing; environment COOLCHIC_GRAPHS=0 turns
+ * this off); longer calls launch eagerly.  n_iters = 0 launches nothing. */
 int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
                          const cc_state_t* state, int32_t n_iters, cc_rd_t* rd_per_iter,
                          void* workspace, size_t workspace_bytes, void* stream);

@@ -136,6 +136,24 @@ def oracle_rate(h, w, iters, seed):
     return h * w * iters / dt / 1e6, dt
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Every rank's x reduced by max (the job ends with its slowest rank); x as is for one rank.
+    device: where the process group's backend takes tensors (cuda for nccl, cpu for gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Whole-job throughput in millions of units per second: the units of all ranks over the
+    slowest rank's time (every rank runs the same work)."""
+    return world * units_per_rank / (ms * 1e-3) / 1e6
+
+
 def run_reference(args, rank):
     """The FP64 oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
@@ -227,13 +245,9 @@ def main():
         t_wall = time.perf_counter() - t_wall
     arm_ms, arm_n = cc.timing_collect()
     cc.timing_disable()
-    tot_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
     ms_per_step = tot_ms / K
-    value = world * H * W * K / (tot_ms * 1e-3) / 1e6
+    value = job_rate(world, H * W * K, tot_ms)
 
     # end to end: pinned host image -> device, iteration, loss record -> pinned host, every step
     host_img = torch.tensor(img_np).pin_memory()
@@ -251,11 +265,7 @@ def main():
         host_rd.copy_(rd_dev[0], non_blocking=True)
         eve[i][1].record(stream)
     barrier()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in eve) / Ke
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_ms = float(te.item())
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in eve) / Ke, world, dev)
     loss_now = float(host_rd[0])
 
     clocks = clk.summary()
@@ -288,7 +298,7 @@ def main():
                        "l2": "flushed between timed iterations (256 MB write outside the events)",
                        "launch": f"{launches_per_step} kernels per iteration, replayed from the library's CUDA "
                                  f"graph of the call (the first {K_arm} timed steps eager, the entropy model timed)"},
-            "e2e": {"value": world * H * W / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+            "e2e": {"value": job_rate(world, H * W, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(host_img.numel() * 4), "d2h_bytes_per_step": 24,
                     "ms_per_step": e2e_ms, "loss_readback": loss_now},
             "gpu_launches": launches_per_step * K,

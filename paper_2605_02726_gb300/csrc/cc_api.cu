@@ -1,4 +1,5 @@
-// C ABI of the library (include/coolchic.h): argument checks, workspace layout, launch order.
+// C ABI of the library (include/coolchic.h): argument checks, workspace layout, launch order, and
+// the CUDA graphs that short encode_step calls replay.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

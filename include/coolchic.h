@@ -116,6 +116,19 @@ int64_t coolchic_param_count(const cc_arch_t* arch);
  * length in floats.  Returns CC_ERR_ARG past the last block. */
 int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int32_t* length);
 
+/* Seeded initial encoder state, written on the device (the paper does not give its
+ * initialisation; this is the library's reading, the distribution of the host generator of the
+ * tests drawn from the counter hash of the relaxation noise instead):
+ *   latents y_i = 0.01 n_i, n_i the Box-Muller standard normal of the hash at (seed, step -1, i);
+ *   hidden-layer weights (ARM W1 and W2, the three IFCE matrices, synthesis W1)
+ *   w_p = 2 u_p / sqrt(fan_in), u_p in [-1/2, 1/2) the uniform of the hash at (seed, step -2, p),
+ *   p the flat parameter index;  upsampling taps the Keys cubic (a = -0.75) samples at every
+ *   stage;  every other parameter, both Adam moments and *state->step zero.
+ *   state [host struct of device pointers], every buffer written (sizes as in
+ *   coolchic_latent_count / coolchic_param_count).
+ * Asynchronous on `stream`.  CC_ERR_ARG for a bad arch or a NULL pointer. */
+int coolchic_init_state(const cc_arch_t* arch, uint64_t seed, const cc_state_t* state, void* stream);
+
 /* Bytes of device workspace one job needs.  `flags` bit 0: room for stored forward activations
  * (coolchic_forward with store_activations = 1).  Returns 0 on a bad arch. */
 size_t coolchic_workspace_bytes(const cc_arch_t* arch, int32_t flags);

@@ -451,6 +451,25 @@ int64_t coolchic_param_count(const cc_arch_t* a) {
     return po::total;
 }
 
+int coolchic_init_state(const cc_arch_t* arch, uint64_t seed, const cc_state_t* st, void* stream) {
+    if (int rc = check_arch(arch)) return rc;
+    if (!st || !st->latents || !st->params || !st->m_lat || !st->v_lat || !st->m_par || !st->v_par || !st->step)
+        return fail(CC_ERR_ARG, "init_state: NULL state pointer");
+    if (int rc = device_setup()) return rc;
+    InitArgs a;
+    a.y = st->latents;
+    a.params = st->params;
+    a.m_lat = st->m_lat;
+    a.v_lat = st->v_lat;
+    a.m_par = st->m_par;
+    a.v_par = st->v_par;
+    a.step = st->step;
+    a.N = make_geom(arch->H, arch->W).off[kL];
+    a.seed = seed;
+    launch_init_state(a, (cudaStream_t)stream);
+    return launched("init_state");
+}
+
 int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int32_t* length) {
     static const struct {
         const char* n;

@@ -370,6 +370,14 @@ void launch_param_reduce(const Work& w, float* params, float* m, float* v, float
 void launch_finish(const Work& w, const Hp& hp, int have_arm, int have_conv, double* rd_out,
                    int64_t* step_dev, int mark_base, int increment, cudaStream_t s);
 void launch_mark_base(const Work& w, const int64_t* step_dev, cudaStream_t s);
+// the seeded initial state (coolchic_init_state)
+struct InitArgs {
+    float *y, *params, *m_lat, *v_lat, *m_par, *v_par;
+    int64_t* step;
+    int64_t N;
+    uint64_t seed;
+};
+void launch_init_state(const InitArgs& a, cudaStream_t s);
 
 // sizes that the workspace layout depends on
 size_t arm_smem_bytes(int pass);

@@ -384,6 +384,45 @@ __global__ void k_finish_b(Batch<FinishArgs> b) {
 }
 
 __global__ void k_mark_base(const int64_t* step_dev, int64_t* base_step) { *base_step = *step_dev; }
+
+// ---------------------------------------------------------------------------------------------
+// Seeded initial state (no counterpart in the paper, which does not give its initialisation):
+// latents 0.01 n_i, n_i the Box-Muller normal of the counter hash at (seed, step -1, i); hidden
+// weights (ARM W1, W2, the IFCE matrices, synthesis W1) 2 u_p / sqrt(fan_in), u_p the uniform of
+// the hash at (seed, step -2, p); bicubic taps; every other parameter, the moments and the step 0.
+// (Negative steps: the encoder's own draws use steps >= 0.)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float init_param(uint64_t seed, int p) {
+    int fan = 0;
+    if (p >= po::arm_w1 && p < po::arm_b1) fan = 20;
+    else if (p >= po::arm_w2 && p < po::arm_b2) fan = 16;
+    else if (p >= po::if_w0 && p < po::if_b0) fan = ifce_nin(0);
+    else if (p >= po::if_w1 && p < po::if_b1) fan = ifce_nin(1);
+    else if (p >= po::if_w2 && p < po::if_b2) fan = ifce_nin(2);
+    else if (p >= po::syn_w1 && p < po::syn_b1) fan = 7;
+    if (fan) return 2.f * counter_uniform(seed, -2, p) / sqrtf((float)fan);
+    if (p >= po::up && p < po::syn_w1) {  // Keys cubic (a = -0.75) at 1.75, 1.25, 0.75, 0.25
+        const int j = (p - po::up) & 3;
+        return j == 0 ? -0.03515625f : j == 1 ? -0.10546875f : j == 2 ? 0.26171875f : 0.87890625f;
+    }
+    return 0.f;
+}
+__global__ void k_init_state(const __grid_constant__ InitArgs a) {
+    const int64_t n_all = a.N + po::total;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_all; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < a.N) {
+            a.y[e] = 0.01f * counter_gauss(a.seed, -1, e);
+            a.m_lat[e] = 0.f;
+            a.v_lat[e] = 0.f;
+        } else {
+            const int p = (int)(e - a.N);
+            a.params[p] = init_param(a.seed, p);
+            a.m_par[p] = 0.f;
+            a.v_par[p] = 0.f;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.step = 0;
+}
 __global__ void k_mark_base_b(Batch<FinishArgs> b) {
     if (threadIdx.x == 0) *b.args[blockIdx.x].base_step = *b.args[blockIdx.x].step_dev;
 }
@@ -510,6 +549,10 @@ void launch_param_reduce(const Work& w, float* params, float* m, float* v, float
 void launch_finish(const Work& w, const Hp& hp, int have_arm, int have_conv, double* rd_out, int64_t* step_dev,
                    int mark_base, int increment, cudaStream_t s) {
     launch_pdl(k_finish, 1, 256, 0, s, finish_args(w, hp, have_arm, have_conv, rd_out, 3, step_dev, mark_base, increment));
+}
+
+void launch_init_state(const InitArgs& a, cudaStream_t s) {
+    k_init_state<<<grid_for(a.N + po::total, 256, 8), 256, 0, s>>>(a);
 }
 
 void launch_mark_base(const Work& w, const int64_t* step_dev, cudaStream_t s) {

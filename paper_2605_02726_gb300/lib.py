@@ -66,6 +66,7 @@ def _load():
         "coolchic_arch_init": (i32, [P(Arch), i32, i32]),
         "coolchic_latent_count": (i64, [P(Arch)]),
         "coolchic_param_count": (i64, [P(Arch)]),
+        "coolchic_init_state": (i32, [P(Arch), ctypes.c_uint64, P(State), vp]),
         "coolchic_param_block": (i32, [i32, P(ctypes.c_char_p), P(i32), P(i32)]),
         "coolchic_workspace_bytes": (sz, [P(Arch), i32]),
         "coolchic_kernel_launches": (i64, [P(Arch), i32]),
@@ -94,7 +95,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count", "coolchic_param_block",
+EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count", "coolchic_init_state",
+            "coolchic_param_block",
             "coolchic_workspace_bytes", "coolchic_kernel_launches", "coolchic_encode_step", "coolchic_forward", "coolchic_backward",
             "coolchic_rate_distortion", "coolchic_decode_image", "coolchic_timing_enable", "coolchic_timing_collect",
             "coolchic_timing_disable", "coolchic_last_error", "coolchic_version",
@@ -214,6 +216,18 @@ class EncoderState:
     def c_state(self) -> State:
         return State(self.latents.data_ptr(), self.params.data_ptr(), self.m_lat.data_ptr(), self.v_lat.data_ptr(),
                      self.m_par.data_ptr(), self.v_par.data_ptr(), self.step.data_ptr())
+
+    @staticmethod
+    def init(H: int, W: int, seed: int, device=None, stream=None) -> "EncoderState":
+        """A fresh state initialised on the device by coolchic_init_state (seeded: latents
+        0.01 N(0, 1), hidden weights U(+-1/sqrt(fan_in)), bicubic taps, the rest zero)."""
+        dev = torch.device(device or "cuda")
+        a = arch(H, W)
+        n_par = int(_lib.coolchic_param_count(ctypes.byref(a)))
+        st = EncoderState(torch.empty(latent_count(H, W), device=dev), torch.empty(n_par, device=dev))
+        cs = st.c_state()
+        _check(_lib.coolchic_init_state(ctypes.byref(a), int(seed), ctypes.byref(cs), _stream(stream)), "init_state")
+        return st
 
     def clone(self) -> "EncoderState":
         s = EncoderState.__new__(EncoderState)

@@ -42,8 +42,8 @@ ARM_MAC_PER_LATENT = 3 * 648
 IFCE_NIN = (6, 5, 4)
 # Peak of the FP32 pipe: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (maximum SM clock).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# DRAM bytes (read + write) per launch of the entropy-model kernel, from the ncu capture of the
-# current kernel in profiles/encode_step_kernels_512x768_full.md (cold caches: 2.16 MB read,
+# DRAM bytes (read + write) per launch of the entropy-model kernel, from the full ncu capture of
+# the current kernel at 512 x 768 (cold caches: 2.16 MB read,
 # 1.44 MB written; most of the context-gradient planes it writes stay in L2, and how much of them
 # is written back during the launch varies from capture to capture: 0.47-1.9 MB).
 ARM_TRAFFIC_BYTES = 3.60e6

@@ -56,3 +56,16 @@ def test_argument_checks_fail_cleanly(lib):
     assert b"architecture" in raw.coolchic_last_error()
     assert raw.coolchic_param_block(99, None, None, None) == -1
     assert raw.coolchic_version().startswith(b"coolchic")
+
+
+def test_launch_count_and_init_state_argument_checks(lib):
+    raw = lib.raw()
+    a = lib.arch(512, 768)
+    # relax once per call, then 16 kernels per iteration
+    assert [raw.coolchic_kernel_launches(ctypes.byref(a), n) for n in (0, 1, 3)] == [0, 17, 49]
+    assert raw.coolchic_kernel_launches(ctypes.byref(a), -1) == -1
+    # NULL state pointers and a bad architecture are refused before any device call
+    st = lib.State()
+    assert raw.coolchic_init_state(ctypes.byref(a), 1, ctypes.byref(st), None) == -1
+    assert b"NULL" in raw.coolchic_last_error()
+    assert raw.coolchic_init_state(None, 1, ctypes.byref(st), None) == -1

@@ -40,8 +40,9 @@ WORKLOAD = "512x768 RGB 1/f^2 + texture noise, L=7 Cool-chic decoder (ARM 16x2 +
 # matrices of grids 0..2 (3 x 4 x nin MAC), 2 FLOP per MAC.
 ARM_MAC_PER_LATENT = 3 * 648
 IFCE_NIN = (6, 5, 4)
-# Peak of the FP32 pipe: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (maximum SM clock).
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Unit-count figure of the FP32 pipe (152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz), reported beside
+# the peak measured in the same run (coolchic_measure_peak), which is the roofline denominator.
+FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch of the entropy-model kernel, from the full ncu capture of
 # the current kernel at 512 x 768 (cold caches: 2.16 MB read,
 # 1.44 MB written; most of the context-gradient planes it writes stay in L2, and how much of them
@@ -190,6 +191,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=10, help="oracle iterations of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--min-seconds", type=float, default=2.0,
+                    help="repeat the K timed steps (whole passes) until the timed region lasts this long")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -227,58 +230,86 @@ def main():
         cc.encode_step(image, st, 1, H=H, W=W, hp=hp, ws=ws)
     barrier()
 
+    # pipe ceilings of this GPU, measured now (FP32 FMA and TF32 mma.sync), before the timed region
+    fp32_peak, _ = cc.measure_peak(cc.PEAK_FP32_FMA)
+    tf32_peak, _ = cc.measure_peak(cc.PEAK_TF32_MMA)
+    for _ in range(3):
+        cc.encode_step(image, st, 1, H=H, W=W, hp=hp, ws=ws)
+    barrier()
+
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     # the entropy-model kernel is timed by event pairs around its launch in the first tenth of the
-    # timed steps (those steps launch eagerly; the rest replay the library's CUDA graph of the call)
+    # first pass's steps (those steps launch eagerly; the rest replay the library's CUDA graph of
+    # the call)
     K_arm = max(3, K // 10)
     cc.timing_enable(cc.KERNEL_ARM, K_arm)
-    with ClockSampler(local) as clk:
+
+    def timed_pass():
+        """Exactly K steps between a barrier + synchronize on both sides; their summed event time."""
         barrier()
-        t_wall = time.perf_counter()
         for i in range(K):
             flush.zero_()  # L2 flushed between timed iterations (outside the events)
             ev[i][0].record(stream)
             cc.encode_step(image, st, 1, H=H, W=W, hp=hp, ws=ws)
             ev[i][1].record(stream)
         barrier()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    # The K timed steps are repeated in whole passes until the timed region lasts --min-seconds,
+    # so that the clock sampler sees the GPU under load; every rank runs the same number of passes.
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        tot_ms = timed_pass()
+        first_s = time.perf_counter() - t_wall
+        passes = max(1, int(np.ceil(args.min_seconds / max(first_s, 1e-6))))
+        passes = int(max_over_ranks(passes, world, dev))
+        for _ in range(passes - 1):
+            tot_ms += timed_pass()
         t_wall = time.perf_counter() - t_wall
     arm_ms, arm_n = cc.timing_collect()
     cc.timing_disable()
-    tot_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
-    ms_per_step = tot_ms / K
-    value = job_rate(world, H * W * K, tot_ms)
+    tot_ms = max_over_ranks(tot_ms, world, dev)
+    ms_per_step = tot_ms / (K * passes)
+    value = job_rate(world, H * W * K * passes, tot_ms)
 
-    # end to end: pinned host image -> device, iteration, loss record -> pinned host, every step
+    # end to end through the host-buffer entry point (coolchic_encode_step_host): every step copies
+    # the image from pinned host memory into the workspace, runs the iteration and copies its loss
+    # record back to pinned host memory, all inside the events
     host_img = torch.tensor(img_np).pin_memory()
     host_rd = torch.zeros(3, dtype=torch.float64).pin_memory()
-    rd_dev = torch.zeros(1, 3, dtype=torch.float64, device=dev)
-    dev_img = torch.empty_like(image)
+    ws_io = cc.workspace(H, W, device=dev, host_io=True)
     Ke = min(K, 200)
     eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ke)]
+    for _ in range(3):
+        cc.encode_step_host(host_img, st, 1, H=H, W=W, hp=hp, ws=ws_io, rd_host=host_rd)
     barrier()
     for i in range(Ke):
         flush.zero_()
         eve[i][0].record(stream)
-        dev_img.copy_(host_img, non_blocking=True)
-        cc.encode_step(dev_img, st, 1, H=H, W=W, hp=hp, ws=ws, rd=rd_dev)
-        host_rd.copy_(rd_dev[0], non_blocking=True)
+        cc.encode_step_host(host_img, st, 1, H=H, W=W, hp=hp, ws=ws_io, rd_host=host_rd)
         eve[i][1].record(stream)
     barrier()
     e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in eve) / Ke, world, dev)
     loss_now = float(host_rd[0])
 
     clocks = clk.summary()
+    if clocks.get("sm_mhz"):
+        clocks["ms_per_step_x_sm_mhz"] = ms_per_step * clocks["sm_mhz"]
     arm_avg_s = arm_ms * 1e-3 / max(arm_n, 1)
     achieved = arm_flops(H, W) / arm_avg_s / 1e12
+    step_achieved = value * 1e6 * STEP_FLOP_PER_PIXEL / 1e12
     roofline = {"kernel": "k_arm (entropy model fwd+adjoint)", "bound": "alu", "achieved": achieved,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "traffic": ARM_TRAFFIC_BYTES, "launch_ms": arm_avg_s * 1e3,
                 "share_of_step": (arm_ms / max(arm_n, 1)) / ms_per_step,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 FLOP x 2070 MHz",
-                "step": {"flop_per_pixel": STEP_FLOP_PER_PIXEL,
-                         "achieved": value * 1e6 * STEP_FLOP_PER_PIXEL / 1e12,
-                         "frac": value * 1e6 * STEP_FLOP_PER_PIXEL / 1e12 / FP32_PEAK_TFLOPS}}
+                "peak_source": "measured in this run: FP32 FMA pipe (coolchic_measure_peak), "
+                               f"unit-count figure {FP32_UNIT_TFLOPS:.1f}",
+                "tensor_pipe": {"peak": tf32_peak, "peak_source": "measured in this run: mma.sync.m16n8k8 TF32",
+                                "frac_algorithmic": achieved / tf32_peak,
+                                "frac_executed_hi_lo": 3.0 * achieved / tf32_peak},
+                "step": {"flop_per_pixel": STEP_FLOP_PER_PIXEL, "achieved": step_achieved,
+                         "frac": step_achieved / fp32_peak}}
 
     if rank == 0:
         cpu = None
@@ -291,17 +322,21 @@ def main():
         launches_per_step = cc.kernel_launches(H, W, 1)  # one encode_step call of one iteration per step
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "passes": passes, "timed_steps": K * passes,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "image": [H, W], "latents": cc.latent_count(H, W),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "flushed between timed iterations (256 MB write outside the events)",
                        "launch": f"{launches_per_step} kernels per iteration, replayed from the library's CUDA "
-                                 f"graph of the call (the first {K_arm} timed steps eager, the entropy model timed)"},
+                                 f"graph of the call (the first {K_arm} timed steps eager, the entropy model timed)",
+                       "timing": f"{passes} passes of the {K} timed steps (each between barriers), "
+                                 f"repeated until the timed region lasted {args.min_seconds} s"},
             "e2e": {"value": job_rate(world, H * W, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(host_img.numel() * 4), "d2h_bytes_per_step": 24,
-                    "ms_per_step": e2e_ms, "loss_readback": loss_now},
-            "gpu_launches": launches_per_step * K,
+                    "ms_per_step": e2e_ms, "loss_readback": loss_now,
+                    "call": "coolchic_encode_step_host (host image in, host loss record out)"},
+            "gpu_launches": launches_per_step * K * passes,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clocks,

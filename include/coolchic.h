@@ -129,8 +129,13 @@ int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int3
  * Asynchronous on `stream`.  CC_ERR_ARG for a bad arch or a NULL pointer. */
 int coolchic_init_state(const cc_arch_t* arch, uint64_t seed, const cc_state_t* state, void* stream);
 
-/* Bytes of device workspace one job needs.  `flags` bit 0: room for stored forward activations
- * (coolchic_forward with store_activations = 1).  Returns 0 on a bad arch. */
+/* Bytes of device workspace one job needs.  `flags` bit 0 (CC_WS_STORE_ACTIVATIONS): room for
+ * stored forward activations (coolchic_forward with store_activations = 1).  Bit 1
+ * (CC_WS_HOST_IO): room for the device copy of the image and of one loss record that
+ * coolchic_encode_step_host uses.  A workspace sized with more flags serves every call that needs
+ * fewer.  Returns 0 on a bad arch. */
+#define CC_WS_STORE_ACTIVATIONS 1
+#define CC_WS_HOST_IO 2
 size_t coolchic_workspace_bytes(const cc_arch_t* arch, int32_t flags);
 
 /* Number of kernel launches a coolchic_encode_step call of n_iters iterations makes (no
@@ -155,6 +160,17 @@ int64_t coolchic_kernel_launches(const cc_arch_t* arch, int32_t n_iters);
 int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
                          const cc_state_t* state, int32_t n_iters, cc_rd_t* rd_per_iter,
                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* coolchic_encode_step for a caller whose image and result live in host memory (the call an
+ * application makes end to end): the image is copied from `image_host` [host, 3*H*W FP32; pinned
+ * memory makes the copy asynchronous] into the workspace, the n_iters >= 1 iterations run on
+ * it, and the record (loss, rate, mse) of the last iteration is copied to `rd_last_host` [host,
+ * nullable].  Both copies are ordered on `stream`: synchronise it before reading rd_last_host.
+ * The workspace must hold coolchic_workspace_bytes(arch, CC_WS_HOST_IO) bytes.  The iterations
+ * are those of coolchic_encode_step (Sec. IV-A..B), with its graph replay of short calls. */
+int coolchic_encode_step_host(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image_host,
+                              const cc_state_t* state, int32_t n_iters, cc_rd_t* rd_last_host,
+                              void* workspace, size_t workspace_bytes, void* stream);
 
 /* Batched encoder iterations (no counterpart in the paper, which encodes one image at a time):
  * n_jobs images of any sizes, each with its own hyper-parameters, state and workspace (sized by
@@ -259,6 +275,21 @@ int coolchic_decode_image(const cc_arch_t* arch, const int32_t* q, const float* 
 int coolchic_timing_enable(int32_t kernel_id, int32_t max_launches);
 int coolchic_timing_collect(double* total_ms, int64_t* launches);
 int coolchic_timing_disable(void);
+
+/* Throughput ceiling of one arithmetic pipe on the current device (no counterpart in the paper;
+ * the denominators of the benchmark's roofline fractions).  Blocking.  Runs a kernel that fills
+ * every SM with independent dependency chains of one instruction kind for at least 2 ms per
+ * launch, times 3 launches with CUDA events on `stream` and returns the best rate in TFLOP/s:
+ *   CC_PEAK_FP32_FMA  FP32 fused multiply-add (2 FLOP each) on the SIMT pipe;
+ *   CC_PEAK_TF32_MMA  warp-level tensor-core mma.sync.m16n8k8 with TF32 operands and FP32
+ *                     accumulation (2 x 16 x 8 x 8 FLOP each), the instruction the entropy
+ *                     model and the synthesis adjoint issue.
+ *   sink        [device] 4 writable bytes (never written in practice; keeps the work alive).
+ *   tflops_out  [host] the measured rate; ms_out [host, nullable] the duration of that launch.
+ * Returns CC_ERR_ARG for an unknown pipe or a NULL pointer, CC_ERR_CUDA if a launch fails. */
+#define CC_PEAK_FP32_FMA 0
+#define CC_PEAK_TF32_MMA 1
+int coolchic_measure_peak(int32_t which, float* sink, double* tflops_out, double* ms_out, void* stream);
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* coolchic_last_error(void);

@@ -141,10 +141,14 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     size_t o_sp = L.take((size_t)W.n_cta_conv * sizeof(double));
     size_t o_gp = L.take(po::total * F);
     size_t o_bs = L.take(4 * sizeof(int64_t));
-    size_t o_aa = 0, o_as = 0;
+    size_t o_aa = 0, o_as = 0, o_ioi = 0, o_ior = 0;
     if (flags & 1) {
         o_aa = L.take(34 * W.N * F);
         o_as = L.take(40 * W.HW * F);
+    }
+    if (flags & 2) {
+        o_ioi = L.take(3 * W.HW * F);
+        o_ior = L.take(3 * sizeof(double));
     }
     if (base && w) {
         W.yt = (float*)(base + o_yt);
@@ -172,6 +176,10 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
         if (flags & 1) {
             W.act_arm = (float*)(base + o_aa);
             W.act_syn = (float*)(base + o_as);
+        }
+        if (flags & 2) {
+            W.io_image = (float*)(base + o_ioi);
+            W.io_record = (double*)(base + o_ior);
         }
         *w = W;
     }
@@ -331,12 +339,14 @@ int encode_enqueue(const Work& w, const cc_hparams_t* hp, const float* image, co
 // capturing thousands of kernels once costs more than it saves; 100 iterations in one new call:
 // 314 against 280 µs per iteration).  Not used while kernel timing records launches, inside the
 // caller's own stream capture, or when COOLCHIC_GRAPHS=0.  At most kMaxGraphs graphs are kept
-// (least recently used evicted).
+// (least recently used evicted).  Each entry records an event after every launch of its graph;
+// eviction waits on that event only, so it stalls no other work on the device.
 constexpr size_t kMaxGraphs = 16;
 constexpr int32_t kGraphMaxIters = 4;
 struct GraphEntry {
     std::string key;
     cudaGraphExec_t exec;
+    cudaEvent_t done;  // recorded after each launch of exec
 };
 std::mutex g_graph_mu;
 std::vector<GraphEntry> g_graphs;  // most recently used last
@@ -377,14 +387,14 @@ bool timing_recording() {
 }
 
 // The graph of this call (captured on first use), or nullptr if capture is not possible here.
-cudaGraphExec_t encode_graph(int dev, const std::string& key, const Work& w, const cc_hparams_t* hp, const float* image,
+GraphEntry* encode_graph(int dev, const std::string& key, const Work& w, const cc_hparams_t* hp, const float* image,
                              const cc_state_t* st, int32_t n_iters, cc_rd_t* rd) {
     for (size_t i = 0; i < g_graphs.size(); ++i)
         if (g_graphs[i].key == key) {
             GraphEntry e = g_graphs[i];
             g_graphs.erase(g_graphs.begin() + (long)i);
             g_graphs.push_back(e);
-            return e.exec;
+            return &g_graphs.back();
         }
     if ((int)g_cap_streams.size() <= dev) g_cap_streams.resize(dev + 1, nullptr);
     if (!g_cap_streams[dev] && cudaStreamCreateWithFlags(&g_cap_streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
@@ -405,13 +415,21 @@ cudaGraphExec_t encode_graph(int dev, const std::string& key, const Work& w, con
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
     if (!ex) return nullptr;
+    cudaEvent_t done = nullptr;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(ex);
+        return nullptr;
+    }
     if (g_graphs.size() >= kMaxGraphs) {
-        cudaDeviceSynchronize();  // the evicted graph may still be running
-        cudaGraphExecDestroy(g_graphs.front().exec);
+        GraphEntry& old = g_graphs.front();
+        cudaEventSynchronize(old.done);  // its last launch may still be running
+        cudaGraphExecDestroy(old.exec);
+        cudaEventDestroy(old.done);
         g_graphs.erase(g_graphs.begin());
     }
-    g_graphs.push_back({key, ex});
-    return ex;
+    g_graphs.push_back({key, ex, done});
+    return &g_graphs.back();
 }
 
 }  // namespace
@@ -508,17 +526,15 @@ size_t coolchic_workspace_bytes(const cc_arch_t* a, int32_t flags) {
     return build_work(a, flags, nullptr, nullptr);
 }
 
-int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image, const cc_state_t* st,
-                         int32_t n_iters, cc_rd_t* rd_per_iter, void* ws, size_t ws_bytes, void* stream) {
-    Work w;
-    int rc = prepare(arch, 0, ws, ws_bytes, &w);
-    if (rc) return rc;
-    if ((rc = check_hp(hp))) return rc;
-    if (!image || !st || !st->latents || !st->params || !st->m_lat || !st->v_lat || !st->m_par || !st->v_par || !st->step)
-        return fail(CC_ERR_ARG, "NULL image or state pointer");
-    if (n_iters < 0) return fail(CC_ERR_ARG, "n_iters must be >= 0");
-    if (n_iters == 0) return CC_OK;
-    cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace cc {
+namespace {
+// The iterations of a checked encode_step call: replayed from the library's graph of the call
+// where that applies, launched eagerly otherwise.
+int encode_dispatch(const Work& w, const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
+                    const cc_state_t* st, int32_t n_iters, cc_rd_t* rd_per_iter, void* ws, size_t ws_bytes,
+                    cudaStream_t s) {
     // inside the caller's own stream capture the launches go into the caller's graph directly
     cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) {
@@ -530,13 +546,62 @@ int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const fl
         cudaGetDevice(&dev);
         const std::string key = encode_key(dev, arch, hp, image, st, n_iters, rd_per_iter, ws, ws_bytes);
         std::lock_guard<std::mutex> lk(g_graph_mu);
-        if (cudaGraphExec_t ex = encode_graph(dev, key, w, hp, image, st, n_iters, rd_per_iter)) {
-            const cudaError_t e = cudaGraphLaunch(ex, s);
+        if (GraphEntry* ge = encode_graph(dev, key, w, hp, image, st, n_iters, rd_per_iter)) {
+            cudaError_t e = cudaGraphLaunch(ge->exec, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ge->done, s);
             if (e != cudaSuccess) return fail(CC_ERR_CUDA, "encode_step: graph launch: %s", cudaGetErrorString(e));
             return CC_OK;
         }
     }
     return encode_enqueue(w, hp, image, st, n_iters, rd_per_iter, s);
+}
+
+int check_state(const cc_state_t* st) {
+    if (!st || !st->latents || !st->params || !st->m_lat || !st->v_lat || !st->m_par || !st->v_par || !st->step)
+        return fail(CC_ERR_ARG, "NULL state pointer");
+    return CC_OK;
+}
+}  // namespace
+}  // namespace cc
+
+extern "C" {
+
+int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image, const cc_state_t* st,
+                         int32_t n_iters, cc_rd_t* rd_per_iter, void* ws, size_t ws_bytes, void* stream) {
+    Work w;
+    int rc = prepare(arch, 0, ws, ws_bytes, &w);
+    if (rc) return rc;
+    if ((rc = check_hp(hp))) return rc;
+    if (!image) return fail(CC_ERR_ARG, "NULL image pointer");
+    if ((rc = check_state(st))) return rc;
+    if (n_iters < 0) return fail(CC_ERR_ARG, "n_iters must be >= 0");
+    if (n_iters == 0) return CC_OK;
+    return encode_dispatch(w, arch, hp, image, st, n_iters, rd_per_iter, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int coolchic_encode_step_host(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image_host,
+                              const cc_state_t* st, int32_t n_iters, cc_rd_t* rd_last_host, void* ws,
+                              size_t ws_bytes, void* stream) {
+    Work w;
+    int rc = prepare(arch, 2, ws, ws_bytes, &w);
+    if (rc) return rc;
+    if ((rc = check_hp(hp))) return rc;
+    if (!image_host) return fail(CC_ERR_ARG, "NULL host image pointer");
+    if ((rc = check_state(st))) return rc;
+    if (n_iters < 1) return fail(CC_ERR_ARG, "encode_step_host: n_iters must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(w.io_image, image_host, (size_t)3 * w.HW * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(CC_ERR_CUDA, "encode_step_host: image copy: %s", cudaGetErrorString(e));
+    if (n_iters > 1 && (rc = encode_dispatch(w, arch, hp, w.io_image, st, n_iters - 1, nullptr, ws, ws_bytes, s)))
+        return rc;
+    if ((rc = encode_dispatch(w, arch, hp, w.io_image, st, 1, rd_last_host ? (cc_rd_t*)w.io_record : nullptr, ws,
+                              ws_bytes, s)))
+        return rc;
+    if (rd_last_host) {
+        e = cudaMemcpyAsync(rd_last_host, w.io_record, sizeof(cc_rd_t), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return fail(CC_ERR_CUDA, "encode_step_host: record copy: %s", cudaGetErrorString(e));
+    }
+    return CC_OK;
 }
 
 int coolchic_forward(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image, const float* latents,

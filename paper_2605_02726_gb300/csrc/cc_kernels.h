@@ -99,6 +99,8 @@ struct Work {
     double* se_part;   // [n_cta_conv]
     float* grad_params;// [1415] reduced parameter gradient
     int64_t* base_step;// step at the start of an encode call
+    float* io_image;   // device copy of a host image [3][HW] (workspace flag bit 1, else null)
+    double* io_record; // one loss record (loss, rate, mse) read back to the host (flag bit 1)
     int n_cta_arm, n_cta_syn, n_cta_conv;
     int n_cta_up[kL];  // CTAs of the upsampling-adjoint kernel of stage s = 1..6
 };

@@ -38,8 +38,9 @@ size_t take(size_t& off, size_t bytes) {
     return o;
 }
 
-// Forward-only layout: y~, the upsampled grids, t, the per-CTA partials and one record.
-size_t layout(const cc_arch_t* a, char* base, Work* out) {
+// Forward-only layout: y~, the upsampled grids, t, the per-CTA partials and one record (three
+// doubles: loss, rate, distortion), whose address goes to *rd.
+size_t layout(const cc_arch_t* a, char* base, Work* out, double** rd) {
     Work w;
     std::memset(&w, 0, sizeof(w));
     w.g = make_geom(a->H, a->W);
@@ -63,8 +64,8 @@ size_t layout(const cc_arch_t* a, char* base, Work* out) {
         w.t = (float*)(base + o_t);
         w.rate_part = (double*)(base + o_rp);
         w.se_part = (double*)(base + o_sp);
-        w.grad_params = (float*)(base + o_rd);  // the record (3 doubles)
         *out = w;
+        *rd = (double*)(base + o_rd);
     }
     return off;
 }
@@ -91,12 +92,15 @@ extern "C" int coolchic_rate_distortion_noalloc(const cc_arch_t* arch, const cc_
         return set_error(CC_ERR_ARG, "rate_distortion_noalloc: NULL image, latents, params or rd_out");
     if (relax < 0 || relax > 2) return set_error(CC_ERR_ARG, "rate_distortion_noalloc: relax must be 0, 1 or 2");
     if (step < 0 || step > 0x7fffffffLL) return set_error(CC_ERR_ARG, "rate_distortion_noalloc: step outside 0..2^31-1");
-    const size_t need = layout(arch, nullptr, nullptr);
+    const size_t need = layout(arch, nullptr, nullptr, nullptr);
     if (need > kNoAllocBytes)
         return set_error(CC_ERR_WORKSPACE,
                          "rate_distortion_noalloc: a %d x %d image needs %zu bytes of scratch, the built-in limit is "
                          "%zu bytes (about 1.4 million pixels: 1024 x 1024 fits); use coolchic_rate_distortion with a workspace",
                          arch->H, arch->W, need, kNoAllocBytes);
+    // SM count and kernel attributes of this device, as every other entry point sets them up first
+    // (this allocates nothing)
+    if (const int rc = device_setup_checked()) return rc;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(CC_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
@@ -114,11 +118,11 @@ extern "C" int coolchic_rate_distortion_noalloc(const cc_arch_t* arch, const cc_
         base = g_na_ptr[dev];
     }
     Work w;
-    layout(arch, (char*)base, &w);
+    double* rd_dev = nullptr;
+    layout(arch, (char*)base, &w, &rd_dev);
     cudaStream_t s = (cudaStream_t)stream;
     Hp h;
     h = hp_from(hp);
-    double* rd_dev = (double*)w.grad_params;
     launch_relax(w, latents, nullptr, step, h, relax, s);
     launch_arm(w, params, PASS_FWD, 0.f, s);
     launch_up_forward(w, params, kUpArmLo - 1, s);

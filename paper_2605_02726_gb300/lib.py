@@ -71,6 +71,7 @@ def _load():
         "coolchic_workspace_bytes": (sz, [P(Arch), i32]),
         "coolchic_kernel_launches": (i64, [P(Arch), i32]),
         "coolchic_encode_step": (i32, [P(Arch), P(HParams), vp, P(State), i32, vp, vp, sz, vp]),
+        "coolchic_encode_step_host": (i32, [P(Arch), P(HParams), vp, P(State), i32, vp, vp, sz, vp]),
         "coolchic_forward": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, i32, vp, vp, vp, sz, vp]),
         "coolchic_backward": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, i32, f32, vp, vp, vp, sz, vp]),
         "coolchic_rate_distortion": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, P(RD), vp, sz, vp]),
@@ -84,6 +85,7 @@ def _load():
         "coolchic_timing_enable": (i32, [i32, i32]),
         "coolchic_timing_collect": (i32, [P(ctypes.c_double), P(i64)]),
         "coolchic_timing_disable": (i32, []),
+        "coolchic_measure_peak": (i32, [i32, vp, P(ctypes.c_double), P(ctypes.c_double), vp]),
         "coolchic_last_error": (ctypes.c_char_p, []),
         "coolchic_version": (ctypes.c_char_p, []),
     }
@@ -101,7 +103,8 @@ EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count
             "coolchic_rate_distortion", "coolchic_decode_image", "coolchic_timing_enable", "coolchic_timing_collect",
             "coolchic_timing_disable", "coolchic_last_error", "coolchic_version",
             "coolchic_rate_distortion_noalloc", "coolchic_batch_table_bytes", "coolchic_batch_create",
-            "coolchic_batch_step", "coolchic_batch_records", "coolchic_batch_destroy"]
+            "coolchic_batch_step", "coolchic_batch_records", "coolchic_batch_destroy", "coolchic_measure_peak",
+            "coolchic_encode_step_host"]
 
 KERNEL_ARM, KERNEL_SYN_BWD, KERNEL_CONV, KERNEL_SYN_FWD = 0, 1, 2, 3
 KERNEL_UP_FWD, KERNEL_UP_ADJ, KERNEL_GATHER = 4, 5, 6
@@ -121,6 +124,20 @@ def timing_disable():
     _lib.coolchic_timing_disable()
 
 
+PEAK_FP32_FMA, PEAK_TF32_MMA = 0, 1
+
+
+def measure_peak(which: int, stream=None):
+    """Measured throughput ceiling of one pipe on the current device: (TFLOP/s, ms of the timed
+    launch).  Blocking."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.coolchic_measure_peak(int(which), _ptr(sink), ctypes.byref(tf), ctypes.byref(ms), _stream(stream)),
+           "measure_peak")
+    return tf.value, ms.value
+
+
 def raw():
     """The ctypes library handle (for tests of the C ABI itself)."""
     return _lib
@@ -138,6 +155,14 @@ def _ptr(t):
         raise ValueError("expected a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t):
+    if t is None:
+        return None
+    if t.device.type != "cpu" or not t.is_contiguous():
+        raise ValueError("expected a contiguous host tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -190,9 +215,11 @@ def param_blocks():
     return out
 
 
-def workspace(H: int, W: int, store_activations: bool = False, device=None) -> torch.Tensor:
-    """Device workspace for one job (256-byte aligned byte tensor)."""
-    n = int(_lib.coolchic_workspace_bytes(ctypes.byref(arch(H, W)), 1 if store_activations else 0))
+def workspace(H: int, W: int, store_activations: bool = False, device=None, host_io: bool = False) -> torch.Tensor:
+    """Device workspace for one job (256-byte aligned byte tensor); host_io adds the room
+    encode_step_host needs."""
+    flags = (1 if store_activations else 0) | (2 if host_io else 0)
+    n = int(_lib.coolchic_workspace_bytes(ctypes.byref(arch(H, W)), flags))
     if n == 0:
         raise CoolChicError(_lib.coolchic_last_error().decode())
     buf = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
@@ -242,6 +269,18 @@ def encode_step(image, state: EncoderState, n_iters: int, *, H, W, hp: HParams, 
     cs = state.c_state()
     _check(_lib.coolchic_encode_step(ctypes.byref(a), ctypes.byref(hp), _ptr(image), ctypes.byref(cs), n_iters,
                                      _ptr(rd), _ptr(ws), ws.numel(), _stream(stream)), "encode_step")
+
+
+def encode_step_host(image_host, state: EncoderState, n_iters: int, *, H, W, hp: HParams, ws, rd_host=None,
+                     stream=None):
+    """encode_step on a host image (CPU tensor, pinned for an asynchronous copy); the last
+    iteration's (loss, rate, mse) lands in rd_host (CPU float64 [3], nullable) once the stream has
+    reached it.  ws must come from workspace(..., host_io=True)."""
+    a = arch(H, W)
+    cs = state.c_state()
+    _check(_lib.coolchic_encode_step_host(ctypes.byref(a), ctypes.byref(hp), _host_ptr(image_host), ctypes.byref(cs),
+                                          n_iters, _host_ptr(rd_host), _ptr(ws), ws.numel(), _stream(stream)),
+           "encode_step_host")
 
 
 def forward(image, latents, params, *, H, W, hp: HParams, step=0, relax=CC_RELAX_NOISE, ws, store=False,

@@ -82,3 +82,36 @@ def test_autotuner_returns_a_measured_candidate(cc):
     assert sched.as_tuple() == min(timings, key=timings.get)
     for (_, st, _), b in zip(jobs, before):  # tuning runs on clones
         assert torch.equal(st.latents, b)
+
+
+def test_batch_with_the_largest_workload_sizes(cc):
+    """A batch in the shape of the mixed-size workload: a 1536x1024 and a 1024x1024 job beside small
+    ones.  One iteration: each job bitwise equal to the single-image path, and the largest job's
+    loss record, forward and gradient against the FP64 oracle."""
+    import oracle
+    from tests.test_gpu_fullsize import _parity
+    sizes = [(1536, 1024), (1024, 1024), (64, 64), (37, 53)]
+    jobs = []
+    for j, (H, W) in enumerate(sizes):
+        img = torch.tensor(inputs.image(H, W, seed=700 + j, texture_sigma=0.02), device="cuda")
+        lat, par = inputs.random_state(H, W, seed=750 + j)
+        st = cc.EncoderState(torch.tensor(lat, device="cuda"), torch.tensor(par, device="cuda"), step=2)
+        jobs.append((img, st, cc.hparams(lam=1e-3, seed=77)))
+    ref = _single(cc, jobs, 1)
+    bjobs = [(img, st.clone(), hp) for img, st, hp in jobs]
+    be = cc.BatchEncoder(bjobs, rd_capacity=1)
+    be.step(1)
+    torch.cuda.synchronize()
+    rec = be.records().cpu().numpy()
+    for j, ((_, st, _), (rs, rrd)) in enumerate(zip(bjobs, ref)):
+        assert torch.equal(st.latents, rs.latents), j
+        assert torch.equal(st.params, rs.params), j
+        np.testing.assert_array_equal(rec[:, j, :], rrd.cpu().numpy())
+    be.close()
+    H, W = sizes[0]
+    img = inputs.image(H, W, seed=700, texture_sigma=0.02)
+    lat, par = inputs.random_state(H, W, seed=750)
+    o = oracle.forward(img, lat, par, lam=1e-3, mode=oracle.MODE_NOISE, seed=77, step=2)
+    assert abs(rec[0, 0, 0] - o["loss"]) <= 1e-4 * abs(o["loss"])
+    assert abs(rec[0, 0, 1] - o["rate_bits"]) <= 1e-4 * abs(o["rate_bits"])
+    _parity(cc, H, W, img, lat, par, step=2)

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2605_02726_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -29,6 +30,14 @@ def test_warmup_keeps_the_best_candidates(cc):
         alone[c] = (st, hp)
     first = sorted(range(3), key=lambda c: (encoder.rd_hard(img, alone[c][0], LAM)[0], c))
     assert [c for c, _ in rankings[0]] == first
+    # the ranking's costs are the FP64 oracle's rate-distortion cost with rounded latents (Eq. 10 at
+    # Eq. 12's quantised latents) of each candidate's trained state
+    img_np = img.cpu().numpy()
+    for c, loss in rankings[0]:
+        st = alone[c][0]
+        o = oracle.forward(img_np, st.latents.cpu().numpy(), st.params.cpu().numpy(), lam=LAM,
+                           mode=oracle.MODE_HARD)
+        assert abs(loss - o["loss"]) <= 1e-4 * abs(o["loss"]), (c, loss, o["loss"])
     for c in first[:2]:
         st, hp = alone[c]
         cc.encode_step(img, st, 12, H=H, W=W, hp=hp, ws=cc.workspace(H, W))

@@ -165,7 +165,7 @@ def test_rate_distortion_hard_matches_oracle(cc):
     assert _rel(r["loss"], o["loss"]) < 1e-4 and _rel(r["rate_bits"], o["rate_bits"]) < 1e-4
 
 
-@pytest.mark.parametrize("H,W", [(64, 64), (45, 77), (1, 1), (16, 5)])
+@pytest.mark.parametrize("H,W", [(64, 64), (45, 77), (1, 1), (16, 5), (512, 768)])
 def test_decode_bit_exact(cc, H, W):
     q = inputs.quantized_latents(H, W, seed=H + 3 * W)
     _, par = inputs.random_state(H, W, seed=H * W + 1)

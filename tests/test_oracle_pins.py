@@ -341,3 +341,92 @@ def test_decode_probabilities_are_valid():
     fl = oracle.forward(np.zeros((3, H, W)), q.astype(np.float64), par.astype(np.float64), lam=0.0,
                         mode=oracle.MODE_IDENTITY, per_latent=True)
     assert np.abs(d["mu_q"] / 256.0 - fl["mu"]).max() < 0.25
+
+
+def _q8(par):
+    """Parameters on the decoder's 2^-8 grid, as FP64 values."""
+    return np.rint(par.astype(np.float64) * 256.0) / 256.0
+
+
+def test_decode_fixed_point_arm_within_its_floor_bound():
+    """The integer ARM computes the FP64 ARM of the same integer latents and of the weights
+    rounded to the 2^-8 grid, except that each hidden or output layer floors its result to the
+    2^-8 grid.  A floor lowers a value by less than 2^-8, ReLU does not enlarge a difference, and
+    a layer scales the difference it receives by the l1 norm of its weight rows, so
+        e1 = 2^-8,  e2[o] = 2^-8 + sum_n |W2[o,n]| e1,  e_out[o] = 2^-8 + sum_n |W3[o,n]| e2[n]
+    bounds |mu_q / 256 - mu| and |logb_q / 256 - log b| (the clamp to [-5, 5] is 1-Lipschitz).  The
+    IFCE and the spatial context enter the integer ARM exactly (products of integers)."""
+    H, W = 24, 40
+    q = inputs.quantized_latents(H, W, seed=41)
+    _, par = inputs.random_state(H, W, seed=42)
+    d = oracle.decode_probs(H, W, q, par)
+    pq = _q8(par)
+    fl = oracle.forward(np.zeros((3, H, W)), q.astype(np.float64), pq, lam=0.0, mode=oracle.MODE_IDENTITY,
+                        per_latent=True)
+    W2 = torch_ref.P(torch.tensor(pq), "arm.w2").numpy()
+    W3 = torch_ref.P(torch.tensor(pq), "arm.w3").numpy()
+    u = 2.0 ** -8
+    e2 = u + np.abs(W2) @ np.full(16, u)
+    e_out = u + np.abs(W3) @ e2
+    assert np.abs(d["mu_q"] / 256.0 - fl["mu"]).max() <= e_out[0] + 1e-12
+    assert np.abs(d["logb_q"] / 256.0 - fl["logb"]).max() <= e_out[1] + 1e-12
+    # the bound is not vacuous: it is far below the size of the biases it would have to hide
+    assert e_out.max() < 0.05
+    # every latent of grids 0..2 went through its IFCE: the IFCE weights matter
+    assert np.any(np.abs(torch_ref.P(torch.tensor(pq), "ifce0.w").numpy()) > 0)
+
+
+def test_decode_probability_is_the_laplace_mass_of_its_integer_parameters():
+    """P_q16 = max(1, C(t+) - C(t-)) with C/65536 within 4 * 2^-16 of the Laplace CDF (pinned above), so
+    P_q16 is within 8 of 65536 times the exact mass of [y - 1/2, y + 1/2) under the Laplace law of
+    mean mu_q / 256 and scale exp(logb_q / 256) (Eq. 3); the floor at 1 stays inside that bound."""
+    H, W = 24, 40
+    q = inputs.quantized_latents(H, W, seed=43)
+    _, par = inputs.random_state(H, W, seed=44)
+    d = oracle.decode_probs(H, W, q, par)
+    mu = d["mu_q"].astype(np.float64) / 256.0
+    b = np.exp(d["logb_q"].astype(np.float64) / 256.0)
+
+    def cdf(z):
+        return 0.5 + 0.5 * np.sign(z) * (1.0 - np.exp(-np.abs(z) / b))
+
+    mass = cdf(q + 0.5 - mu) - cdf(q - 0.5 - mu)
+    assert np.abs(d["prob_q16"].astype(np.float64) - 65536.0 * mass).max() <= 8.0
+    # both tails and the centre are exercised
+    assert (mass < 1e-4).any() and (mass > 0.5).any()
+
+
+def test_encode_iteration_is_loss_grad_then_adam():
+    """One iteration of the uniform-proxy encoder from step t: the loss and gradient with the noise
+    keyed by t, then Adam with step count t + 1 on latents and parameters (Sec. IV-B), then the
+    next iteration keyed by t + 1."""
+    H, W = 8, 12
+    img = inputs.image(H, W, seed=12)
+    lat, par = inputs.random_state(H, W, seed=13)
+    lam, seed, t0 = 1e-2, 77, 3
+    st = oracle.State(lat, par, step=t0)
+    out = oracle.encode(img, st, 2, lam=lam, seed=seed)
+    assert st.step == t0 + 2
+
+    ref = oracle.State(lat, par, step=t0)
+    for it in range(2):
+        g = oracle.loss_grad(img, ref.latents, ref.params, lam=lam, mode=oracle.MODE_NOISE, seed=seed,
+                             step=t0 + it)
+        assert abs(g["loss"] - out["loss"][it]) <= 1e-15 * abs(g["loss"])
+        assert abs(g["rate_bits"] - out["rate_bits"][it]) <= 1e-15 * abs(g["rate_bits"])
+        oracle.adam(ref.latents, g["grad_latents"], ref.m_lat, ref.v_lat, t0 + it + 1, lr=1e-2)
+        oracle.adam(ref.params, g["grad_params"], ref.m_par, ref.v_par, t0 + it + 1, lr=1e-2)
+    np.testing.assert_allclose(st.latents, ref.latents, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(st.params, ref.params, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(st.m_lat, ref.m_lat, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(st.v_par, ref.v_par, rtol=0, atol=1e-15)
+    # a slip of the noise key would show: the neighbouring key gives another loss
+    other = oracle.forward(img, lat, par, lam=lam, mode=oracle.MODE_NOISE, seed=seed, step=t0 + 1)
+    assert abs(other["loss"] - out["loss"][0]) > 1e-9 * abs(out["loss"][0])
+    # a slip of the Adam count would show: bias correction at t0 + 2 instead of t0 + 1
+    slip = oracle.State(lat, par, step=t0)
+    g = oracle.loss_grad(img, slip.latents, slip.params, lam=lam, mode=oracle.MODE_NOISE, seed=seed, step=t0)
+    one = oracle.State(lat, par, step=t0)
+    oracle.encode(img, one, 1, lam=lam, seed=seed)
+    oracle.adam(slip.latents, g["grad_latents"], slip.m_lat, slip.v_lat, t0 + 2, lr=1e-2)
+    assert np.abs(slip.latents - one.latents).max() > 1e-6

@@ -33,7 +33,7 @@ def _alone(cc, req):
 
 def test_each_result_is_the_same_alone_and_in_the_mix(cc):
     from paper_2605_02726_gb300.serve import EncodeServer
-    reqs = _requests(20, [0.0, 0.0, 0.03, 0.06, 0.01], SIZES + [(512, 768)])
+    reqs = _requests(20, [0.0, 0.0, 0.03, 0.06, 0.09], SIZES + [(512, 768)])  # ids follow arrival order
     srv = EncodeServer(hbm_budget=8 << 30, tick_iters=7)
     srv.run(reqs)
     assert len(srv.done) == len(reqs) and not srv.failed

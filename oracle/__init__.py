@@ -76,6 +76,12 @@ def _load():
             "orc_table_entry": (i64, [c_int, c_int]),
             "orc_decode_probs": (None, [c_int, c_int, I32, F32, I32, I32, U32]),
             "orc_decode_image": (None, [c_int, c_int, I32, F32, D]),
+            "orc_soap_blocks": (c_int, [ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+            "orc_soap_state_count": (i64, []),
+            "orc_sym_eig": (None, [c_int, D, D, D]),
+            "orc_soap_params": (None, [D, D, D, D, D, i64, dbl, dbl, dbl, dbl, dbl, dbl, c_int, dbl]),
+            "orc_encode_soap": (None, [c_int, c_int, D, D, D, D, D, D, D, D, ctypes.POINTER(i64), c_int, u64,
+                                       dbl, dbl, dbl, dbl, dbl, dbl, dbl, c_int, dbl, D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -287,3 +293,52 @@ def decode_image(H, W, q_latents, params_f32):
     _load().orc_decode_image(H, W, q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                              p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _d(out))
     return out
+
+
+# ---------------------------------------------------------------------------------------------
+# SOAP for the network parameters (Sec. IV-B)
+# ---------------------------------------------------------------------------------------------
+SOAP_DEFAULTS = dict(b1s=0.95, b2s=0.95, bshamp=0.95, freq=10)
+
+
+def soap_blocks():
+    """[(parameter offset, m, n)] of the two-dimensional blocks that SOAP preconditions."""
+    off, m, n = ((ctypes.c_int * 16)() for _ in range(3))
+    nb = _load().orc_soap_blocks(off, m, n)
+    return [(off[b], m[b], n[b]) for b in range(nb)]
+
+
+def soap_state_count() -> int:
+    return int(_load().orc_soap_state_count())
+
+
+def sym_eig(A):
+    """(Q, lam): eigenvectors as columns of Q, decreasing eigenvalues, canonical signs."""
+    A = _f64(A)
+    n = A.shape[0]
+    Q = np.zeros((n, n))
+    lam = np.zeros(n)
+    _load().orc_sym_eig(n, _d(np.ascontiguousarray(A)), _d(Q), _d(lam))
+    return Q, lam
+
+
+def soap_params(P, g, m, v, S, t_new, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, **kw):
+    """In-place optimizer step of the parameter vector: SOAP on the 2-D blocks, Adam on the rest."""
+    o = dict(SOAP_DEFAULTS, **kw)
+    _load().orc_soap_params(_d(P), _d(_f64(g)), _d(m), _d(v), _d(S), int(t_new), lr, b1, b2, o["b1s"], o["b2s"],
+                            o["bshamp"], int(o["freq"]), eps)
+
+
+def encode_soap(image, state: State, soap_state, n_iters, *, lam, seed, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, **kw):
+    """orc_encode with SOAP on the network parameters; soap_state (float64, soap_state_count())
+    is updated in place.  Returns the per-iteration losses."""
+    o = dict(SOAP_DEFAULTS, **kw)
+    image = _f64(image)
+    _, H, W = image.shape
+    loss = np.zeros(n_iters)
+    step = ctypes.c_int64(state.step)
+    _load().orc_encode_soap(H, W, _d(image), _d(state.latents), _d(state.params), _d(state.m_lat), _d(state.v_lat),
+                            _d(state.m_par), _d(state.v_par), _d(soap_state), ctypes.byref(step), n_iters, seed, lam,
+                            lr, b1, b2, o["b1s"], o["b2s"], o["bshamp"], int(o["freq"]), eps, _d(loss))
+    state.step = step.value
+    return loss

@@ -940,3 +940,222 @@ void orc_decode_image(int H, int W, const int32_t* q, const float* Pf, double* i
     free(zero);
     free(y);
 }
+
+/* ----------------------------------------------------------------------------------------
+ * SOAP for the neural-network parameters (Sec. IV-B: SOAP for the networks, Adam for the latents).
+ * The paper names the optimizer (Vyas et al., "SOAP: Improving and Stabilizing Shampoo using Adam")
+ * and fixes none of its settings; this restatement follows the SOAP paper's single-layer step.
+ * For every two-dimensional weight block W (m x n; a residual convolution's kernel taken as
+ * [out][in * 9]) with gradient G:
+ *   step s = 0 (the first call): L = (1 - bs) G G^T, R = (1 - bs) G^T G, Q_L, Q_R = their
+ *     eigenvectors; no parameter update;
+ *   step s >= 1:  G' = Q_L^T G Q_R,  M = b1 M + (1 - b1) G,  M' = Q_L^T M Q_R,
+ *     V = b2 V + (1 - b2) G' * G'  (element-wise, kept in the rotated coordinates),
+ *     N' = (M' / (1 - b1^s)) / (sqrt(V / (1 - b2^s)) + eps),  W -= lr Q_L N' Q_R^T,
+ *     then L = bs L + (1 - bs) G G^T, R = bs R + (1 - bs) G^T G, and every `freq` steps
+ *     Q_L, Q_R = the eigenvectors of the new L, R.
+ * Eigenvectors are the columns of Q, ordered by decreasing eigenvalue, each with its entry of
+ * largest magnitude positive (unique when the eigenvalues are distinct).  They are computed by
+ * the cyclic Jacobi method (Golub and Van Loan, Matrix Computations, the symmetric Schur 2 x 2
+ * rotation applied pair by pair until the off-diagonal mass vanishes).  The SOAP paper refreshes
+ * the eigenbasis with one power-iteration step and a QR decomposition; a full decomposition gives
+ * the eigenbasis that iteration tracks.  One-dimensional blocks (biases, upsampling taps) and the
+ * latents use Adam.  M and V of a block live in the parameter moment arrays at the block's offsets;
+ * L, R, Q_L, Q_R in a separate state array, block after block, each row-major.
+ * ---------------------------------------------------------------------------------------- */
+#define N_SOAP 12
+static const int SOAP_OFF[N_SOAP] = {O_ARM_W1, O_ARM_W2, O_ARM_W3, O_ARM_WS, O_IF0_W, O_IF1_W,
+                                     O_IF2_W, O_SYN_W1, O_SYN_W2, O_SYN_WS, O_CV1_W, O_CV2_W};
+static const int SOAP_M[N_SOAP] = {AH, AH, 2, 2, NF, NF, NF, SH, NCH, NCH, NCH, NCH};
+static const int SOAP_N[N_SOAP] = {AIN, AH, AH, AIN, 6, 5, 4, NG, SH, NG, 27, 27};
+
+int orc_soap_blocks(int* off, int* m, int* n) {
+    for (int b = 0; b < N_SOAP; ++b) {
+        if (off) off[b] = SOAP_OFF[b];
+        if (m) m[b] = SOAP_M[b];
+        if (n) n[b] = SOAP_N[b];
+    }
+    return N_SOAP;
+}
+
+int64_t orc_soap_state_count(void) {
+    int64_t t = 0;
+    for (int b = 0; b < N_SOAP; ++b) t += 2 * ((int64_t)SOAP_M[b] * SOAP_M[b] + (int64_t)SOAP_N[b] * SOAP_N[b]);
+    return t;
+}
+
+/* Eigen-decomposition of the symmetric n x n matrix A (row-major): Q (row-major, eigenvectors
+ * as columns) and lam, ordered by decreasing eigenvalue, canonical signs. */
+void orc_sym_eig(int n, const double* A_in, double* Q, double* lam) {
+    double* A = (double*)malloc(sizeof(double) * n * n);
+    double* V = (double*)malloc(sizeof(double) * n * n);
+    memcpy(A, A_in, sizeof(double) * n * n);
+    for (int i = 0; i < n * n; ++i) V[i] = 0.0;
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    double norm = 0.0;
+    for (int i = 0; i < n * n; ++i) norm += A[i] * A[i];
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += 2.0 * A[p * n + q] * A[p * n + q];
+        if (off <= 1e-30 * norm || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                const double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                /* A <- J^T A J with J the rotation in the (p, q) plane */
+                for (int k = 0; k < n; ++k) {
+                    const double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    /* order by decreasing eigenvalue (selection sort), canonical sign per column */
+    int* idx = (int*)malloc(sizeof(int) * n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    for (int i = 0; i < n; ++i) {
+        int best = i;
+        for (int j = i + 1; j < n; ++j)
+            if (A[idx[j] * n + idx[j]] > A[idx[best] * n + idx[best]]) best = j;
+        const int tmp = idx[i];
+        idx[i] = idx[best];
+        idx[best] = tmp;
+    }
+    for (int j = 0; j < n; ++j) {
+        const int src = idx[j];
+        if (lam) lam[j] = A[src * n + src];
+        int imax = 0;
+        for (int i = 1; i < n; ++i)
+            if (fabs(V[i * n + src]) > fabs(V[imax * n + src])) imax = i;
+        const double sg = V[imax * n + src] < 0.0 ? -1.0 : 1.0;
+        for (int i = 0; i < n; ++i) Q[i * n + j] = sg * V[i * n + src];
+    }
+    free(idx);
+    free(V);
+    free(A);
+}
+
+/* C = op(A) * op(B) for small row-major matrices; ta / tb: use the transpose. */
+static void small_gemm(int m, int n, int k, const double* A, int ta, const double* B, int tb, double* C) {
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int q = 0; q < k; ++q) {
+                const double a = ta ? A[q * m + i] : A[i * k + q];
+                const double b = tb ? B[j * k + q] : B[q * n + j];
+                acc += a * b;
+            }
+            C[i * n + j] = acc;
+        }
+}
+
+/* One optimizer step of the network parameters at Adam count t_new (the SOAP step is t_new - 1):
+ * SOAP on the two-dimensional blocks (b1s, b2s, bshamp, freq), Adam (b1, b2) on the rest, both
+ * with learning rate lr and eps. */
+void orc_soap_params(double* P, const double* g, double* m, double* v, double* S, int64_t t_new, double lr,
+                     double b1, double b2, double b1s, double b2s, double bshamp, int freq, double eps) {
+    int is_soap[N_PARAMS];
+    for (int i = 0; i < N_PARAMS; ++i) is_soap[i] = 0;
+    for (int b = 0; b < N_SOAP; ++b)
+        for (int i = 0; i < SOAP_M[b] * SOAP_N[b]; ++i) is_soap[SOAP_OFF[b] + i] = 1;
+    /* Adam on the one-dimensional blocks */
+    {
+        const double bc1 = 1.0 - pow(b1, (double)t_new), bc2 = 1.0 - pow(b2, (double)t_new);
+        for (int i = 0; i < N_PARAMS; ++i) {
+            if (is_soap[i]) continue;
+            m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+            v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+            P[i] -= lr * (m[i] / bc1) / (sqrt(v[i] / bc2) + eps);
+        }
+    }
+    const int64_t s = t_new - 1;
+    double* st = S;
+    for (int b = 0; b < N_SOAP; ++b) {
+        const int M_ = SOAP_M[b], N_ = SOAP_N[b], off = SOAP_OFF[b];
+        double* L = st;
+        double* R = L + M_ * M_;
+        double* QL = R + N_ * N_;
+        double* QR = QL + M_ * M_;
+        st = QR + N_ * N_;
+        const double* G = g + off;
+        double* W = P + off;
+        double* Mb = m + off;
+        double* Vb = v + off;
+        double* GGt = (double*)malloc(sizeof(double) * M_ * M_);
+        double* GtG = (double*)malloc(sizeof(double) * N_ * N_);
+        small_gemm(M_, M_, N_, G, 0, G, 1, GGt);
+        small_gemm(N_, N_, M_, G, 1, G, 0, GtG);
+        if (s == 0) {
+            for (int i = 0; i < M_ * M_; ++i) L[i] = (1.0 - bshamp) * GGt[i];
+            for (int i = 0; i < N_ * N_; ++i) R[i] = (1.0 - bshamp) * GtG[i];
+            orc_sym_eig(M_, L, QL, NULL);
+            orc_sym_eig(N_, R, QR, NULL);
+        } else {
+            double* T = (double*)malloc(sizeof(double) * M_ * N_);
+            double* Gr = (double*)malloc(sizeof(double) * M_ * N_);
+            double* Mr = (double*)malloc(sizeof(double) * M_ * N_);
+            double* Nr = (double*)malloc(sizeof(double) * M_ * N_);
+            /* G' = Q_L^T G Q_R */
+            small_gemm(M_, N_, M_, QL, 1, G, 0, T);
+            small_gemm(M_, N_, N_, T, 0, QR, 0, Gr);
+            for (int i = 0; i < M_ * N_; ++i) Mb[i] = b1s * Mb[i] + (1.0 - b1s) * G[i];
+            small_gemm(M_, N_, M_, QL, 1, Mb, 0, T);
+            small_gemm(M_, N_, N_, T, 0, QR, 0, Mr);
+            const double bc1 = 1.0 - pow(b1s, (double)s), bc2 = 1.0 - pow(b2s, (double)s);
+            for (int i = 0; i < M_ * N_; ++i) {
+                Vb[i] = b2s * Vb[i] + (1.0 - b2s) * Gr[i] * Gr[i];
+                Nr[i] = (Mr[i] / bc1) / (sqrt(Vb[i] / bc2) + eps);
+            }
+            /* N = Q_L N' Q_R^T */
+            small_gemm(M_, N_, M_, QL, 0, Nr, 0, T);
+            small_gemm(M_, N_, N_, T, 0, QR, 1, Gr);
+            for (int i = 0; i < M_ * N_; ++i) W[i] -= lr * Gr[i];
+            for (int i = 0; i < M_ * M_; ++i) L[i] = bshamp * L[i] + (1.0 - bshamp) * GGt[i];
+            for (int i = 0; i < N_ * N_; ++i) R[i] = bshamp * R[i] + (1.0 - bshamp) * GtG[i];
+            if (freq > 0 && s % freq == 0) {
+                orc_sym_eig(M_, L, QL, NULL);
+                orc_sym_eig(N_, R, QR, NULL);
+            }
+            free(T);
+            free(Gr);
+            free(Mr);
+            free(Nr);
+        }
+        free(GGt);
+        free(GtG);
+    }
+}
+
+/* n_iters encoder iterations with the uniform proxy (as orc_encode), Adam on the latents and
+ * SOAP / Adam on the network parameters (orc_soap_params). */
+void orc_encode_soap(int H, int W, const double* img, double* y, double* P, double* m_y, double* v_y,
+                     double* m_p, double* v_p, double* S, int64_t* step, int n_iters, uint64_t seed, double lambda,
+                     double lr, double b1, double b2, double b1s, double b2s, double bshamp, int freq, double eps,
+                     double* loss_out) {
+    int64_t N = orc_latent_count(H, W);
+    double* gy = (double*)malloc(sizeof(double) * N);
+    double gP[N_PARAMS];
+    for (int it = 0; it < n_iters; ++it) {
+        double rate, mse;
+        double loss = orc_loss_grad(H, W, img, y, P, MODE_NOISE, seed, *step, 0.0, 1.0, lambda, &rate, &mse, gy, gP);
+        if (loss_out) loss_out[it] = loss;
+        *step += 1;
+        orc_adam(N, y, gy, m_y, v_y, *step, lr, b1, b2, eps);
+        orc_soap_params(P, gP, m_p, v_p, S, *step, lr, b1, b2, b1s, b2s, bshamp, freq, eps);
+    }
+    free(gy);
+}

@@ -82,9 +82,30 @@ typedef struct {
     int32_t noise_mode;
     uint64_t seed;
     float sigma0, sigma1, temp0, temp1, lr_min; /* CC_NOISE_SOFTROUND only */
-    int32_t reserved;                           /* 0 */
+    int32_t nn_optimizer;                       /* CC_OPT_ADAM or CC_OPT_SOAP                */
     int64_t n_main;                             /* CC_NOISE_SOFTROUND only */
+    float soap_beta1, soap_beta2, soap_shampoo_beta; /* CC_OPT_SOAP only, each in [0, 1)  */
+    int32_t soap_freq;                          /* CC_OPT_SOAP only: eigenbasis refresh period >= 1 */
 } cc_hparams_t;
+
+/* Optimizer of the network parameters (the latents always use Adam, Sec. IV-B):
+ *   CC_OPT_ADAM: Adam with beta1, beta2, eps, like the latents.
+ *   CC_OPT_SOAP: SOAP (Vyas et al., cited by Sec. IV-B; the paper gives none of its settings) on the
+ *     two-dimensional weight blocks (ARM W1, W2, W3, Ws; the three IFCE matrices; synthesis W1, W2,
+ *     Ws; each residual convolution's kernel as [out][in * 9]) and Adam on the other parameters.
+ *     For a block W (m x n) with gradient G, at SOAP step s = Adam count - 1:
+ *       s = 0: L = (1 - bs) G G^T, R = (1 - bs) G^T G, Q_L, Q_R = their eigenvectors; W unchanged;
+ *       s >= 1: G' = Q_L^T G Q_R, M = b1 M + (1 - b1) G, M' = Q_L^T M Q_R, V = b2 V + (1 - b2) G'^2,
+ *         W -= lr Q_L [(M' / (1 - b1^s)) / (sqrt(V / (1 - b2^s)) + eps)] Q_R^T, then L, R take the
+ *         new G (same beta bs) and, every soap_freq steps, Q_L, Q_R become their eigenvectors
+ *         (full eigen-decomposition; columns by decreasing eigenvalue, the entry of largest
+ *         magnitude of each positive).
+ *     (b1, b2, bs) = (soap_beta1, soap_beta2, soap_shampoo_beta); lr is the proxy's learning rate.
+ *     M and V are the block's slots of m_par and v_par (V in the rotated coordinates); L, R, Q_L,
+ *     Q_R live in state->soap.  Within a repeated eigenvalue the eigenbasis is not unique, so two
+ *     implementations agree on the step only where the preconditioners' eigenvalues are distinct. */
+#define CC_OPT_ADAM 0
+#define CC_OPT_SOAP 1
 
 /* Encoder state, all [device], caller-owned: latents, params and their Adam moments (same
  * sizes), and the step counter (one int64; the number of Adam steps already taken, which also
@@ -92,6 +113,7 @@ typedef struct {
 typedef struct {
     float *latents, *params, *m_lat, *v_lat, *m_par, *v_par;
     int64_t* step;
+    float* soap; /* CC_OPT_SOAP: coolchic_soap_state_floats() floats (zero before the first step); else NULL */
 } cc_state_t;
 
 /* Rate-distortion record: loss = mse + lambda * rate_bits / (H*W). */
@@ -128,6 +150,10 @@ int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int3
  *   coolchic_latent_count / coolchic_param_count).
  * Asynchronous on `stream`.  CC_ERR_ARG for a bad arch or a NULL pointer. */
 int coolchic_init_state(const cc_arch_t* arch, uint64_t seed, const cc_state_t* state, void* stream);
+
+/* Floats of the SOAP state (CC_OPT_SOAP): for each two-dimensional block in storage order, L
+ * [m][m], R [n][n], Q_L [m][m], Q_R [n][n] (13498 floats). */
+int64_t coolchic_soap_state_floats(void);
 
 /* Bytes of device workspace one job needs.  `flags` bit 0 (CC_WS_STORE_ACTIVATIONS): room for
  * stored forward activations (coolchic_forward with store_activations = 1).  Bit 1

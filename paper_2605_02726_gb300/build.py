@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcoolchic.so")
-SOURCES = ["cc_api.cu", "cc_arm.cu", "cc_synth.cu", "cc_syn.cu", "cc_conv.cu", "cc_optim.cu", "cc_decode.cu", "cc_noalloc.cu", "cc_batch.cu", "cc_peaks.cu"]
+SOURCES = ["cc_api.cu", "cc_arm.cu", "cc_synth.cu", "cc_syn.cu", "cc_conv.cu", "cc_optim.cu", "cc_decode.cu", "cc_noalloc.cu", "cc_batch.cu", "cc_peaks.cu", "cc_soap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

@@ -81,6 +81,12 @@ int check_hp(const cc_hparams_t* hp) {
           hp->sigma0 >= 0.f && hp->sigma1 >= 0.f && std::isfinite(hp->sigma0) && std::isfinite(hp->sigma1) &&
           std::isfinite(hp->lr_min) && hp->n_main >= 0))
         return fail(CC_ERR_ARG, "soft-round schedule: temperatures > 0, sigmas >= 0, finite lr_min, n_main >= 0");
+    if (hp->nn_optimizer != CC_OPT_ADAM && hp->nn_optimizer != CC_OPT_SOAP)
+        return fail(CC_ERR_UNSUPPORTED, "nn_optimizer must be CC_OPT_ADAM or CC_OPT_SOAP");
+    if (hp->nn_optimizer == CC_OPT_SOAP &&
+        !(hp->soap_beta1 >= 0.f && hp->soap_beta1 < 1.f && hp->soap_beta2 >= 0.f && hp->soap_beta2 < 1.f &&
+          hp->soap_shampoo_beta >= 0.f && hp->soap_shampoo_beta < 1.f && hp->soap_freq >= 1))
+        return fail(CC_ERR_ARG, "SOAP: betas in [0, 1) and soap_freq >= 1");
     return CC_OK;
 }
 
@@ -290,6 +296,11 @@ Hp hp_from(const cc_hparams_t* h) {
     o.temp1 = h->temp1;
     o.lr_min = h->lr_min;
     o.n_main = h->n_main;
+    o.nn_opt = h->nn_optimizer;
+    o.sb1 = h->soap_beta1;
+    o.sb2 = h->soap_beta2;
+    o.sbs = h->soap_shampoo_beta;
+    o.sfreq = h->soap_freq;
     return o;
 }
 
@@ -325,6 +336,7 @@ int encode_enqueue(const Work& w, const cc_hparams_t* hp, const float* image, co
                       it + 1 < n_iters);
         tend(CC_KERNEL_GATHER, s);
         launch_param_reduce(w, st->params, st->m_par, st->v_par, nullptr, 1.f, h, st->step, s);
+        if (h.nn_opt == CC_OPT_SOAP) launch_soap(w, st->params, st->m_par, st->v_par, st->soap, h, st->step, s);
         launch_finish(w, h, 1, 1, (double*)rd_per_iter, st->step, 0, 1, s);
         if ((rc = launched("encode_step"))) return rc;
     }
@@ -360,16 +372,17 @@ std::string encode_key(int dev, const cc_arch_t* a, const cc_hparams_t* hp, cons
                        int32_t n_iters, const cc_rd_t* rd, const void* ws, size_t ws_bytes) {
     std::string k;
     for (int32_t v : {dev, a->C, a->H, a->W, a->L, a->n_ctx, a->ifce_dim, a->ifce_grids, a->arm_hidden, a->arm_layers,
-                      a->syn_hidden, a->n_resconv, a->up_taps, a->stabilizer, n_iters, hp->noise_mode, hp->reserved})
+                      a->syn_hidden, a->n_resconv, a->up_taps, a->stabilizer, n_iters, hp->noise_mode, hp->nn_optimizer,
+                      hp->soap_freq})
         key_put(k, v);
     for (float v : {hp->lambda, hp->lr, hp->beta1, hp->beta2, hp->eps, hp->sigma0, hp->sigma1, hp->temp0, hp->temp1,
-                    hp->lr_min})
+                    hp->lr_min, hp->soap_beta1, hp->soap_beta2, hp->soap_shampoo_beta})
         key_put(k, v);
     key_put(k, hp->seed);
     key_put(k, hp->n_main);
     for (const void* p : {(const void*)image, (const void*)st->latents, (const void*)st->params, (const void*)st->m_lat,
                           (const void*)st->v_lat, (const void*)st->m_par, (const void*)st->v_par, (const void*)st->step,
-                          (const void*)rd, ws})
+                          (const void*)st->soap, (const void*)rd, ws})
         key_put(k, p);
     key_put(k, ws_bytes);
     return k;
@@ -485,6 +498,10 @@ int coolchic_init_state(const cc_arch_t* arch, uint64_t seed, const cc_state_t* 
     a.N = make_geom(arch->H, arch->W).off[kL];
     a.seed = seed;
     launch_init_state(a, (cudaStream_t)stream);
+    if (st->soap) {  // the SOAP state starts at zero
+        const cudaError_t e = cudaMemsetAsync(st->soap, 0, sizeof(float) * (size_t)soap_state_floats(), (cudaStream_t)stream);
+        if (e != cudaSuccess) return fail(CC_ERR_CUDA, "init_state: %s", cudaGetErrorString(e));
+    }
     return launched("init_state");
 }
 
@@ -519,6 +536,8 @@ int64_t coolchic_kernel_launches(const cc_arch_t* a, int32_t n_iters) {
     const int64_t per_iter = 8 + (kUpArmLo - 1) + (kL - 1);
     return 1 + per_iter * n_iters;
 }
+
+int64_t coolchic_soap_state_floats(void) { return soap_state_floats(); }
 
 size_t coolchic_workspace_bytes(const cc_arch_t* a, int32_t flags) {
     if (check_arch(a)) return 0;
@@ -556,9 +575,10 @@ int encode_dispatch(const Work& w, const cc_arch_t* arch, const cc_hparams_t* hp
     return encode_enqueue(w, hp, image, st, n_iters, rd_per_iter, s);
 }
 
-int check_state(const cc_state_t* st) {
+int check_state(const cc_state_t* st, const cc_hparams_t* hp) {
     if (!st || !st->latents || !st->params || !st->m_lat || !st->v_lat || !st->m_par || !st->v_par || !st->step)
         return fail(CC_ERR_ARG, "NULL state pointer");
+    if (hp->nn_optimizer == CC_OPT_SOAP && !st->soap) return fail(CC_ERR_ARG, "CC_OPT_SOAP needs state->soap");
     return CC_OK;
 }
 }  // namespace
@@ -573,7 +593,7 @@ int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const fl
     if (rc) return rc;
     if ((rc = check_hp(hp))) return rc;
     if (!image) return fail(CC_ERR_ARG, "NULL image pointer");
-    if ((rc = check_state(st))) return rc;
+    if ((rc = check_state(st, hp))) return rc;
     if (n_iters < 0) return fail(CC_ERR_ARG, "n_iters must be >= 0");
     if (n_iters == 0) return CC_OK;
     return encode_dispatch(w, arch, hp, image, st, n_iters, rd_per_iter, ws, ws_bytes, (cudaStream_t)stream);
@@ -587,7 +607,7 @@ int coolchic_encode_step_host(const cc_arch_t* arch, const cc_hparams_t* hp, con
     if (rc) return rc;
     if ((rc = check_hp(hp))) return rc;
     if (!image_host) return fail(CC_ERR_ARG, "NULL host image pointer");
-    if ((rc = check_state(st))) return rc;
+    if ((rc = check_state(st, hp))) return rc;
     if (n_iters < 1) return fail(CC_ERR_ARG, "encode_step_host: n_iters must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(w.io_image, image_host, (size_t)3 * w.HW * sizeof(float), cudaMemcpyHostToDevice, s);

@@ -29,6 +29,8 @@ struct cc_batch {
     cc::Batch<cc::GatherArgs> gather;       // last iteration of a call: Adam only
     cc::Batch<cc::GatherArgs> gather_next;  // other iterations: Adam + next step's relaxed latents
     cc::Batch<cc::ReduceArgs> reduce;
+    cc::Batch<cc::SoapArgs> soap;  // launched when some job uses CC_OPT_SOAP
+    bool any_soap = false;
     cc::Batch<cc::FinishArgs> finish;
     double* rd = nullptr;  // device [rd_capacity][n][3]
 };
@@ -76,8 +78,8 @@ int scaled(int cap, float f) {
 }
 
 size_t table_bytes(int n, int rd_capacity) {
-    // upper bound: 21 kernel tables of at most 512-byte args plus CTA arrays, and the records
-    return (size_t)21 * ((size_t)512 * n + 256 + sizeof(int) * (n + 1) + 256) + (size_t)rd_capacity * n * 3 * sizeof(double) + 4096;
+    // upper bound: 22 kernel tables of at most 512-byte args plus CTA arrays, and the records
+    return (size_t)22 * ((size_t)512 * n + 256 + sizeof(int) * (n + 1) + 256) + (size_t)rd_capacity * n * 3 * sizeof(double) + 4096;
 }
 
 }  // namespace
@@ -119,6 +121,8 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
         const cc_state_t& st = states[j];
         if (!images[j] || !st.latents || !st.params || !st.m_lat || !st.v_lat || !st.m_par || !st.v_par || !st.step)
             return set_error(CC_ERR_ARG, "batch_create: job %d has a NULL image or state pointer", j);
+        if (h.nn_optimizer == CC_OPT_SOAP && !st.soap)
+            return set_error(CC_ERR_ARG, "batch_create: job %d uses CC_OPT_SOAP without a SOAP state", j);
         if (!workspaces[j] || ((uintptr_t)workspaces[j] & 255))
             return set_error(CC_ERR_WORKSPACE, "batch_create: job %d workspace NULL or misaligned", j);
         const size_t need = layout_job(&archs[j], 0, nullptr, nullptr);
@@ -179,6 +183,10 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
                           [&](int j) { return scaled(gather_ctas(W[j]), sc.other); });
     b->reduce = fill([&](int j) { return reduce_args(W[j], states[j].params, states[j].m_par, states[j].v_par, nullptr, 1.f, H[j], states[j].step); },
                      [&](int) { return reduce_ctas(); });
+    b->soap = fill([&](int j) { return soap_args(W[j], states[j].params, states[j].m_par, states[j].v_par,
+                                                 states[j].soap, H[j], states[j].step); },
+                   [&](int) { return kSoapBlocks; });
+    for (int j = 0; j < n; ++j) b->any_soap |= H[j].nn_opt == 1;
     b->finish = fill([&](int j) {
                          // record pointer: offset of this job's first slot inside the table (fixed up below)
                          return finish_args(W[j], H[j], 1, 1, reinterpret_cast<double*>(rd_off + (size_t)j * 3 * sizeof(double)),
@@ -211,6 +219,7 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
     place(b->gather, base);
     place(b->gather_next, base);
     place(b->reduce, base);
+    place(b->soap, base);
     place(b->finish, base);
     b->rd = rd_capacity > 0 ? reinterpret_cast<double*>(base + rd_off) : nullptr;
     b->table = base;
@@ -240,6 +249,7 @@ int coolchic_batch_step(cc_batch_t* b, int32_t n_iters, void* stream) {
         launch_ifce_b(b->ifce, s);
         launch_gather_b(it + 1 < n_iters ? b->gather_next : b->gather, s);
         launch_reduce_b(b->reduce, s);
+        if (b->any_soap) launch_soap_b(b->soap, s);
         launch_finish_b(b->finish, s);
     }
     cudaError_t e = cudaGetLastError();

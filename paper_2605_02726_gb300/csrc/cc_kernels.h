@@ -22,6 +22,9 @@ struct Hp {
     int noise_mode;                              // 0 additive uniform, 1 soft-round schedule
     float sigma0, sigma1, temp0, temp1, lr_min;  // mode 1
     int64_t n_main;                              // mode 1: first step of the hard-round stage
+    int nn_opt;                                  // network parameters: 0 Adam, 1 SOAP
+    float sb1, sb2, sbs;                         // SOAP: moment betas, preconditioner beta
+    int sfreq;                                   // SOAP: eigenbasis refresh every sfreq steps
 };
 Hp hp_from(const cc_hparams_t* h);
 int validate_hparams(const cc_hparams_t* h);  // CC_OK or an error code with the message set
@@ -315,6 +318,7 @@ struct GatherArgs {
     int proxy;        // latents relaxed by the training proxy: chain rule through dy~/dy
 };
 struct ReduceArgs {
+    float* gsoap;  // SOAP (hp.nn_opt == 1): the reduced gradient of the SOAP blocks goes here
     const float* garm;
     const float* gup;  // [6][kUpMaxCta][4]
     const float* gsyn;
@@ -338,6 +342,33 @@ struct FinishArgs {
     double inv_hw, inv_3hw, lambda;
     int n_rate, n_se, rd_stride, mark_base, increment, pad_;
 };
+
+// The network-parameter blocks that SOAP preconditions (two-dimensional weights).
+constexpr int kSoapBlocks = 12;
+__host__ __device__ constexpr bool soap_param(int p) {
+    return (p >= po::arm_w1 && p < po::arm_b1) || (p >= po::arm_w2 && p < po::arm_b2) ||
+           (p >= po::arm_w3 && p < po::arm_b3) || (p >= po::arm_ws && p < po::arm_bs) ||
+           (p >= po::if_w0 && p < po::if_b0) || (p >= po::if_w1 && p < po::if_b1) ||
+           (p >= po::if_w2 && p < po::if_b2) || (p >= po::syn_w1 && p < po::syn_b1) ||
+           (p >= po::syn_w2 && p < po::syn_b2) || (p >= po::syn_ws && p < po::syn_bs) ||
+           (p >= po::cv1_w && p < po::cv1_b) || (p >= po::cv2_w && p < po::cv2_b);
+}
+struct SoapArgs {
+    const float* grad;  // reduced gradient (workspace)
+    float* params;
+    float* m;
+    float* v;
+    float* soap;        // L, R, Q_L, Q_R of every block
+    const int64_t* step_dev;
+    Hp hp;
+};
+int64_t soap_state_floats();
+SoapArgs soap_args(const Work& w, float* params, float* m, float* v, float* soap, const Hp& hp,
+                   const int64_t* step_dev);
+// SOAP step of the two-dimensional network blocks (after the parameter reduction)
+void launch_soap(const Work& w, float* params, float* m, float* v, float* soap, const Hp& hp,
+                 const int64_t* step_dev, cudaStream_t s);
+void launch_soap_b(const Batch<SoapArgs>& b, cudaStream_t s);
 
 int num_sms();
 // Records a printf-style message for coolchic_last_error() and returns `code`.

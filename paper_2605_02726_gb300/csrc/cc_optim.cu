@@ -313,6 +313,10 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
         a.grad_out[p] = gsum * a.out_scale;
         return;
     }
+    if (a.hp.nn_opt == 1 && soap_param(p)) {  // updated by the SOAP kernel that follows
+        a.gsoap[p] = gsum;
+        return;
+    }
     float bc1, bc2;
     adam_bias_corrections(step + 1, a.hp.beta1, a.hp.beta2, bc1, bc2);
     const float lr = proxy_at(a.hp, step).lr;
@@ -485,6 +489,7 @@ GatherArgs gather_args(const Work& w, int relax, float* grad_out, float* y, floa
 ReduceArgs reduce_args(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,
                        const Hp& hp, const int64_t* step_dev) {
     ReduceArgs a;
+    a.gsoap = w.grad_params;
     a.garm = w.gpart_arm;
     a.gup = w.gpart_up;
     a.gsyn = w.gpart_syn;

@@ -31,13 +31,14 @@ class HParams(ctypes.Structure):
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("noise_mode", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("sigma0", ctypes.c_float), ("sigma1", ctypes.c_float),
                 ("temp0", ctypes.c_float), ("temp1", ctypes.c_float), ("lr_min", ctypes.c_float),
-                ("reserved", ctypes.c_int32), ("n_main", ctypes.c_int64)]
+                ("nn_optimizer", ctypes.c_int32), ("n_main", ctypes.c_int64), ("soap_beta1", ctypes.c_float),
+                ("soap_beta2", ctypes.c_float), ("soap_shampoo_beta", ctypes.c_float), ("soap_freq", ctypes.c_int32)]
 
 
 class State(ctypes.Structure):
     _fields_ = [("latents", ctypes.c_void_p), ("params", ctypes.c_void_p), ("m_lat", ctypes.c_void_p),
                 ("v_lat", ctypes.c_void_p), ("m_par", ctypes.c_void_p), ("v_par", ctypes.c_void_p),
-                ("step", ctypes.c_void_p)]
+                ("step", ctypes.c_void_p), ("soap", ctypes.c_void_p)]
 
 
 class RD(ctypes.Structure):
@@ -86,6 +87,7 @@ def _load():
         "coolchic_timing_collect": (i32, [P(ctypes.c_double), P(i64)]),
         "coolchic_timing_disable": (i32, []),
         "coolchic_measure_peak": (i32, [i32, vp, P(ctypes.c_double), P(ctypes.c_double), vp]),
+        "coolchic_soap_state_floats": (i64, []),
         "coolchic_last_error": (ctypes.c_char_p, []),
         "coolchic_version": (ctypes.c_char_p, []),
     }
@@ -104,7 +106,7 @@ EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count
             "coolchic_timing_disable", "coolchic_last_error", "coolchic_version",
             "coolchic_rate_distortion_noalloc", "coolchic_batch_table_bytes", "coolchic_batch_create",
             "coolchic_batch_step", "coolchic_batch_records", "coolchic_batch_destroy", "coolchic_measure_peak",
-            "coolchic_encode_step_host"]
+            "coolchic_encode_step_host", "coolchic_soap_state_floats"]
 
 KERNEL_ARM, KERNEL_SYN_BWD, KERNEL_CONV, KERNEL_SYN_FWD = 0, 1, 2, 3
 KERNEL_UP_FWD, KERNEL_UP_ADJ, KERNEL_GATHER = 4, 5, 6
@@ -180,17 +182,36 @@ def arch(H: int, W: int) -> Arch:
 CC_NOISE_UNIFORM, CC_NOISE_SOFTROUND = 0, 1
 
 
-def hparams(lam=1e-3, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, seed=0) -> HParams:
-    """Additive uniform proxy, constant learning rate."""
-    return HParams(lam, lr, beta1, beta2, eps, CC_NOISE_UNIFORM, seed, 0.0, 0.0, 1.0, 1.0, lr, 0, 0)
+CC_OPT_ADAM, CC_OPT_SOAP = 0, 1
+# SOAP settings (the SOAP paper's defaults; the Cool-chic paper gives none): moment betas,
+# preconditioner beta, eigenbasis refresh period
+SOAP_DEFAULTS = dict(soap_beta1=0.95, soap_beta2=0.95, soap_shampoo_beta=0.95, soap_freq=10)
+
+
+def _with_soap(hp: HParams, soap: bool, **kw) -> HParams:
+    o = dict(SOAP_DEFAULTS, **kw)
+    hp.nn_optimizer = CC_OPT_SOAP if soap else CC_OPT_ADAM
+    hp.soap_beta1, hp.soap_beta2 = o["soap_beta1"], o["soap_beta2"]
+    hp.soap_shampoo_beta, hp.soap_freq = o["soap_shampoo_beta"], int(o["soap_freq"])
+    return hp
+
+
+def hparams(lam=1e-3, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, seed=0, soap=False, **soap_kw) -> HParams:
+    """Additive uniform proxy, constant learning rate; soap=True: SOAP on the network's 2-D blocks."""
+    return _with_soap(HParams(lam, lr, beta1, beta2, eps, CC_NOISE_UNIFORM, seed, 0.0, 0.0, 1.0, 1.0, lr, 0, 0),
+                      soap, **soap_kw)
 
 
 def hparams_schedule(lam=1e-3, n_main=1000, lr=1e-2, lr_min=1e-5, sigma0=0.22, sigma1=0.15, temp0=0.35,
-                     temp1=0.08, beta1=0.9, beta2=0.999, eps=1e-8, seed=0) -> HParams:
+                     temp1=0.08, beta1=0.9, beta2=0.999, eps=1e-8, seed=0, soap=False, **soap_kw) -> HParams:
     """The paper's soft-round proxy and schedule (Table I defaults): main stage for steps < n_main,
     then the hard-round stage."""
-    return HParams(lam, lr, beta1, beta2, eps, CC_NOISE_SOFTROUND, seed, sigma0, sigma1, temp0, temp1, lr_min,
-                   0, int(n_main))
+    return _with_soap(HParams(lam, lr, beta1, beta2, eps, CC_NOISE_SOFTROUND, seed, sigma0, sigma1, temp0, temp1,
+                              lr_min, 0, int(n_main)), soap, **soap_kw)
+
+
+def soap_state_floats() -> int:
+    return int(_lib.coolchic_soap_state_floats())
 
 
 def latent_count(H: int, W: int) -> int:
@@ -230,7 +251,7 @@ def workspace(H: int, W: int, store_activations: bool = False, device=None, host
 class EncoderState:
     """Device-resident encoder state: latents, parameters, Adam moments, step counter."""
 
-    def __init__(self, latents: torch.Tensor, params: torch.Tensor, step: int = 0):
+    def __init__(self, latents: torch.Tensor, params: torch.Tensor, step: int = 0, soap: bool = False):
         dev = latents.device
         self.latents = latents.detach().clone().float().contiguous()
         self.params = params.detach().clone().float().contiguous()
@@ -239,10 +260,13 @@ class EncoderState:
         self.m_par = torch.zeros_like(self.params)
         self.v_par = torch.zeros_like(self.params)
         self.step = torch.full((1,), int(step), dtype=torch.int64, device=dev)
+        # SOAP preconditioners and eigenbases (L, R, Q_L, Q_R of every 2-D block), zero at the start
+        self.soap = torch.zeros(soap_state_floats(), device=dev) if soap else None
 
     def c_state(self) -> State:
         return State(self.latents.data_ptr(), self.params.data_ptr(), self.m_lat.data_ptr(), self.v_lat.data_ptr(),
-                     self.m_par.data_ptr(), self.v_par.data_ptr(), self.step.data_ptr())
+                     self.m_par.data_ptr(), self.v_par.data_ptr(), self.step.data_ptr(),
+                     self.soap.data_ptr() if self.soap is not None else None)
 
     @staticmethod
     def init(H: int, W: int, seed: int, device=None, stream=None) -> "EncoderState":
@@ -260,6 +284,7 @@ class EncoderState:
         s = EncoderState.__new__(EncoderState)
         for k in ("latents", "params", "m_lat", "v_lat", "m_par", "v_par", "step"):
             setattr(s, k, getattr(self, k).clone())
+        s.soap = self.soap.clone() if self.soap is not None else None
         return s
 
 

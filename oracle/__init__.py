@@ -24,6 +24,8 @@ _lib = None
 
 N_GRIDS = 7
 N_PARAMS = 1415
+N_HYPER_GRIDS = 3
+N_PARAMS_H = N_PARAMS + 3 * 4 * N_HYPER_GRIDS  # + IFCE weights of the hyperlatent inputs
 MODE_NOISE, MODE_HARD, MODE_IDENTITY, MODE_SOFTROUND = 0, 1, 2, 3
 
 
@@ -53,8 +55,8 @@ def _load():
         c_int = ctypes.c_int
         dbl = ctypes.c_double
         sig = {
-            "orc_param_count": (c_int, []),
-            "orc_latent_count": (i64, [c_int, c_int]),
+            "orc_param_count": (c_int, [c_int]),
+            "orc_latent_count": (i64, [c_int, c_int, c_int]),
             "orc_grid_shape": (None, [c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
             "orc_context_offsets": (None, [ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
             "orc_splitmix64_mix": (u64, [u64]),
@@ -64,30 +66,30 @@ def _load():
             "orc_laplace_prob": (dbl, [dbl, dbl, dbl, D, D]),
             "orc_upsample": (None, [c_int, c_int, c_int, c_int, D, D, D]),
             "orc_conv3x3_res": (None, [c_int, c_int, D, D, D, D]),
-            "orc_forward": (dbl, [c_int, c_int, D, D, D, c_int, u64, i64, dbl, dbl, dbl, D, D, D, D, D, D]),
-            "orc_loss_grad": (dbl, [c_int, c_int, D, D, D, c_int, u64, i64, dbl, dbl, dbl, D, D, D, D]),
+            "orc_forward": (dbl, [c_int, c_int, c_int, D, D, D, c_int, u64, i64, dbl, dbl, dbl, D, D, D, D, D, D]),
+            "orc_loss_grad": (dbl, [c_int, c_int, c_int, D, D, D, c_int, u64, i64, dbl, dbl, dbl, D, D, D, D]),
             "orc_adam": (None, [i64, D, D, D, D, i64, dbl, dbl, dbl, dbl]),
-            "orc_encode": (None, [c_int, c_int, D, D, D, D, D, D, D, ctypes.POINTER(i64), c_int, u64,
+            "orc_encode": (None, [c_int, c_int, c_int, D, D, D, D, D, D, D, ctypes.POINTER(i64), c_int, u64,
                                   dbl, dbl, dbl, dbl, dbl, D, D, D]),
-            "orc_encode_schedule": (None, [c_int, c_int, D, D, D, D, D, D, D, ctypes.POINTER(i64), c_int,
+            "orc_encode_schedule": (None, [c_int, c_int, c_int, D, D, D, D, D, D, D, ctypes.POINTER(i64), c_int,
                                            u64, dbl, dbl, dbl, dbl, dbl, dbl, dbl, i64, dbl, dbl, dbl, D,
                                            D, D]),
             "orc_cdf_q16": (i64, [ctypes.c_int32, i64]),
             "orc_table_entry": (i64, [c_int, c_int]),
-            "orc_decode_probs": (None, [c_int, c_int, I32, F32, I32, I32, U32]),
-            "orc_decode_image": (None, [c_int, c_int, I32, F32, D]),
+            "orc_decode_probs": (None, [c_int, c_int, c_int, I32, F32, I32, I32, U32]),
+            "orc_decode_image": (None, [c_int, c_int, c_int, I32, F32, D]),
             "orc_soap_blocks": (c_int, [ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
             "orc_soap_state_count": (i64, []),
             "orc_sym_eig": (None, [c_int, D, D, D]),
-            "orc_soap_params": (None, [D, D, D, D, D, i64, dbl, dbl, dbl, dbl, dbl, dbl, c_int, dbl]),
-            "orc_encode_soap": (None, [c_int, c_int, D, D, D, D, D, D, D, D, ctypes.POINTER(i64), c_int, u64,
+            "orc_soap_params": (None, [c_int, D, D, D, D, D, i64, dbl, dbl, dbl, dbl, dbl, dbl, c_int, dbl]),
+            "orc_encode_soap": (None, [c_int, c_int, c_int, D, D, D, D, D, D, D, D, ctypes.POINTER(i64), c_int, u64,
                                        dbl, dbl, dbl, dbl, dbl, dbl, dbl, c_int, dbl, D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
-        assert lib.orc_param_count() == N_PARAMS
+        assert lib.orc_param_count(0) == N_PARAMS and lib.orc_param_count(1) == N_PARAMS_H
         _lib = lib
         return lib
 
@@ -106,14 +108,22 @@ def _f64(a):
 # ---------------------------------------------------------------------------------------------
 # geometry
 # ---------------------------------------------------------------------------------------------
-def latent_count(H: int, W: int) -> int:
-    return int(_load().orc_latent_count(H, W))
+def _hyper(params) -> int:
+    """1 when the parameter vector carries the hyperlatent IFCE block (Sec. III-A3)."""
+    n = np.asarray(params).shape[0]
+    assert n in (N_PARAMS, N_PARAMS_H), n
+    return 1 if n == N_PARAMS_H else 0
 
 
-def grid_shapes(H: int, W: int):
+def latent_count(H: int, W: int, hyper: bool = False) -> int:
+    return int(_load().orc_latent_count(H, W, 1 if hyper else 0))
+
+
+def grid_shapes(H: int, W: int, hyper: bool = False):
+    """Shapes of the latent grids, then (hyper) of the hyperlatent grids (1/16, 1/32, 1/64)."""
     lib = _load()
     out = []
-    for k in range(N_GRIDS):
+    for k in range(N_GRIDS + (N_HYPER_GRIDS if hyper else 0)):
         h, w = ctypes.c_int(), ctypes.c_int()
         lib.orc_grid_shape(H, W, k, ctypes.byref(h), ctypes.byref(w))
         out.append((h.value, w.value))
@@ -185,13 +195,15 @@ def forward(image, latents, params, *, lam, mode=MODE_NOISE, seed=0, step=0, sig
     MODE_SOFTROUND (Eq. 13)."""
     image, latents, params = _f64(image), _f64(latents), _f64(params)
     _, H, W = image.shape
-    N = latent_count(H, W)
+    N = latent_count(H, W, _hyper(params))
+    assert latents.shape[0] == N, (latents.shape, N)
     rate, mse = ctypes.c_double(), ctypes.c_double()
     mu = logb = bits = xhat = None
     if per_latent:
         mu, logb, bits = (np.zeros(N) for _ in range(3))
         xhat = np.zeros_like(image)
-    loss = _load().orc_forward(H, W, _d(image), _d(latents), _d(params), mode, seed, step, sigma, temp, lam,
+    loss = _load().orc_forward(H, W, _hyper(params), _d(image), _d(latents), _d(params), mode, seed, step, sigma,
+                               temp, lam,
                                ctypes.byref(rate), ctypes.byref(mse), _d(mu), _d(logb), _d(bits),
                                _d(xhat))
     out = dict(loss=loss, rate_bits=rate.value, mse=mse.value)
@@ -204,10 +216,12 @@ def loss_grad(image, latents, params, *, lam, mode=MODE_NOISE, seed=0, step=0, s
     """Returns dict(loss, rate_bits, mse, grad_latents, grad_params)."""
     image, latents, params = _f64(image), _f64(latents), _f64(params)
     _, H, W = image.shape
+    assert latents.shape[0] == latent_count(H, W, _hyper(params)), latents.shape
     gy = np.zeros(latents.shape[0])
-    gp = np.zeros(N_PARAMS)
+    gp = np.zeros(params.shape[0])
     rate, mse = ctypes.c_double(), ctypes.c_double()
-    loss = _load().orc_loss_grad(H, W, _d(image), _d(latents), _d(params), mode, seed, step, sigma, temp,
+    loss = _load().orc_loss_grad(H, W, _hyper(params), _d(image), _d(latents), _d(params), mode, seed, step, sigma,
+                                 temp,
                                  lam, ctypes.byref(rate), ctypes.byref(mse), _d(gy), _d(gp))
     return dict(loss=loss, rate_bits=rate.value, mse=mse.value, grad_latents=gy, grad_params=gp)
 
@@ -236,7 +250,7 @@ def encode(image, state: State, n_iters, *, lam, seed, lr=1e-2, b1=0.9, b2=0.999
     _, H, W = image.shape
     loss, rate, mse = (np.zeros(n_iters) for _ in range(3))
     step = ctypes.c_int64(state.step)
-    _load().orc_encode(H, W, _d(image), _d(state.latents), _d(state.params), _d(state.m_lat),
+    _load().orc_encode(H, W, _hyper(state.params), _d(image), _d(state.latents), _d(state.params), _d(state.m_lat),
                        _d(state.v_lat), _d(state.m_par), _d(state.v_par), ctypes.byref(step), n_iters,
                        seed, lam, lr, b1, b2, eps, _d(loss), _d(rate), _d(mse))
     state.step = step.value
@@ -252,7 +266,8 @@ def encode_schedule(image, state: State, n_iters, *, lam, seed, n_main, lr_max=1
     _, H, W = image.shape
     loss, rate, mse = (np.zeros(n_iters) for _ in range(3))
     step = ctypes.c_int64(state.step)
-    _load().orc_encode_schedule(H, W, _d(image), _d(state.latents), _d(state.params), _d(state.m_lat),
+    _load().orc_encode_schedule(H, W, _hyper(state.params), _d(image), _d(state.latents), _d(state.params),
+                                _d(state.m_lat),
                                 _d(state.v_lat), _d(state.m_par), _d(state.v_par), ctypes.byref(step), n_iters,
                                 seed, lam, lr_max, lr_min, sigma0, sigma1, temp0, temp1, int(n_main), b1, b2, eps,
                                 _d(loss), _d(rate), _d(mse))
@@ -275,10 +290,11 @@ def decode_probs(H, W, q_latents, params_f32):
     q = np.ascontiguousarray(q_latents, dtype=np.int32)
     p = np.ascontiguousarray(params_f32, dtype=np.float32)
     N = q.shape[0]
+    assert N == latent_count(H, W, _hyper(p)), (N, H, W)
     mu = np.zeros(N, np.int32)
     lb = np.zeros(N, np.int32)
     pr = np.zeros(N, np.uint32)
-    _load().orc_decode_probs(H, W, q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+    _load().orc_decode_probs(H, W, _hyper(p), q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                              p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                              mu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                              lb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
@@ -289,8 +305,9 @@ def decode_probs(H, W, q_latents, params_f32):
 def decode_image(H, W, q_latents, params_f32):
     q = np.ascontiguousarray(q_latents, dtype=np.int32)
     p = np.ascontiguousarray(params_f32, dtype=np.float32)
+    assert q.shape[0] == latent_count(H, W, _hyper(p)), (q.shape, H, W)
     out = np.zeros((3, H, W))
-    _load().orc_decode_image(H, W, q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+    _load().orc_decode_image(H, W, _hyper(p), q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                              p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _d(out))
     return out
 
@@ -325,7 +342,8 @@ def sym_eig(A):
 def soap_params(P, g, m, v, S, t_new, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, **kw):
     """In-place optimizer step of the parameter vector: SOAP on the 2-D blocks, Adam on the rest."""
     o = dict(SOAP_DEFAULTS, **kw)
-    _load().orc_soap_params(_d(P), _d(_f64(g)), _d(m), _d(v), _d(S), int(t_new), lr, b1, b2, o["b1s"], o["b2s"],
+    _load().orc_soap_params(_hyper(P), _d(P), _d(_f64(g)), _d(m), _d(v), _d(S), int(t_new), lr, b1, b2, o["b1s"],
+                            o["b2s"],
                             o["bshamp"], int(o["freq"]), eps)
 
 
@@ -337,7 +355,7 @@ def encode_soap(image, state: State, soap_state, n_iters, *, lam, seed, lr=1e-2,
     _, H, W = image.shape
     loss = np.zeros(n_iters)
     step = ctypes.c_int64(state.step)
-    _load().orc_encode_soap(H, W, _d(image), _d(state.latents), _d(state.params), _d(state.m_lat), _d(state.v_lat),
+    _load().orc_encode_soap(H, W, _hyper(state.params), _d(image), _d(state.latents), _d(state.params), _d(state.m_lat), _d(state.v_lat),
                             _d(state.m_par), _d(state.v_par), _d(soap_state), ctypes.byref(step), n_iters, seed, lam,
                             lr, b1, b2, o["b1s"], o["b2s"], o["bshamp"], int(o["freq"]), eps, _d(loss))
     state.step = step.value

@@ -25,6 +25,12 @@
  *   - hard quantisation  Q = rint                                            [Sec. IV-C, Eq. 12]
  *   - integer decode ARM and integer Laplace CDF (16-bit probabilities)       [Sec. III-A2: integer,
  *     cross-platform decoding motivates it; the fixed-point format is this project's reading]
+ *   - optional hyperlatent grids (`hyper` = 1)                                 [Sec. III-A3, Eq. 6]:
+ *     three more grids at 1/16, 1/32, 1/64 of the image (b = 4, L_h = L = 7, Table II, small
+ *     images), entropy coded by the same ARM (spatial context only, f = 0), read by the IFCEs of
+ *     grids 0..2 as three more nearest-neighbour inputs, never by the upsampling or the synthesis.
+ *     Their latents follow the main grids in the latent vector; the IFCE weights of the extra
+ *     inputs follow the 1415 main parameters as one block [grid k = 0..2][output o][hyper grid q].
  *
  * Parity status: the spatial context pattern, the IFCE width F = 4, the upsampling filter form,
  * the initialisation and the integer decode format are readings of a paper that leaves them open;
@@ -57,6 +63,8 @@
 #define LOGB_MIN (-5.0)
 #define LOGB_MAX (5.0)
 #define P_MIN (1.0 / 65536.0)
+#define NH 3          /* hyperlatent grids                                                */
+#define HB 4          /* the largest hyperlatent grid is 1/2^HB of the image               */
 
 /* Flat parameter vector, all matrices row-major [out][in]. */
 enum {
@@ -66,7 +74,9 @@ enum {
     O_UP = 756,
     O_SYN_W1 = 780, O_SYN_B1 = 1060, O_SYN_W2 = 1100, O_SYN_B2 = 1220, O_SYN_WS = 1223, O_SYN_BS = 1244,
     O_CV1_W = 1247, O_CV1_B = 1328, O_CV2_W = 1331, O_CV2_B = 1412,
-    N_PARAMS = 1415
+    N_PARAMS = 1415,
+    O_IFH = N_PARAMS,                  /* IFCE weights of the hyperlatent inputs [NIFCE][NF][NH] */
+    N_PARAMS_H = N_PARAMS + NIFCE * NF * NH
 };
 static const int IF_W[NIFCE] = {O_IF0_W, O_IF1_W, O_IF2_W};
 static const int IF_B[NIFCE] = {O_IF0_B, O_IF1_B, O_IF2_B};
@@ -75,34 +85,39 @@ static const int IF_B[NIFCE] = {O_IF0_B, O_IF1_B, O_IF2_B};
 static const int CTX_DY[NCTX] = {0, -1, -1, -1, 0, -2, -1, -1, -2, -2, -2, -2, 0, -3, -1, -1};
 static const int CTX_DX[NCTX] = {-1, 0, -1, 1, -2, 0, -2, 2, -1, 1, -2, 2, -3, 0, -3, 3};
 
+/* Grids 0..NG-1 are the latent grids; with hyperlatents (nh = NH) grids NG..NG+NH-1 are the
+ * hyperlatent grids, grid NG + q with the shape of latent grid HB + q. */
 typedef struct {
-    int H, W;
-    int h[NG], w[NG];
-    int64_t off[NG + 1];
+    int H, W, nh;
+    int h[NG + NH], w[NG + NH];
+    int64_t off[NG + NH + 1];
 } geom_t;
+#define NGT(g) (NG + (g)->nh)
 
-static void geom_init(geom_t* g, int H, int W) {
+static void geom_init(geom_t* g, int H, int W, int hyper) {
     g->H = H;
     g->W = W;
+    g->nh = hyper ? NH : 0;
     g->off[0] = 0;
-    for (int k = 0; k < NG; ++k) {
-        g->h[k] = (H + (1 << k) - 1) >> k; /* ceil(H / 2^k) */
-        g->w[k] = (W + (1 << k) - 1) >> k;
+    for (int k = 0; k < NG + g->nh; ++k) {
+        const int s = k < NG ? k : HB + (k - NG);
+        g->h[k] = (H + (1 << s) - 1) >> s; /* ceil(H / 2^s) */
+        g->w[k] = (W + (1 << s) - 1) >> s;
         g->off[k + 1] = g->off[k] + (int64_t)g->h[k] * g->w[k];
     }
 }
 
-int orc_param_count(void) { return N_PARAMS; }
+int orc_param_count(int hyper) { return hyper ? N_PARAMS_H : N_PARAMS; }
 
-int64_t orc_latent_count(int H, int W) {
+int64_t orc_latent_count(int H, int W, int hyper) {
     geom_t g;
-    geom_init(&g, H, W);
-    return g.off[NG];
+    geom_init(&g, H, W, hyper);
+    return g.off[NGT(&g)];
 }
 
 void orc_grid_shape(int H, int W, int k, int* hk, int* wk) {
     geom_t g;
-    geom_init(&g, H, W);
+    geom_init(&g, H, W, k >= NG);
     *hk = g.h[k];
     *wk = g.w[k];
 }
@@ -254,7 +269,8 @@ static void arm_backward(const double* P, const arm_act_t* A, double dmu, double
 static int ifce_inputs(int k) { return (k < NIFCE && k < NG - 1) ? NG - k - 1 : 0; }
 
 /* Builds c_i = concat(s_i, f_i) for latent (k, r, c) of the relaxed latents yt.  r_i holds the
- * nearest-neighbour co-located values of the coarser grids k+1..L-1 (Sec. III-A2). */
+ * nearest-neighbour co-located values of the coarser grids k+1..L-1 (Sec. III-A2), then, with
+ * hyperlatents, those of the hyperlatent grids (Sec. III-A3); rvec has room for NG + NH values. */
 static void build_context(const geom_t* g, const double* P, const double* yt, int k, int r, int c,
                           double* ctx, double* rvec) {
     const double* yk = yt + g->off[k];
@@ -271,11 +287,20 @@ static void build_context(const geom_t* g, const double* P, const double* yt, in
         if (cc > g->w[gj] - 1) cc = g->w[gj] - 1;
         rvec[j] = yt[g->off[gj] + (int64_t)rr * g->w[gj] + cc];
     }
+    const int nh = nin > 0 ? g->nh : 0;
+    for (int q = 0; q < nh; ++q) {
+        int gq = NG + q, sh = HB + q - k;
+        int rr = r >> sh, cc = c >> sh;
+        if (rr > g->h[gq] - 1) rr = g->h[gq] - 1;
+        if (cc > g->w[gq] - 1) cc = g->w[gq] - 1;
+        rvec[nin + q] = yt[g->off[gq] + (int64_t)rr * g->w[gq] + cc];
+    }
     for (int o = 0; o < NF; ++o) {
         double acc = 0.0;
         if (nin > 0) {
             acc = P[IF_B[k] + o];
             for (int j = 0; j < nin; ++j) acc += P[IF_W[k] + o * nin + j] * rvec[j];
+            for (int q = 0; q < nh; ++q) acc += P[O_IFH + (k * NF + o) * NH + q] * rvec[nin + q];
         }
         ctx[NCTX + o] = acc;
     }
@@ -497,24 +522,24 @@ static double relax_one(const relax_t* R, double y, int64_t i, double* jac) {
     return v;
 }
 
-static double run_forward(int H, int W, const double* img, const double* y, const double* P,
+static double run_forward(int H, int W, int hyper, const double* img, const double* y, const double* P,
                           const relax_t* R, double lambda, fwd_t* F, double* rate_out, double* mse_out) {
-    geom_init(&F->g, H, W);
+    geom_init(&F->g, H, W, hyper);
     const geom_t* g = &F->g;
-    int64_t N = g->off[NG], HW = (int64_t)H * W;
+    int64_t N = g->off[NGT(g)], HW = (int64_t)H * W;
     F->yt = (double*)malloc(sizeof(double) * N);
     F->mu = (double*)malloc(sizeof(double) * N);
     F->logb = (double*)malloc(sizeof(double) * N);
     F->bits = (double*)malloc(sizeof(double) * N);
     for (int64_t i = 0; i < N; ++i) F->yt[i] = relax_one(R, y[i], i, NULL);
-    /* entropy model: Eqs. 2-5, 9, 11 */
-    for (int k = 0; k < NG; ++k) {
+    /* entropy model: Eqs. 2-5, 9, 11 (every grid, hyperlatent grids included) */
+    for (int k = 0; k < NGT(g); ++k) {
 #pragma omp parallel for schedule(static)
         for (int r = 0; r < g->h[k]; ++r)
             for (int c = 0; c < g->w[k]; ++c) {
                 int64_t i = g->off[k] + (int64_t)r * g->w[k] + c;
                 arm_act_t A;
-                double rv[NG];
+                double rv[NG + NH];
                 build_context(g, P, F->yt, k, r, c, A.c, rv);
                 arm_forward(P, &A);
                 double p = orc_laplace_prob(F->yt[i], A.mu, A.b, NULL, NULL);
@@ -562,14 +587,14 @@ static double run_forward(int H, int W, const double* img, const double* y, cons
     return mse + lambda * rate / (double)HW;
 }
 
-double orc_forward(int H, int W, const double* img, const double* y, const double* P, int mode,
+double orc_forward(int H, int W, int hyper, const double* img, const double* y, const double* P, int mode,
                    uint64_t seed, int64_t t, double sigma, double temp, double lambda, double* rate_out,
                    double* mse_out, double* mu_out, double* logb_out, double* bits_out, double* xhat_out) {
     fwd_t F;
     memset(&F, 0, sizeof(F));
     relax_t R = {mode, seed, t, sigma, temp};
-    double loss = run_forward(H, W, img, y, P, &R, lambda, &F, rate_out, mse_out);
-    int64_t N = F.g.off[NG], HW = (int64_t)H * W;
+    double loss = run_forward(H, W, hyper, img, y, P, &R, lambda, &F, rate_out, mse_out);
+    int64_t N = F.g.off[NGT(&F.g)], HW = (int64_t)H * W;
     if (mu_out) memcpy(mu_out, F.mu, sizeof(double) * N);
     if (logb_out) memcpy(logb_out, F.logb, sizeof(double) * N);
     if (bits_out) memcpy(bits_out, F.bits, sizeof(double) * N);
@@ -581,17 +606,17 @@ double orc_forward(int H, int W, const double* img, const double* y, const doubl
 /* Loss and its gradient with respect to the continuous latents y and the parameters:
  * dL/dy = dL/dy~ * dy~/dy (1 for the additive proxy, 0 under hard rounding, the product of the
  * two soft-rounding derivatives for Eq. 13). */
-double orc_loss_grad(int H, int W, const double* img, const double* y, const double* P, int mode,
+double orc_loss_grad(int H, int W, int hyper, const double* img, const double* y, const double* P, int mode,
                      uint64_t seed, int64_t t, double sigma, double temp, double lambda, double* rate_out,
                      double* mse_out, double* gy, double* gP) {
     fwd_t F;
     memset(&F, 0, sizeof(F));
     relax_t R = {mode, seed, t, sigma, temp};
-    double loss = run_forward(H, W, img, y, P, &R, lambda, &F, rate_out, mse_out);
+    double loss = run_forward(H, W, hyper, img, y, P, &R, lambda, &F, rate_out, mse_out);
     const geom_t* g = &F.g;
-    int64_t N = g->off[NG], HW = (int64_t)H * W;
+    int64_t N = g->off[NGT(g)], HW = (int64_t)H * W;
     double* gyt = (double*)calloc(N, sizeof(double));
-    for (int q = 0; q < N_PARAMS; ++q) gP[q] = 0.0;
+    for (int q = 0; q < orc_param_count(hyper); ++q) gP[q] = 0.0;
 
     /* distortion: D = mean (xh - x)^2 */
     double* dxh = (double*)malloc(sizeof(double) * NCH * HW);
@@ -664,10 +689,11 @@ double orc_loss_grad(int H, int W, const double* img, const double* y, const dou
     /* entropy-model adjoint: per-latent contributions computed in parallel, scattered serially */
     double dbits = lambda / (double)HW;
     const int NARM = O_UP; /* ARM + IFCE parameter block */
-    for (int k = 0; k < NG; ++k) {
+    const int RV = NG + NH; /* room for the IFCE inputs of one latent */
+    for (int k = 0; k < NGT(g); ++k) {
         int h = g->h[k], w = g->w[k];
         double* dcs = (double*)malloc(sizeof(double) * (size_t)h * w * AIN);
-        double* rvs = (double*)malloc(sizeof(double) * (size_t)h * w * NG);
+        double* rvs = (double*)malloc(sizeof(double) * (size_t)h * w * RV);
         double* ddir = (double*)malloc(sizeof(double) * (size_t)h * w);
         double* rowa = (double*)calloc((size_t)h * NARM, sizeof(double));
 #pragma omp parallel for schedule(static)
@@ -676,7 +702,7 @@ double orc_loss_grad(int H, int W, const double* img, const double* y, const dou
             for (int c = 0; c < w; ++c) {
                 int64_t li = (int64_t)r * w + c, i = g->off[k] + li;
                 arm_act_t A;
-                double* rv = rvs + li * NG;
+                double* rv = rvs + li * RV;
                 build_context(g, P, F.yt, k, r, c, A.c, rv);
                 arm_forward(P, &A);
                 double dpdy, dpdlb;
@@ -702,7 +728,18 @@ double orc_loss_grad(int H, int W, const double* img, const double* y, const dou
                     const double* df = dc + NCTX;
                     for (int o = 0; o < NF; ++o) {
                         gP[IF_B[k] + o] += df[o];
-                        for (int j = 0; j < nin; ++j) gP[IF_W[k] + o * nin + j] += df[o] * rvs[li * NG + j];
+                        for (int j = 0; j < nin; ++j) gP[IF_W[k] + o * nin + j] += df[o] * rvs[li * RV + j];
+                        for (int q = 0; q < g->nh; ++q)
+                            gP[O_IFH + (k * NF + o) * NH + q] += df[o] * rvs[li * RV + nin + q];
+                    }
+                    for (int q = 0; q < g->nh; ++q) {
+                        int gq = NG + q, sh = HB + q - k;
+                        int rr = r >> sh, cc = c >> sh;
+                        if (rr > g->h[gq] - 1) rr = g->h[gq] - 1;
+                        if (cc > g->w[gq] - 1) cc = g->w[gq] - 1;
+                        double acc = 0.0;
+                        for (int o = 0; o < NF; ++o) acc += P[O_IFH + (k * NF + o) * NH + q] * df[o];
+                        gyt[g->off[gq] + (int64_t)rr * g->w[gq] + cc] += acc;
                     }
                     for (int j = 0; j < nin; ++j) {
                         int gj = k + 1 + j, sh = gj - k;
@@ -750,22 +787,24 @@ void orc_adam(int64_t n, double* p, const double* g, double* m, double* v, int64
 
 /* n_iters encoder iterations: loss+gradient at step t (noise keyed by t), then Adam on latents
  * and parameters.  Per-iteration loss, rate and mse (before the update) are reported. */
-void orc_encode(int H, int W, const double* img, double* y, double* P, double* m_y, double* v_y,
+void orc_encode(int H, int W, int hyper, const double* img, double* y, double* P, double* m_y, double* v_y,
                 double* m_p, double* v_p, int64_t* step, int n_iters, uint64_t seed, double lambda,
                 double lr, double b1, double b2, double eps, double* loss_out, double* rate_out,
                 double* mse_out) {
-    int64_t N = orc_latent_count(H, W);
+    int64_t N = orc_latent_count(H, W, hyper);
+    const int NP = orc_param_count(hyper);
     double* gy = (double*)malloc(sizeof(double) * N);
-    double gP[N_PARAMS];
+    double gP[N_PARAMS_H];
     for (int it = 0; it < n_iters; ++it) {
         double rate, mse;
-        double loss = orc_loss_grad(H, W, img, y, P, MODE_NOISE, seed, *step, 0.0, 1.0, lambda, &rate, &mse, gy, gP);
+        double loss = orc_loss_grad(H, W, hyper, img, y, P, MODE_NOISE, seed, *step, 0.0, 1.0, lambda, &rate, &mse,
+                                    gy, gP);
         if (loss_out) loss_out[it] = loss;
         if (rate_out) rate_out[it] = rate;
         if (mse_out) mse_out[it] = mse;
         *step += 1;
         orc_adam(N, y, gy, m_y, v_y, *step, lr, b1, b2, eps);
-        orc_adam(N_PARAMS, P, gP, m_p, v_p, *step, lr, b1, b2, eps);
+        orc_adam(NP, P, gP, m_p, v_p, *step, lr, b1, b2, eps);
     }
     free(gy);
 }
@@ -777,14 +816,15 @@ void orc_encode(int H, int W, const double* img, double* y, double* P, double* m
  *   hard-round stage, t >= n_main:  y~ = rint(y), latents frozen (no update, moments kept),
  *     Adam on the parameters at lr_min.
  * The Adam step count is t + 1 in both stages. */
-void orc_encode_schedule(int H, int W, const double* img, double* y, double* P, double* m_y, double* v_y,
+void orc_encode_schedule(int H, int W, int hyper, const double* img, double* y, double* P, double* m_y, double* v_y,
                          double* m_p, double* v_p, int64_t* step, int n_iters, uint64_t seed, double lambda,
                          double lr_max, double lr_min, double sigma0, double sigma1, double temp0, double temp1,
                          int64_t n_main, double b1, double b2, double eps, double* loss_out, double* rate_out,
                          double* mse_out) {
-    int64_t N = orc_latent_count(H, W);
+    int64_t N = orc_latent_count(H, W, hyper);
+    const int NP = orc_param_count(hyper);
     double* gy = (double*)malloc(sizeof(double) * N);
-    double gP[N_PARAMS];
+    double gP[N_PARAMS_H];
     for (int it = 0; it < n_iters; ++it) {
         const int64_t t = *step;
         const int main_stage = t < n_main;
@@ -792,14 +832,14 @@ void orc_encode_schedule(int H, int W, const double* img, double* y, double* P, 
         const double sigma = sigma0 + (sigma1 - sigma0) * f, temp = temp0 + (temp1 - temp0) * f;
         const double lr = main_stage ? lr_min + 0.5 * (lr_max - lr_min) * (1.0 + cos(M_PI * f)) : lr_min;
         double rate, mse;
-        double loss = orc_loss_grad(H, W, img, y, P, main_stage ? MODE_SOFTROUND : MODE_HARD, seed, t, sigma,
-                                    temp, lambda, &rate, &mse, gy, gP);
+        double loss = orc_loss_grad(H, W, hyper, img, y, P, main_stage ? MODE_SOFTROUND : MODE_HARD, seed, t,
+                                    sigma, temp, lambda, &rate, &mse, gy, gP);
         if (loss_out) loss_out[it] = loss;
         if (rate_out) rate_out[it] = rate;
         if (mse_out) mse_out[it] = mse;
         *step += 1;
         if (main_stage) orc_adam(N, y, gy, m_y, v_y, *step, lr, b1, b2, eps);
-        orc_adam(N_PARAMS, P, gP, m_p, v_p, *step, lr, b1, b2, eps);
+        orc_adam(NP, P, gP, m_p, v_p, *step, lr, b1, b2, eps);
     }
     free(gy);
 }
@@ -855,12 +895,12 @@ static int64_t floor_shift8(int64_t v) { return v >> 8; } /* arithmetic shift = 
 static int64_t q8(float w) { return (int64_t)rint((double)w * 256.0); }
 
 /* Integer ARM for every latent of the hard-quantised grids q; writes mu_q, logb_q, P_q16. */
-void orc_decode_probs(int H, int W, const int32_t* q, const float* Pf, int32_t* mu_out,
+void orc_decode_probs(int H, int W, int hyper, const int32_t* q, const float* Pf, int32_t* mu_out,
                       int32_t* logb_out, uint32_t* prob_out) {
     build_tables();
     geom_t g;
-    geom_init(&g, H, W);
-    for (int k = 0; k < NG; ++k) {
+    geom_init(&g, H, W, hyper);
+    for (int k = 0; k < NGT(&g); ++k) {
         int nin = ifce_inputs(k);
         for (int r = 0; r < g.h[k]; ++r)
             for (int c = 0; c < g.w[k]; ++c) {
@@ -884,6 +924,14 @@ void orc_decode_probs(int H, int W, const int32_t* q, const float* Pf, int32_t* 
                             if (cc > g.w[gj] - 1) cc = g.w[gj] - 1;
                             acc += q8(Pf[IF_W[k] + o * nin + j]) *
                                    (int64_t)q[g.off[gj] + (int64_t)rr * g.w[gj] + cc];
+                        }
+                        for (int hq = 0; hq < g.nh; ++hq) {
+                            int gq = NG + hq, sh = HB + hq - k;
+                            int rr = r >> sh, cc = c >> sh;
+                            if (rr > g.h[gq] - 1) rr = g.h[gq] - 1;
+                            if (cc > g.w[gq] - 1) cc = g.w[gq] - 1;
+                            acc += q8(Pf[O_IFH + (k * NF + o) * NH + hq]) *
+                                   (int64_t)q[g.off[gq] + (int64_t)rr * g.w[gq] + cc];
                         }
                     }
                     ctx[NCTX + o] = acc;
@@ -922,19 +970,19 @@ void orc_decode_probs(int H, int W, const int32_t* q, const float* Pf, int32_t* 
 
 /* Decoder reconstruction from hard-quantised latents: upsampling + synthesis in FP64, x^ clamped
  * to [0, 1] (Sec. III-B). */
-void orc_decode_image(int H, int W, const int32_t* q, const float* Pf, double* img_out) {
-    int64_t N = orc_latent_count(H, W);
+void orc_decode_image(int H, int W, int hyper, const int32_t* q, const float* Pf, double* img_out) {
+    int64_t N = orc_latent_count(H, W, hyper);
     double* y = (double*)malloc(sizeof(double) * N);
-    double P[N_PARAMS];
+    double P[N_PARAMS_H];
     for (int64_t i = 0; i < N; ++i) y[i] = (double)q[i];
-    for (int j = 0; j < N_PARAMS; ++j) P[j] = (double)Pf[j];
+    for (int j = 0; j < orc_param_count(hyper); ++j) P[j] = (double)Pf[j];
     double rate, mse;
     int64_t HW = (int64_t)H * W;
     double* zero = (double*)calloc(NCH * HW, sizeof(double));
     fwd_t F;
     memset(&F, 0, sizeof(F));
     relax_t R = {MODE_IDENTITY, 0, 0, 0.0, 1.0};
-    run_forward(H, W, zero, y, P, &R, 0.0, &F, &rate, &mse);
+    run_forward(H, W, hyper, zero, y, P, &R, 0.0, &F, &rate, &mse);
     for (int64_t q2 = 0; q2 < NCH * HW; ++q2) img_out[q2] = fmin(fmax(F.xh[q2], 0.0), 1.0);
     fwd_free(&F);
     free(zero);
@@ -1066,16 +1114,17 @@ static void small_gemm(int m, int n, int k, const double* A, int ta, const doubl
 /* One optimizer step of the network parameters at Adam count t_new (the SOAP step is t_new - 1):
  * SOAP on the two-dimensional blocks (b1s, b2s, bshamp, freq), Adam (b1, b2) on the rest, both
  * with learning rate lr and eps. */
-void orc_soap_params(double* P, const double* g, double* m, double* v, double* S, int64_t t_new, double lr,
-                     double b1, double b2, double b1s, double b2s, double bshamp, int freq, double eps) {
-    int is_soap[N_PARAMS];
-    for (int i = 0; i < N_PARAMS; ++i) is_soap[i] = 0;
+void orc_soap_params(int hyper, double* P, const double* g, double* m, double* v, double* S, int64_t t_new,
+                     double lr, double b1, double b2, double b1s, double b2s, double bshamp, int freq, double eps) {
+    const int NP = orc_param_count(hyper);
+    int is_soap[N_PARAMS_H];
+    for (int i = 0; i < NP; ++i) is_soap[i] = 0;
     for (int b = 0; b < N_SOAP; ++b)
         for (int i = 0; i < SOAP_M[b] * SOAP_N[b]; ++i) is_soap[SOAP_OFF[b] + i] = 1;
     /* Adam on the one-dimensional blocks */
     {
         const double bc1 = 1.0 - pow(b1, (double)t_new), bc2 = 1.0 - pow(b2, (double)t_new);
-        for (int i = 0; i < N_PARAMS; ++i) {
+        for (int i = 0; i < NP; ++i) {
             if (is_soap[i]) continue;
             m[i] = b1 * m[i] + (1.0 - b1) * g[i];
             v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
@@ -1142,20 +1191,21 @@ void orc_soap_params(double* P, const double* g, double* m, double* v, double* S
 
 /* n_iters encoder iterations with the uniform proxy (as orc_encode), Adam on the latents and
  * SOAP / Adam on the network parameters (orc_soap_params). */
-void orc_encode_soap(int H, int W, const double* img, double* y, double* P, double* m_y, double* v_y,
+void orc_encode_soap(int H, int W, int hyper, const double* img, double* y, double* P, double* m_y, double* v_y,
                      double* m_p, double* v_p, double* S, int64_t* step, int n_iters, uint64_t seed, double lambda,
                      double lr, double b1, double b2, double b1s, double b2s, double bshamp, int freq, double eps,
                      double* loss_out) {
-    int64_t N = orc_latent_count(H, W);
+    int64_t N = orc_latent_count(H, W, hyper);
     double* gy = (double*)malloc(sizeof(double) * N);
-    double gP[N_PARAMS];
+    double gP[N_PARAMS_H];
     for (int it = 0; it < n_iters; ++it) {
         double rate, mse;
-        double loss = orc_loss_grad(H, W, img, y, P, MODE_NOISE, seed, *step, 0.0, 1.0, lambda, &rate, &mse, gy, gP);
+        double loss = orc_loss_grad(H, W, hyper, img, y, P, MODE_NOISE, seed, *step, 0.0, 1.0, lambda, &rate, &mse,
+                                    gy, gP);
         if (loss_out) loss_out[it] = loss;
         *step += 1;
         orc_adam(N, y, gy, m_y, v_y, *step, lr, b1, b2, eps);
-        orc_soap_params(P, gP, m_p, v_p, S, *step, lr, b1, b2, b1s, b2s, bshamp, freq, eps);
+        orc_soap_params(hyper, P, gP, m_p, v_p, S, *step, lr, b1, b2, b1s, b2s, bshamp, freq, eps);
     }
     free(gy);
 }

@@ -40,16 +40,25 @@ def param_offsets():
 PARAM_OFFSETS, N_PARAMS = param_offsets()
 assert N_PARAMS == 1415
 
+# Hyperlatent grids (optional, Sec. III-A3): three more grids at 1/16, 1/32, 1/64 of the image whose
+# latents follow the main ones; the IFCE weights of their inputs follow the 1415 main parameters as
+# one block [grid k = 0..2][output o = 0..3][hyperlatent grid q = 0..2].
+N_HYPER_GRIDS = 3
+HYPER_BLOCK = ("ifce_h.w", (3, 4, 3))
+N_PARAMS_H = N_PARAMS + 36
+
 # Keys cubic kernel (a = -0.75) sampled at distances 1.75, 1.25, 0.75, 0.25: exact binary fractions.
 BICUBIC_TAPS = (-0.03515625, -0.10546875, 0.26171875, 0.87890625)
 
 
-def grid_shapes(H: int, W: int, L: int = N_GRIDS):
-    return [(-(-H // (1 << k)), -(-W // (1 << k))) for k in range(L)]
+def grid_shapes(H: int, W: int, L: int = N_GRIDS, hyper: bool = False):
+    """Latent grid shapes; with hyper, then the hyperlatent grids (shapes of grids 4, 5, 6)."""
+    main = [(-(-H // (1 << k)), -(-W // (1 << k))) for k in range(L)]
+    return main + ([(-(-H // (1 << k)), -(-W // (1 << k))) for k in range(4, 4 + N_HYPER_GRIDS)] if hyper else [])
 
 
-def latent_count(H: int, W: int) -> int:
-    return sum(h * w for h, w in grid_shapes(H, W))
+def latent_count(H: int, W: int, hyper: bool = False) -> int:
+    return sum(h * w for h, w in grid_shapes(H, W, hyper=hyper))
 
 
 def block(params: np.ndarray, name: str) -> np.ndarray:
@@ -79,25 +88,34 @@ def image(H: int, W: int, seed: int, texture_sigma: float = 0.0) -> np.ndarray:
     return out.astype(np.float32)
 
 
-def initial_state(H: int, W: int, seed: int):
+def initial_state(H: int, W: int, seed: int, hyper: bool = False):
     """Encoder starting point: latents N(0, 0.01^2); hidden-layer weights U(+-1/sqrt(fan_in));
-    biases, last layers, stabilizers and residual convs zero; upsampling taps bicubic.
-    Returns (latents float32 [N], params float32 [1415])."""
+    biases, last layers, stabilizers and residual convs zero; upsampling taps bicubic.  With
+    hyper, the hyperlatents and the IFCE weights of their inputs are drawn the same way (an IFCE's
+    fan-in then counts its hyperlatent inputs too).
+    Returns (latents float32 [N], params float32 [1415, or 1451 with hyper])."""
     rng = np.random.default_rng(seed)
     lat = rng.normal(0.0, 0.01, latent_count(H, W)).astype(np.float32)
     p = np.zeros(N_PARAMS, dtype=np.float64)
     for name in ("arm.w1", "arm.w2", "ifce0.w", "ifce1.w", "ifce2.w", "syn.w1"):
         o, shape = PARAM_OFFSETS[name]
         n = int(np.prod(shape))
-        bound = 1.0 / np.sqrt(shape[1])
+        fan = shape[1] + (N_HYPER_GRIDS if hyper and name.startswith("ifce") else 0)
+        bound = 1.0 / np.sqrt(fan)
         p[o:o + n] = rng.uniform(-bound, bound, n)
     block(p, "up.taps")[:] = BICUBIC_TAPS
+    if hyper:
+        lat = np.concatenate([lat, rng.normal(0.0, 0.01, latent_count(H, W, True) - lat.shape[0]).astype(np.float32)])
+        fans = np.repeat([6 + 3, 5 + 3, 4 + 3], 12)
+        p = np.concatenate([p, rng.uniform(-1.0, 1.0, 36) / np.sqrt(fans)])
     return lat, p.astype(np.float32)
 
 
-def random_state(H: int, W: int, seed: int, latent_sigma: float = 1.5, scale: float = 1.0):
+def random_state(H: int, W: int, seed: int, latent_sigma: float = 1.5, scale: float = 1.0, hyper: bool = False):
     """A mid-training-like state for parity tests: every block random and non-zero so that
-    every gradient path is exercised.  Returns (latents float32, params float32)."""
+    every gradient path is exercised.  Returns (latents float32, params float32); with hyper the
+    hyperlatents and their IFCE weights are appended (drawn after the main state, which is
+    therefore the same with and without them)."""
     rng = np.random.default_rng(seed)
     lat = rng.normal(0.0, latent_sigma, latent_count(H, W)).astype(np.float32)
     p = np.zeros(N_PARAMS, dtype=np.float64)
@@ -115,13 +133,17 @@ def random_state(H: int, W: int, seed: int, latent_sigma: float = 1.5, scale: fl
             p[o:o + n] = rng.uniform(-bound, bound, n) * scale
     # keep the Laplace log-scale away from its clamp and the mean near the latents
     block(p, "arm.b3")[:] = (0.0, 0.3)
+    if hyper:
+        lat = np.concatenate([lat, rng.normal(0.0, latent_sigma, latent_count(H, W, True) - lat.shape[0])
+                              .astype(np.float32)])
+        p = np.concatenate([p, rng.uniform(-0.4, 0.4, 36) * scale])
     return lat, p.astype(np.float32)
 
 
-def quantized_latents(H: int, W: int, seed: int, sigma: float = 3.0) -> np.ndarray:
+def quantized_latents(H: int, W: int, seed: int, sigma: float = 3.0, hyper: bool = False) -> np.ndarray:
     """Integer latents for decode tests (int32), Laplace-like spread."""
     rng = np.random.default_rng(seed)
-    return np.rint(rng.laplace(0.0, sigma, latent_count(H, W))).astype(np.int32)
+    return np.rint(rng.laplace(0.0, sigma, latent_count(H, W, hyper))).astype(np.int32)
 
 
 BATCH_SIZES = [(256, 256), (512, 768), (768, 512), (1024, 1024), (1536, 1024)]

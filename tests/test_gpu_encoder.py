@@ -23,9 +23,9 @@ def test_warmup_keeps_the_best_candidates(cc):
     alone = {}
     for c in range(3):
         lat, par = inputs.initial_state(H, W, seed=5 + c)
-        st = cc.EncoderState(torch.tensor(lat, device="cuda"), torch.tensor(par, device="cuda"))
+        st = cc.EncoderState(torch.tensor(lat, device="cuda"), torch.tensor(par, device="cuda"), soap=True)
         hp = cc.hparams_schedule(lam=LAM, n_main=1 << 40, lr=1e-2, lr_min=1e-2, sigma0=0.22, sigma1=0.22,
-                                 temp0=0.35, temp1=0.35, seed=5 + 1000 + c)
+                                 temp0=0.35, temp1=0.35, seed=5 + 1000 + c, soap=True)
         cc.encode_step(img, st, 12, H=H, W=W, hp=hp, ws=cc.workspace(H, W))
         alone[c] = (st, hp)
     first = sorted(range(3), key=lambda c: (encoder.rd_hard(img, alone[c][0], LAM)[0], c))

@@ -39,9 +39,9 @@ def P(params: torch.Tensor, name: str) -> torch.Tensor:
     return params[o:o + int(np.prod(shape))].reshape(shape)
 
 
-def split_grids(lat: torch.Tensor, H: int, W: int):
+def split_grids(lat: torch.Tensor, H: int, W: int, hyper: bool = False):
     out, o = [], 0
-    for h, w in inputs.grid_shapes(H, W):
+    for h, w in inputs.grid_shapes(H, W, hyper=hyper):
         out.append(lat[o:o + h * w].reshape(h, w))
         o += h * w
     return out
@@ -73,13 +73,16 @@ def laplace_mass(y, mu, b):
 
 
 def forward(image: torch.Tensor, yt_flat: torch.Tensor, params: torch.Tensor, lam: float):
-    """Returns (loss, rate_bits, mse, mu, logb) from already-relaxed latents yt_flat."""
+    """Returns (loss, rate_bits, mse, mu, logb) from already-relaxed latents yt_flat.  A parameter
+    vector of 1451 values carries the hyperlatent IFCE block: the latents then hold three
+    hyperlatent grids after the main ones (Sec. III-A3)."""
     _, H, W = image.shape
-    grids = split_grids(yt_flat, H, W)
-    shapes = inputs.grid_shapes(H, W)
+    hyper = params.shape[0] == inputs.N_PARAMS_H
+    grids = split_grids(yt_flat, H, W, hyper)
+    shapes = inputs.grid_shapes(H, W, hyper=hyper)
     rate = yt_flat.new_zeros(())
     mus, lbs = [], []
-    for k in range(L):
+    for k in range(len(shapes)):
         Y = grids[k]
         h, w = shapes[k]
         Yp = F.pad(Y[None, None], (3, 3, 3, 0))[0, 0]
@@ -94,6 +97,16 @@ def forward(image: torch.Tensor, yt_flat: torch.Tensor, params: torch.Tensor, la
                 rs.append(grids[gj][ri][:, ci])
             r = torch.stack(rs, dim=-1)
             f = r @ P(params, f"ifce{k}.w").T + P(params, f"ifce{k}.b")
+            if hyper:  # the hyperlatent grids (shapes of grids 4, 5, 6) as three more inputs
+                hs = []
+                for q in range(inputs.N_HYPER_GRIDS):
+                    sh = 4 + q - k
+                    hj, wj = shapes[L + q]
+                    ri = torch.clamp(torch.arange(h) >> sh, max=hj - 1)
+                    ci = torch.clamp(torch.arange(w) >> sh, max=wj - 1)
+                    hs.append(grids[L + q][ri][:, ci])
+                wh = params[inputs.N_PARAMS:].reshape(3, 4, 3)[k]
+                f = f + torch.stack(hs, dim=-1) @ wh.T
         else:
             f = s.new_zeros(h, w, 4)
         c = torch.cat([s, f], dim=-1)

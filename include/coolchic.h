@@ -64,6 +64,13 @@ typedef struct {
     int32_t n_resconv;  /* [2]                                                     */
     int32_t up_taps;    /* [8]                                                     */
     int32_t stabilizer; /* [1]                                                     */
+    int32_t hyper_grids;/* [0] or 3: hyperlatent grids (Sec. III-A3, Eq. 6; Table II: 1/16 to
+                           1/64 for small images).  They follow the latent grids in the latent
+                           vector (grid 7 + q has the shape of grid 4 + q), are coded by the same
+                           ARM from their spatial context, and are read by the IFCEs of grids 0..2
+                           as three more nearest-neighbour inputs; the upsampling and the
+                           synthesis never see them.  The IFCE weights of those inputs follow
+                           the 1415 parameters as the block ifce_h.w [3][4][3] (1451 in all). */
 } cc_arch_t;
 
 /* Encoder hyper-parameters.  lambda weighs the rate in bits per pixel (Eq. 10 with R divided by
@@ -130,12 +137,14 @@ typedef struct {
  * NULL pointer or a size outside 1..16384. */
 int coolchic_arch_init(cc_arch_t* arch, int32_t H, int32_t W);
 
-/* Number of latents (sum over grids of h_k * w_k) and of parameters (1415); -1 on a bad arch. */
+/* Number of latents (sum over grids of h_k * w_k, hyperlatent grids included) and of parameters
+ * (1415, or 1451 with hyperlatent grids); -1 on a bad arch. */
 int64_t coolchic_latent_count(const cc_arch_t* arch);
 int64_t coolchic_param_count(const cc_arch_t* arch);
 
 /* Parameter block `index` (0-based, in storage order): its name (static string), offset and
- * length in floats.  Returns CC_ERR_ARG past the last block. */
+ * length in floats.  Returns CC_ERR_ARG past the last block.  Block 25, ifce_h.w, exists only
+ * in the parameter vectors of architectures with hyperlatent grids. */
 int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int32_t* length);
 
 /* Seeded initial encoder state, written on the device (the paper does not give its

@@ -62,9 +62,10 @@ int check_arch(const cc_arch_t* a) {
         return fail(CC_ERR_ARG, "image size %d x %d outside 1..16384", a->H, a->W);
     if (a->C != kC || a->L != kL || a->n_ctx != kNCtx || a->ifce_dim != kF || a->ifce_grids != kNIfce ||
         a->arm_hidden != kAH || a->arm_layers != 2 || a->syn_hidden != kSH || a->n_resconv != 2 || a->up_taps != 8 ||
-        a->stabilizer != 1)
+        a->stabilizer != 1 || (a->hyper_grids != 0 && a->hyper_grids != kNH))
         return fail(CC_ERR_UNSUPPORTED, "only the C=3, L=7, ctx 16, F=4 (3 IFCEs), ARM 16x2, synthesis 40, "
-                                        "2 residual convs, 8-tap upsampling, stabilizer-on architecture is built");
+                                        "2 residual convs, 8-tap upsampling, stabilizer-on architecture, with 0 or 3 "
+                                        "hyperlatent grids, is built");
     return CC_OK;
 }
 
@@ -105,9 +106,9 @@ struct Layout {
 size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     Work W;
     std::memset(&W, 0, sizeof(W));
-    W.g = make_geom(a->H, a->W);
+    W.g = make_geom(a->H, a->W, a->hyper_grids);
     const Geom& g = W.g;
-    W.N = g.off[kL];
+    W.N = g.off[kG];
     W.HW = (int64_t)a->H * a->W;
     const int sms = num_sms();
     W.n_cta_arm = arm_grid(W.N);
@@ -126,10 +127,10 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     size_t o_yt = L.take(W.N * F);
     size_t o_dS = L.take(16 * W.N * F);
     size_t o_dR[3];
-    for (int k = 0; k < kNIfce; ++k) o_dR[k] = L.take((size_t)ifce_nin(k) * g.h[k] * g.w[k] * F);
+    for (int k = 0; k < kNIfce; ++k) o_dR[k] = L.take((size_t)(ifce_nin(k) + g.nh) * g.h[k] * g.w[k] * F);
     size_t o_dYd = L.take(W.N * F);
     size_t o_dYsyn = L.take(W.N * F);
-    size_t o_dIf = L.take((size_t)4 * g.h[kNIfce] * g.w[kNIfce] * F);
+    size_t o_dIf = L.take((size_t)(4 + g.nh) * g.h[kNIfce] * g.w[kNIfce] * F);
     size_t o_up[kL] = {0}, o_dup[kL] = {0};
     for (int m = 1; m <= kL - 2; ++m) {
         o_up[m] = L.take((size_t)(kL - 1 - m) * g.h[m] * g.w[m] * F);
@@ -139,13 +140,13 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     size_t o_dt = L.take(3 * W.HW * F);
     size_t o_dz = L.take(6 * W.HW * F);
     size_t o_zd = L.take(6 * W.HW * F);
-    size_t o_ga = L.take((size_t)W.n_cta_arm * po::arm_block * F);
+    size_t o_ga = L.take((size_t)W.n_cta_arm * (g.nh ? po::arm_block_h : po::arm_block) * F);
     size_t o_gs = L.take((size_t)W.n_cta_syn * po::syn_block * F);
     size_t o_gc = L.take((size_t)W.n_cta_conv * po::conv_block * F);
     size_t o_gu = L.take((size_t)6 * kUpMaxCta * 4 * F);
     size_t o_rp = L.take((size_t)W.n_cta_arm * sizeof(double));
     size_t o_sp = L.take((size_t)W.n_cta_conv * sizeof(double));
-    size_t o_gp = L.take(po::total * F);
+    size_t o_gp = L.take(po::total_h * F);
     size_t o_bs = L.take(4 * sizeof(int64_t));
     size_t o_aa = 0, o_as = 0, o_ioi = 0, o_ior = 0;
     if (flags & 1) {
@@ -469,17 +470,18 @@ int coolchic_arch_init(cc_arch_t* a, int32_t H, int32_t W) {
     a->n_resconv = 2;
     a->up_taps = 8;
     a->stabilizer = 1;
+    a->hyper_grids = 0;
     return CC_OK;
 }
 
 int64_t coolchic_latent_count(const cc_arch_t* a) {
     if (check_arch(a)) return -1;
-    return make_geom(a->H, a->W).off[kL];
+    return make_geom(a->H, a->W, a->hyper_grids).off[kG];
 }
 
 int64_t coolchic_param_count(const cc_arch_t* a) {
     if (check_arch(a)) return -1;
-    return po::total;
+    return a->hyper_grids ? po::total_h : po::total;
 }
 
 int coolchic_init_state(const cc_arch_t* arch, uint64_t seed, const cc_state_t* st, void* stream) {
@@ -495,8 +497,10 @@ int coolchic_init_state(const cc_arch_t* arch, uint64_t seed, const cc_state_t* 
     a.m_par = st->m_par;
     a.v_par = st->v_par;
     a.step = st->step;
-    a.N = make_geom(arch->H, arch->W).off[kL];
+    a.N = make_geom(arch->H, arch->W, arch->hyper_grids).off[kG];
     a.seed = seed;
+    a.nh = arch->hyper_grids;
+    a.pad_ = 0;
     launch_init_state(a, (cudaStream_t)stream);
     if (st->soap) {  // the SOAP state starts at zero
         const cudaError_t e = cudaMemsetAsync(st->soap, 0, sizeof(float) * (size_t)soap_state_floats(), (cudaStream_t)stream);
@@ -517,7 +521,7 @@ int coolchic_param_block(int32_t index, const char** name, int32_t* offset, int3
              {"syn.w1", po::syn_w1, 280},  {"syn.b1", po::syn_b1, 40},   {"syn.w2", po::syn_w2, 120},
              {"syn.b2", po::syn_b2, 3},    {"syn.ws", po::syn_ws, 21},   {"syn.bs", po::syn_bs, 3},
              {"conv1.w", po::cv1_w, 81},   {"conv1.b", po::cv1_b, 3},    {"conv2.w", po::cv2_w, 81},
-             {"conv2.b", po::cv2_b, 3}};
+             {"conv2.b", po::cv2_b, 3},    {"ifce_h.w", po::ifce_h, po::ifce_h_n}};
     const int n = (int)(sizeof(B) / sizeof(B[0]));
     if (index < 0 || index >= n) return fail(CC_ERR_ARG, "parameter block %d out of range", index);
     if (name) *name = B[index].n;

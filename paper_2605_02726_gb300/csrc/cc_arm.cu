@@ -35,6 +35,11 @@
 // (again bounded) for its MMAs in flight, frees its Tensor Memory and writes a NaN rate partial,
 // so that the loss of the call is NaN instead of the GPU hanging.
 //
+// With hyperlatent grids (Sec. III-A3, Eq. 6; the HYPER instantiation), their latents are coded
+// like the others (spatial context only), and the IFCEs of grids 0..2 take three more inputs, the
+// co-located hyperlatents; their gradients go to IFCE-input planes nin..nin+2 of the grid, their
+// weights' gradients to entries 756..791 of the CTA's partial row.
+//
 // The first CTA also computes the coarse forward upsampling stages 6..4 (it needs none of the
 // entropy model's results, and the other CTAs take the latents), so that they cost no launch.
 #include "cc_kernels.h"
@@ -62,26 +67,38 @@ constexpr int B4_N = 32, B4_K = 24;  // [W1^T | Ws^T]: row f, k < 16: W1[k][f], 
 constexpr uint32_t B1_BYTES = B1_N * B1_K * 4, B2_BYTES = B2_N * B2_K * 4, B3_BYTES = B3_N * B3_K * 4,
                    B4_BYTES = B4_N * B4_K * 4;
 constexpr int kSld = 36;                                  // staging row stride (32 latents + 4)
-constexpr int kStRows = 72;                               // staging rows, see below
-constexpr uint32_t ST_BYTES = kStRows * kSld * 4;         // per warp
 constexpr uint32_t SM_B1 = 0, SM_B2 = SM_B1 + 2 * B1_BYTES, SM_B3 = SM_B2 + 2 * B2_BYTES,
-                   SM_B4 = SM_B3 + 2 * B3_BYTES, SM_ST = SM_B4 + 2 * B4_BYTES,
-                   SM_MISC = SM_ST + kWarps * ST_BYTES;
-// misc floats: IFCE weights and biases in flat parameter order, W3 [2][16], b2, Ws [2][20], b3 + bs
-constexpr int MS_IF = 0, MS_W3 = 72, MS_B2 = 104, MS_WS = 120, MS_OB = 160, MS_N = 164;
-constexpr uint32_t SM_TOTAL = SM_MISC + MS_N * 4;
-static_assert(SM_ST % 16 == 0 && ST_BYTES % 16 == 0, "16-byte alignment of the staging tiles");
+                   SM_B4 = SM_B3 + 2 * B3_BYTES, SM_ST = SM_B4 + 2 * B4_BYTES;
+// misc floats: IFCE weights and biases in flat parameter order, W3 [2][16], b2, Ws [2][20], b3 + bs,
+// then (hyperlatents) the IFCE weights of the hyperlatent inputs [k][o][q]
+constexpr int MS_IF = 0, MS_W3 = 72, MS_B2 = 104, MS_WS = 120, MS_OB = 160, MS_IFH = 164;
+// Layout of one instantiation: staging rows per warp (the IFCE inputs take one more 8-row block
+// with hyperlatents), gradient tiles, shared memory
+template <bool HY>
+struct ArmLayout {
+    static constexpr int st_rows = HY ? 80 : 72;
+    static constexpr uint32_t st_bytes = st_rows * kSld * 4;
+    static constexpr uint32_t misc = SM_ST + kWarps * st_bytes;
+    static constexpr int ms_n = MS_IFH + (HY ? po::ifce_h_n : 0);
+    static constexpr uint32_t total = misc + ms_n * 4;
+    static constexpr int tiles = HY ? 13 : 12;
+    static_assert(st_bytes % 16 == 0, "16-byte alignment of the staging tiles");
+};
+static_assert(SM_ST % 16 == 0, "16-byte alignment of the staging tiles");
 
 // Staging rows of a warp's [feature][latent] tile, first fill (gradient side U, activation side V):
 //   U: 0..15 da1, 16..31 da2, 32 dmu, 33 dlogb, 34 + 4k + o: IFCE output gradient o of grid k
 //      (zero unless the latent is on grid k), 46, 47 zero
 //   V: 48..71 c (features 0..19, 68 = one, 69..71 zero)
-// second fill: 0..15 h2, 16..47 as before, 48..63 h1, 64..69 IFCE inputs r0..r5, 70 one, 71 zero
+// second fill: 0..15 h2, 16..47 as before, 48..63 h1, then the IFCE inputs: 64..69 r0..r5,
+// 70 one, 71 zero; with hyperlatents 64..69 r0..r5, 70..72 the three hyperlatent inputs, 73 one,
+// 74..79 zero.
 constexpr int R_DA1 = 0, R_DA2 = 16, R_U2 = 32, R_C = 48;
 constexpr int R_H2 = 0, R_H1 = 48, R_R = 64;
-constexpr int kTiles = 12;  // gradient tiles (m16 x n8), see wgrad_index
 
-// Parameter index of gradient tile T, row, column (-1: padding).
+// Parameter index of gradient tile T, row, column (-1: padding); with hyperlatents, an index
+// past po::total stands for entry (index - po::total + 756) of the CTA's partial row.
+template <bool HY>
 __device__ int wgrad_index(int T, int row, int col) {
     if (T <= 2) {  // da1 x c
         const int f = T * 8 + col;
@@ -95,10 +112,12 @@ __device__ int wgrad_index(int T, int row, int col) {
         return f < 20 ? po::arm_ws + row * 20 + f : (f == 20 ? po::arm_b3 + row : -1);
     }
     if (T <= 10) return row < 2 ? po::arm_w3 + row * 16 + (T - 9) * 8 + col : -1;  // (dmu, dlogb) x h2
-    if (row < 2 || row >= 14) return -1;  // T == 11: IFCE output gradients x IFCE inputs
+    if (row < 2 || row >= 14) return -1;  // T == 11 (12): IFCE output gradients x IFCE inputs
     const int k = (row - 2) >> 2, o = (row - 2) & 3, nin = ifce_nin(k);
-    if (col < nin) return ifce_w_off(k) + o * nin + col;
-    if (col == 6) return ifce_b_off(k) + o;
+    const int j = (T - 11) * 8 + col;  // column of the IFCE-input block
+    if (j < nin) return ifce_w_off(k) + o * nin + j;
+    if (HY && j >= 6 && j < 6 + kNH) return po::ifce_h + (k * kF + o) * kNH + (j - 6);
+    if (j == (HY ? 6 + kNH : 6)) return ifce_b_off(k) + o;
     return -1;
 }
 
@@ -145,23 +164,32 @@ __device__ __forceinline__ void mma_group(uint32_t tmem, uint32_t sB, uint32_t i
     }
 }
 
-template <int PASS>
+template <int PASS, bool HY>
 __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     constexpr bool BWD = pass_bwd(PASS);
     constexpr bool LOAD = PASS == PASS_BWD_LOAD;
+    using LY = ArmLayout<HY>;
+    constexpr int kTiles = LY::tiles;
+    constexpr uint32_t ST_BYTES = LY::st_bytes;
+    constexpr int kRR = HY ? 16 : 8;        // rows of the IFCE-input block
+    constexpr int kOneCol = HY ? 6 + kNH : 6;  // its column of ones
     extern __shared__ __align__(1024) unsigned char smem[];
-    float* sMisc = reinterpret_cast<float*>(smem + SM_MISC);
+    float* sMisc = reinterpret_cast<float*>(smem + LY::misc);
     __shared__ Geom g;
-    __shared__ float rcp_w[kL];
+    __shared__ float rcp_w[kG];
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     float* st = reinterpret_cast<float*>(smem + SM_ST + wid * ST_BYTES);  // this warp's staging tile
 
     if (tid == 0) g = a.g;
-    if (tid < kL) rcp_w[tid] = 1.f / (float)a.g.w[tid];
+    if (tid < kG) rcp_w[tid] = a.g.w[tid] > 0 ? 1.f / (float)a.g.w[tid] : 0.f;
+    const bool hyper = HY && a.g.nh > 0;  // this job has hyperlatent grids
     // parameters staged through the staging area (free until the coarse stages and the first tile)
     const float* P = stage_params(a.params, 0, po::arm_block, reinterpret_cast<float*>(smem + SM_ST));
+    const float* Ph = nullptr;  // the hyperlatent IFCE weights, at their absolute offsets
+    if (hyper)
+        Ph = stage_params(a.params, po::ifce_h, po::ifce_h_n, reinterpret_cast<float*>(smem + SM_ST) + po::arm_block);
     // B operands: element (n, k) of each, hi and lo
     for (int e = tid; e < B1_N * B1_K; e += kT) {
         const int n = e / B1_K, k = e - n * B1_K;
@@ -195,13 +223,14 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         *reinterpret_cast<float*>(smem + off) = h;
         *reinterpret_cast<float*>(smem + off + B4_BYTES) = l;
     }
-    for (int j = tid; j < MS_N; j += kT) {
+    for (int j = tid; j < LY::ms_n; j += kT) {
         float v;
         if (j < MS_W3) v = P[po::if_w0 + j];
         else if (j < MS_B2) v = P[po::arm_w3 + (j - MS_W3)];
         else if (j < MS_WS) v = P[po::arm_b2 + (j - MS_B2)];
         else if (j < MS_OB) v = P[po::arm_ws + (j - MS_WS)];
-        else v = j - MS_OB < 2 ? P[po::arm_b3 + (j - MS_OB)] + P[po::arm_bs + (j - MS_OB)] : 0.f;
+        else if (j < MS_IFH) v = j - MS_OB < 2 ? P[po::arm_b3 + (j - MS_OB)] + P[po::arm_bs + (j - MS_OB)] : 0.f;
+        else v = hyper ? Ph[po::ifce_h + (j - MS_IFH)] : 0.f;
         sMisc[j] = v;
     }
     const uint32_t mbar = smem_u32(&s_mbar);
@@ -289,8 +318,8 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             const int dy = ctx_dy(n), dx = ctx_dx(n);
             cx[n] = (r + dy >= 0 && c + dx >= 0 && c + dx < w) ? __ldg(yk + dy * w + dx) : 0.f;
         }
-        const int nin = ifce_nin(k);
-        float rin[6];
+        const int nin = ifce_nin(k);  // main-grid IFCE inputs (0 on grids 3.. and on hyperlatent grids)
+        float rin[6 + (HY ? kNH : 0)];  // main inputs 0..5 (zero past nin), hyperlatent inputs 6..8
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
             rin[j] = 0.f;
@@ -300,8 +329,20 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 rin[j] = __ldg(a.yt + g.off[gj] + (int64_t)rr * g.w[gj] + cc);
             }
         }
+        if constexpr (HY) {
+#pragma unroll
+            for (int q = 0; q < kNH; ++q) {
+                rin[6 + q] = 0.f;
+                if (hyper && nin > 0) {
+                    const int gq = kL + q, sh = kHB + q - k;
+                    const int rr = min(r >> sh, g.h[gq] - 1), cc = min(c >> sh, g.w[gq] - 1);
+                    rin[6 + q] = __ldg(a.yt + g.off[gq] + (int64_t)rr * g.w[gq] + cc);
+                }
+            }
+        }
         {
-            const int wo = ifce_w_off(k < kNIfce ? k : 0) - po::if_w0, bo = ifce_b_off(k < kNIfce ? k : 0) - po::if_w0;
+            const int kk = k < kNIfce ? k : 0;
+            const int wo = ifce_w_off(kk) - po::if_w0, bo = ifce_b_off(kk) - po::if_w0;
 #pragma unroll
             for (int o = 0; o < kF; ++o) {
                 float f = 0.f;
@@ -310,6 +351,10 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
 #pragma unroll
                     for (int j = 0; j < 6; ++j)
                         if (j < nin) f = fmaf(sMisc[MS_IF + wo + o * nin + j], rin[j], f);
+                    if constexpr (HY) {
+#pragma unroll
+                        for (int q = 0; q < kNH; ++q) f = fmaf(sMisc[MS_IFH + (kk * kF + o) * kNH + q], rin[6 + q], f);
+                    }
                 }
                 cx[kNCtx + o] = f;
             }
@@ -467,6 +512,17 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                     for (int o = 0; o < kF; ++o) v = fmaf(sMisc[MS_IF + wo + o * nin + j], dc[16 + o], v);
                     dR[(int64_t)j * nk + li] = v;
                 }
+            if constexpr (HY) {
+                if (hyper) {  // planes nin..nin+2: the hyperlatent inputs
+#pragma unroll
+                    for (int q = 0; q < kNH; ++q) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int o = 0; o < kF; ++o) v = fmaf(sMisc[MS_IFH + (k * kF + o) * kNH + q], dc[16 + o], v);
+                        dR[(int64_t)(nin + q) * nk + li] = v;
+                    }
+                }
+            }
         }
         __syncwarp();
         // ---- parameter-gradient tiles over K = 32 latents (four k-steps of 8), fragments by ldmatrix:
@@ -520,9 +576,10 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 st[(R_H1 + j) * kSld + lane] = fmaxf(a1[j], 0.f);
             }
 #pragma unroll
-            for (int j = 0; j < 6; ++j) st[(R_R + j) * kSld + lane] = rin[j];
-            st[(R_R + 6) * kSld + lane] = 1.f;
-            st[(R_R + 7) * kSld + lane] = 0.f;
+            for (int j = 0; j < 6 + (HY ? kNH : 0); ++j) st[(R_R + j) * kSld + lane] = rin[j];
+            st[(R_R + kOneCol) * kSld + lane] = 1.f;
+#pragma unroll
+            for (int j = kOneCol + 1; j < kRR; ++j) st[(R_R + j) * kSld + lane] = 0.f;
             __syncwarp();
             // the gradient factors x h1, h2, r (tiles 3-4, 9-10, 11)
 #pragma unroll
@@ -531,19 +588,20 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 const float* arow = st + (ri + (mi & 1) * 8) * kSld + k0 + (mi >> 1) * 4;
                 const float* brow = st + ri * kSld + k0 + (mi & 1) * 4;
                 const AFrag U1 = afrag(arow, R_DA2), U2 = afrag(arow, R_U2);
-                AFrag H1a, H1b, H2a, H2b, Rr, Vx;
+                AFrag H1a, H1b, H2a, H2b, Rr, Rr2;
                 bpair(brow, R_H1, R_H1 + 8, H1a, H1b);
                 bpair(brow, R_H2, R_H2 + 8, H2a, H2b);
-                bpair(brow, R_R, R_R, Rr, Vx);
-                const AFrag* TA[5] = {&U1, &U1, &U2, &U2, &U2};
-                const AFrag* TB[5] = {&H1a, &H1b, &H2a, &H2b, &Rr};
-                constexpr int TT[5] = {3, 4, 9, 10, 11};
+                bpair(brow, R_R, R_R + (HY ? 8 : 0), Rr, Rr2);
+                constexpr int NT2 = HY ? 6 : 5;
+                const AFrag* TA[6] = {&U1, &U1, &U2, &U2, &U2, &U2};
+                const AFrag* TB[6] = {&H1a, &H1b, &H2a, &H2b, &Rr, &Rr2};
+                constexpr int TT[6] = {3, 4, 9, 10, 11, 12};
 #pragma unroll
-                for (int q = 0; q < 5; ++q) mma1(acc[TT[q]], TA[q]->l, TB[q]->h[0], TB[q]->h[1]);
+                for (int q = 0; q < NT2; ++q) mma1(acc[TT[q]], TA[q]->l, TB[q]->h[0], TB[q]->h[1]);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) mma1(acc[TT[q]], TA[q]->h, TB[q]->l[0], TB[q]->l[1]);
+                for (int q = 0; q < NT2; ++q) mma1(acc[TT[q]], TA[q]->h, TB[q]->l[0], TB[q]->l[1]);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) mma1(acc[TT[q]], TA[q]->h, TB[q]->h[0], TB[q]->h[1]);
+                for (int q = 0; q < NT2; ++q) mma1(acc[TT[q]], TA[q]->h, TB[q]->h[0], TB[q]->h[1]);
             }
         }
         __syncwarp();
@@ -572,12 +630,16 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) sAcc[((wid * kTiles + T) * 32 + lane) * 4 + q] = acc[T][q];
         __syncthreads();
-        float* gp = a.gpart + (int64_t)cta * po::arm_block;
+        float* gp = a.gpart + (int64_t)cta * (hyper ? po::arm_block_h : po::arm_block);
         for (int e = tid; e < kTiles * 32 * 4; e += kT) {
             const int T = e >> 7, l = (e >> 2) & 31, q = e & 3;
             const int row = (l >> 2) + (q >= 2 ? 8 : 0), col = 2 * (l & 3) + (q & 1);
-            const int idx = wgrad_index(T, row, col);
+            int idx = wgrad_index<HY>(T, row, col);
             if (idx < 0) continue;
+            if (idx >= po::total) {  // a hyperlatent IFCE weight
+                if (!hyper) continue;
+                idx = po::arm_block + (idx - po::ifce_h);
+            }
             float sum = 0.f;
             for (int wv = 0; wv < kWarps; ++wv) sum += sAcc[((wv * kTiles + T) * 32 + l) * 4 + q];
             gp[idx] = sum;
@@ -586,25 +648,33 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     }
 }
 
-template <int PASS>
+template <int PASS, bool HY>
 __global__ void __launch_bounds__(kT, 3) k_arm(const __grid_constant__ ArmArgs a) {
     __shared__ ArmArgs sa;
     param_fetch(a, sa);
-    arm_body<PASS>(sa, blockIdx.x, gridDim.x);
+    arm_body<PASS, HY>(sa, blockIdx.x, gridDim.x);
 }
-template <int PASS>
+template <int PASS, bool HY>
 __global__ void __launch_bounds__(kT, 3) k_arm_b(Batch<ArmArgs> b) {
     __shared__ ArmArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
-    arm_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
+    arm_body<PASS, HY>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
+}
+
+template <bool HY, typename F>
+void for_passes(F f) {
+    f(k_arm<PASS_FWD, HY>, k_arm_b<PASS_FWD, HY>);
+    f(k_arm<PASS_FWD_STORE, HY>, k_arm_b<PASS_FWD_STORE, HY>);
+    f(k_arm<PASS_FWD_BWD, HY>, k_arm_b<PASS_FWD_BWD, HY>);
+    f(k_arm<PASS_BWD_LOAD, HY>, k_arm_b<PASS_BWD_LOAD, HY>);
 }
 
 }  // namespace
 
-size_t arm_smem_bytes(int pass) {
+size_t arm_smem_bytes(int pass, bool hyper) {
     (void)pass;
-    return SM_TOTAL;
+    return hyper ? ArmLayout<true>::total : ArmLayout<false>::total;
 }
 
 int arm_grid(int64_t N) {
@@ -635,39 +705,54 @@ ArmArgs arm_args(const Work& w, const float* params, float grad_scale) {
     return a;
 }
 
+template <bool HY>
+void launch_arm_t(const Work& w, const ArmArgs& a, int pass, cudaStream_t s) {
+    const size_t sm = arm_smem_bytes(pass, HY);
+    const int grid = w.n_cta_arm;
+    switch (pass) {
+        case PASS_FWD: launch_pdl(k_arm<PASS_FWD, HY>, grid, kT, sm, s, a); break;
+        case PASS_FWD_STORE: launch_pdl(k_arm<PASS_FWD_STORE, HY>, grid, kT, sm, s, a); break;
+        case PASS_FWD_BWD: launch_pdl(k_arm<PASS_FWD_BWD, HY>, grid, kT, sm, s, a); break;
+        default: launch_pdl(k_arm<PASS_BWD_LOAD, HY>, grid, kT, sm, s, a); break;
+    }
+}
+
 void launch_arm(const Work& w, const float* params, int pass, float grad_scale, cudaStream_t s) {
     ArmArgs a = arm_args(w, params, grad_scale);
     if (pass == PASS_BWD_LOAD) a.upc_on = 0;  // the upsampled grids are still in the workspace
-    const size_t sm = arm_smem_bytes(pass);
-    const int grid = w.n_cta_arm;
+    if (w.g.nh > 0)
+        launch_arm_t<true>(w, a, pass, s);
+    else
+        launch_arm_t<false>(w, a, pass, s);
+}
+
+template <bool HY>
+void launch_arm_b_t(const Batch<ArmArgs>& b, int pass, cudaStream_t s) {
+    const size_t sm = arm_smem_bytes(pass, HY);
     switch (pass) {
-        case PASS_FWD: launch_pdl(k_arm<PASS_FWD>, grid, kT, sm, s, a); break;
-        case PASS_FWD_STORE: launch_pdl(k_arm<PASS_FWD_STORE>, grid, kT, sm, s, a); break;
-        case PASS_FWD_BWD: launch_pdl(k_arm<PASS_FWD_BWD>, grid, kT, sm, s, a); break;
-        default: launch_pdl(k_arm<PASS_BWD_LOAD>, grid, kT, sm, s, a); break;
+        case PASS_FWD: launch_pdl(k_arm_b<PASS_FWD, HY>, b.total_ctas, kT, sm, s, b); break;
+        case PASS_FWD_STORE: launch_pdl(k_arm_b<PASS_FWD_STORE, HY>, b.total_ctas, kT, sm, s, b); break;
+        case PASS_FWD_BWD: launch_pdl(k_arm_b<PASS_FWD_BWD, HY>, b.total_ctas, kT, sm, s, b); break;
+        default: launch_pdl(k_arm_b<PASS_BWD_LOAD, HY>, b.total_ctas, kT, sm, s, b); break;
     }
 }
 
-void launch_arm_b(const Batch<ArmArgs>& b, int pass, cudaStream_t s) {
-    const size_t sm = arm_smem_bytes(pass);
-    switch (pass) {
-        case PASS_FWD: launch_pdl(k_arm_b<PASS_FWD>, b.total_ctas, kT, sm, s, b); break;
-        case PASS_FWD_STORE: launch_pdl(k_arm_b<PASS_FWD_STORE>, b.total_ctas, kT, sm, s, b); break;
-        case PASS_FWD_BWD: launch_pdl(k_arm_b<PASS_FWD_BWD>, b.total_ctas, kT, sm, s, b); break;
-        default: launch_pdl(k_arm_b<PASS_BWD_LOAD>, b.total_ctas, kT, sm, s, b); break;
-    }
+void launch_arm_b(const Batch<ArmArgs>& b, int pass, bool any_hyper, cudaStream_t s) {
+    if (any_hyper)
+        launch_arm_b_t<true>(b, pass, s);
+    else
+        launch_arm_b_t<false>(b, pass, s);
 }
 
 void arm_init_attributes() {
-    const int sm = (int)arm_smem_bytes(PASS_FWD_BWD);
-    cudaFuncSetAttribute(k_arm<PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_arm<PASS_FWD_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_arm<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_arm<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_arm_b<PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_arm_b<PASS_FWD_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_arm_b<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_arm_b<PASS_BWD_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    for_passes<false>([](auto k1, auto kb) {
+        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arm_smem_bytes(0, false));
+        cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arm_smem_bytes(0, false));
+    });
+    for_passes<true>([](auto k1, auto kb) {
+        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arm_smem_bytes(0, true));
+        cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arm_smem_bytes(0, true));
+    });
 }
 
 }  // namespace cc

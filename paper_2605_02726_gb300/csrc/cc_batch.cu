@@ -31,6 +31,7 @@ struct cc_batch {
     cc::Batch<cc::ReduceArgs> reduce;
     cc::Batch<cc::SoapArgs> soap;  // launched when some job uses CC_OPT_SOAP
     bool any_soap = false;
+    bool any_hyper = false;  // some job has hyperlatent grids: the entropy model's general form
     cc::Batch<cc::FinishArgs> finish;
     double* rd = nullptr;  // device [rd_capacity][n][3]
 };
@@ -114,7 +115,8 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
     for (int j = 0; j < n; ++j) {
         cc_arch_t ref;
         if (coolchic_arch_init(&ref, archs[j].H, archs[j].W) != CC_OK) return CC_ERR_ARG;
-        if (std::memcmp(&ref, &archs[j], sizeof(ref)) != 0)
+        ref.hyper_grids = archs[j].hyper_grids;
+        if (std::memcmp(&ref, &archs[j], sizeof(ref)) != 0 || (ref.hyper_grids != 0 && ref.hyper_grids != kNH))
             return set_error(CC_ERR_UNSUPPORTED, "batch_create: job %d has an unsupported architecture", j);
         const cc_hparams_t& h = hps[j];
         if (const int rc = validate_hparams(&h)) return rc;
@@ -186,7 +188,10 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
     b->soap = fill([&](int j) { return soap_args(W[j], states[j].params, states[j].m_par, states[j].v_par,
                                                  states[j].soap, H[j], states[j].step); },
                    [&](int) { return kSoapBlocks; });
-    for (int j = 0; j < n; ++j) b->any_soap |= H[j].nn_opt == 1;
+    for (int j = 0; j < n; ++j) {
+        b->any_soap |= H[j].nn_opt == 1;
+        b->any_hyper |= W[j].g.nh > 0;
+    }
     b->finish = fill([&](int j) {
                          // record pointer: offset of this job's first slot inside the table (fixed up below)
                          return finish_args(W[j], H[j], 1, 1, reinterpret_cast<double*>(rd_off + (size_t)j * 3 * sizeof(double)),
@@ -240,7 +245,7 @@ int coolchic_batch_step(cc_batch_t* b, int32_t n_iters, void* stream) {
     if (b->rd) launch_mark_base_b(b->finish, s);
     for (int it = 0; it < n_iters; ++it) {
         if (it == 0) launch_relax_b(b->relax, s);  // later iterations: relaxed by the previous Adam update
-        launch_arm_b(b->arm, PASS_FWD_BWD, s);
+        launch_arm_b(b->arm, PASS_FWD_BWD, b->any_hyper, s);
         for (int m = kUpArmLo - 1; m >= 1; --m) launch_up_fwd_b(b->upf[m], s);  // the rest in the entropy-model launch
         launch_syn_fwd_b(b->synf, s);
         launch_conv_b(b->conv, s);

@@ -8,6 +8,9 @@
 namespace cc {
 
 constexpr int kL = 7;        // latent grids (Sec. III-A1, Eq. 1; Table II 1/1..1/64)
+constexpr int kNH = 3;       // hyperlatent grids when enabled (Sec. III-A3, Eq. 6; Table II 1/16..1/64)
+constexpr int kHB = 4;       // the largest hyperlatent grid is 1/2^kHB of the image
+constexpr int kG = kL + kNH; // grid slots: latent grids 0..6, then hyperlatent grids 7..9
 constexpr int kNCtx = 16;    // spatial context values
 constexpr int kF = 4;        // IFCE output width
 constexpr int kNIfce = 3;    // grids 0..2 carry an IFCE (Table II)
@@ -30,6 +33,9 @@ constexpr int total = 1415;
 constexpr int arm_block = up;                 // ARM + IFCE parameters: [0, 756)
 constexpr int syn_block = cv1_w - syn_w1;     // 467
 constexpr int conv_block = total - cv1_w;     // 168
+// with hyperlatents: the IFCE weights of the hyperlatent inputs [grid k][output o][grid q] follow
+constexpr int ifce_h = total, ifce_h_n = kNIfce * kF * kNH, total_h = total + ifce_h_n;  // 1451
+constexpr int arm_block_h = arm_block + ifce_h_n;  // per-CTA ARM partials with hyperlatents: 792
 }  // namespace po
 
 __host__ __device__ constexpr int ifce_w_off(int k) { return k == 0 ? po::if_w0 : (k == 1 ? po::if_w1 : po::if_w2); }
@@ -50,20 +56,27 @@ __host__ __device__ constexpr int ctx_dx(int n) {
          : n == 14 ? -3 : 3;
 }
 
+// Grid slots k = 0..kL-1 are the latent grids (ceil(H/2^k) x ceil(W/2^k)); with hyperlatents
+// (nh = kNH) slots kL..kL+kNH-1 are the hyperlatent grids, slot kL + q with the shape of latent
+// grid kHB + q.  Unused slots are empty and start at the end of the latents, off[kG] = N.
 struct Geom {
-    int H, W;
-    int h[kL], w[kL];
-    int64_t off[kL + 1];
+    int H, W, nh, pad_;
+    int h[kG], w[kG];
+    int64_t off[kG + 1];
 };
 
-inline Geom make_geom(int H, int W) {
+inline Geom make_geom(int H, int W, int hyper = 0) {
     Geom g;
     g.H = H;
     g.W = W;
+    g.nh = hyper ? kNH : 0;
+    g.pad_ = 0;
     g.off[0] = 0;
-    for (int k = 0; k < kL; ++k) {
-        g.h[k] = (H + (1 << k) - 1) >> k;
-        g.w[k] = (W + (1 << k) - 1) >> k;
+    for (int k = 0; k < kG; ++k) {
+        const int s = k < kL ? k : kHB + (k - kL);
+        const bool used = k < kL + g.nh;
+        g.h[k] = used ? (H + (1 << s) - 1) >> s : 0;
+        g.w[k] = used ? (W + (1 << s) - 1) >> s : 0;
         g.off[k + 1] = g.off[k] + (int64_t)g.h[k] * g.w[k];
     }
     return g;
@@ -72,7 +85,7 @@ inline Geom make_geom(int H, int W) {
 __device__ __forceinline__ int grid_of(const Geom& g, int64_t i) {
     int k = 0;
 #pragma unroll
-    for (int j = 1; j < kL; ++j) k += (i >= g.off[j]) ? 1 : 0;
+    for (int j = 1; j < kG; ++j) k += (i >= g.off[j]) ? 1 : 0;
     return k;
 }
 

@@ -10,7 +10,9 @@
 //   hi = (v >> 18) & 1023, lo = (v >> 8) & 1023, E = 0 once n >= 16,
 //   K[s] = rint(2^20 log2(e) exp(-s/256)), T_HI[j] = rint(2^15 2^(-j/1024)), T_LO[j] = rint(2^15 2^(-j/2^20)),
 // i.e. E ~ 2^15 exp(-u / (256 b)).  The tables are built here on the host in FP64 and copied
-// to each device once; everything after them is integer arithmetic, hence bit-exact.
+// to each device once; everything after them is integer arithmetic, hence bit-exact.  With
+// hyperlatent grids (Sec. III-A3) their latents are decoded by the same model, and the IFCEs of
+// grids 0..2 add the co-located hyperlatents times their 2^-8-grid weights.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -39,11 +41,13 @@ __device__ __forceinline__ long long cdf_q16(int s, long long t) {
 __global__ void k_decode_arm(Geom gp, const int32_t* __restrict__ q, const float* __restrict__ P, float* yq,
                              uint32_t* prob, int32_t* mu_out, int32_t* logb_out) {
     __shared__ long long sW[po::arm_block];
+    __shared__ long long sWh[po::ifce_h_n];  // hyperlatent IFCE weights [k][o][q]
     __shared__ Geom g;  // shared copy: the grid tables are indexed with a runtime grid number
     for (int j = threadIdx.x; j < po::arm_block; j += blockDim.x) sW[j] = q8(P[j]);
+    for (int j = threadIdx.x; j < po::ifce_h_n; j += blockDim.x) sWh[j] = gp.nh ? q8(P[po::ifce_h + j]) : 0ll;
     if (threadIdx.x == 0) g = gp;
     __syncthreads();
-    const int64_t N = g.off[kL];
+    const int64_t N = g.off[kG];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int k = grid_of(g, i);
         const int wk = g.w[k];
@@ -75,6 +79,11 @@ __global__ void k_decode_arm(Geom gp, const int32_t* __restrict__ q, const float
 #pragma unroll
                 for (int j = 0; j < 6; ++j)
                     if (j < nin) acc += sW[ifce_w_off(k) + o * nin + j] * rv[j];
+                for (int hq = 0; hq < g.nh; ++hq) {
+                    const int gq = kL + hq, sh = kHB + hq - k;
+                    const int rr = min(r >> sh, g.h[gq] - 1), cc = min(c >> sh, g.w[gq] - 1);
+                    acc += sWh[(k * kF + o) * kNH + hq] * (long long)q[g.off[gq] + rr * g.w[gq] + cc];
+                }
             }
             x[kNCtx + o] = acc;
         }
@@ -148,7 +157,7 @@ void decode_init_tables() {
 
 void launch_decode(const Geom& g, const int32_t* q, const float* params, float* yq, uint32_t* prob, int32_t* mu_q,
                    int32_t* logb_q, cudaStream_t s) {
-    const int64_t N = g.off[kL];
+    const int64_t N = g.off[kG];
     int64_t blocks = (N + 127) / 128;
     if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
     k_decode_arm<<<(int)blocks, 128, 0, s>>>(g, q, params, yq, prob, mu_q, logb_q);

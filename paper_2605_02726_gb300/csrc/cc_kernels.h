@@ -81,10 +81,10 @@ struct Work {
     int64_t HW;
     float* yt;         // relaxed latents [N]
     float* dS;         // context-gradient planes [16][N]
-    float* dR[3];      // IFCE-input gradient planes: grid k has ifce_nin(k) planes of h_k*w_k
+    float* dR[3];      // IFCE-input gradient planes: grid k has ifce_nin(k) (+ nh) planes of h_k*w_k
     float* dYd;        // direct rate gradient [N]
     float* dYsyn;      // gradient reaching each grid through upsampling + synthesis [N]
-    float* dIf;        // IFCE gradient of grids 3..6 summed per grid-3 cell [4][h_3*w_3]
+    float* dIf;        // IFCE gradient of grids 3..6 (then the hyperlatent grids) per grid-3 cell [4 + nh][h_3*w_3]
     float* up[kL];     // up[m], m = 1..5: channels of grids m+1..6 upsampled to grid m
     float* dup[kL];    // adjoints of up[m], m = 1..5
     float* t;          // synthesis output before the residual convs [3][HW]
@@ -94,7 +94,7 @@ struct Work {
                        // synthesis forward for its adjoint (null: not kept)
     float* act_arm;    // stored ARM activations [34][N] (optional)
     float* act_syn;    // stored synthesis pre-activations [40][HW] (optional)
-    float* gpart_arm;  // per-CTA partial gradients [n_cta_arm][756]
+    float* gpart_arm;  // per-CTA partial gradients [n_cta_arm][756, or 792 with hyperlatents]
     float* gpart_syn;  // [n_cta_syn][467]
     float* gpart_conv; // [n_cta_conv][168]
     float* gpart_up;   // [6 stages][kUpMaxCta][4]
@@ -319,6 +319,8 @@ struct GatherArgs {
 };
 struct ReduceArgs {
     float* gsoap;  // SOAP (hp.nn_opt == 1): the reduced gradient of the SOAP blocks goes here
+    int hyper;     // the job has hyperlatent grids: 1451 parameters, ARM partial rows of 792
+    int pad_h_;
     const float* garm;
     const float* gup;  // [6][kUpMaxCta][4]
     const float* gsyn;
@@ -409,11 +411,13 @@ struct InitArgs {
     int64_t* step;
     int64_t N;
     uint64_t seed;
+    int nh;  // hyperlatent grids (0 or kNH)
+    int pad_;
 };
 void launch_init_state(const InitArgs& a, cudaStream_t s);
 
 // sizes that the workspace layout depends on
-size_t arm_smem_bytes(int pass);
+size_t arm_smem_bytes(int pass, bool hyper);
 int arm_grid(int64_t N);
 int conv_tiles(int H, int W);
 int up_adj_ctas(int nch, int hs, int ws);
@@ -443,7 +447,7 @@ int ifce_ctas(const Work& w);
 int gather_ctas(const Work& w);
 int reduce_ctas();
 void launch_relax_b(const Batch<RelaxArgs>& b, cudaStream_t s);
-void launch_arm_b(const Batch<ArmArgs>& b, int pass, cudaStream_t s);
+void launch_arm_b(const Batch<ArmArgs>& b, int pass, bool any_hyper, cudaStream_t s);
 void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s);
 void launch_syn_fwd_b(const Batch<SynArgs>& b, cudaStream_t s);
 void launch_conv_b(const Batch<ConvArgs>& b, cudaStream_t s);

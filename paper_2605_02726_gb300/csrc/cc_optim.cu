@@ -44,6 +44,8 @@ __global__ void k_relax_b(Batch<RelaxArgs> b) {
 // grid-3 cells, so per grid-3 cell and per g: Q[g-3][cell] = sum_k' (block of 2^(3-k') x 2^(3-k')
 // under the cell of dR_k' channel g - k' - 1).  One thread per (g, cell); fixed-size unrolled
 // loads.  The gather kernel adds Q over the 2^(g-3) x 2^(g-3) cells under each grid-g latent.
+// Hyperlatent grid q (the shape of grid 4 + q) is input 6 - k' + q of IFCE k', i.e. channel
+// 2 + (4 + q) - k' as well: its plane is Q[4 + q], the same formula with "g" = 7 + q.
 // ---------------------------------------------------------------------------------------------
 template <int B>
 __device__ __forceinline__ float block_sum_clipped(const float* __restrict__ plane, int h, int w, int r0, int c0) {
@@ -74,7 +76,7 @@ __device__ __forceinline__ void ifce_body(const IfceArgs& a, int cta, int ncta) 
     const Geom& g = a.g;
     const int n3 = g.h[3] * g.w[3];
     const int64_t n0 = (int64_t)g.h[0] * g.w[0], n1 = (int64_t)g.h[1] * g.w[1], n2 = (int64_t)g.h[2] * g.w[2];
-    const int64_t total = 4 * (int64_t)n3 * 8;  // a multiple of 8: the 8 threads of a task share a warp
+    const int64_t total = (4 + g.nh) * (int64_t)n3 * 8;  // a multiple of 8: the 8 threads of a task share a warp
     // the loop runs while any lane of the warp has a task, so that every lane takes part in the shuffles
     for (int64_t e = cta * (int64_t)blockDim.x + threadIdx.x; e - (int)(threadIdx.x & 31) < total;
          e += (int64_t)ncta * blockDim.x) {
@@ -115,7 +117,7 @@ __global__ void k_ifce_cells_b(Batch<IfceArgs> b) {
 // context users all lie inside the grid load them without bounds tests.
 // ---------------------------------------------------------------------------------------------
 struct GatherScalars {
-    float invw[kL];
+    float invw[kG];
     float bc1, bc2;
     ProxyAt px, px_next;
     int64_t step;
@@ -156,14 +158,14 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
             } else {
                 sc.px_next = proxy_at(a.hp, step + 1);
             }
-        } else if (wid == 3 && lane < kL) {
-            sc.invw[lane] = 1.f / (float)a.g.w[lane];
+        } else if (wid == 3 && lane < kG) {
+            sc.invw[lane] = a.g.w[lane] > 0 ? 1.f / (float)a.g.w[lane] : 0.f;
         }
     }
     __syncthreads();
     const Geom& g = a.g;
     const int64_t step = sc.step;
-    const int64_t N = g.off[kL];
+    const int64_t N = g.off[kG];  // with hyperlatent grids, their latents too
     const float* __restrict__ dS = a.dS;
     for (int64_t i = cta * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)ncta * blockDim.x) {
         const int k = grid_of(g, i);
@@ -184,7 +186,8 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
                 v[n] = (rr < hk && cc >= 0 && cc < wk) ? __ldg(p0 + (int64_t)n * N - ctx_dy(n) * wk - ctx_dx(n)) : 0.f;
             }
         }
-        float acc = a.dYd[i] + a.dYsyn[i];
+        // (hyperlatents reach neither the upsampling nor the synthesis)
+        float acc = a.dYd[i] + (k < kL ? a.dYsyn[i] : 0.f);
 #pragma unroll
         for (int n = 0; n < kNCtx; ++n) acc += v[n];
         // IFCE users, as blocks summed with all their loads in flight (unrolled, clipped to the grid)
@@ -197,9 +200,11 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a, int cta, int nc
         } else if (k == kNIfce) {
             acc += a.dIf[li];
         } else if (k > kNIfce) {
-            // grid k >= 4: the 2^(k-3) x 2^(k-3) grid-3 cells under (r, c), plane k-3 of Q
-            const int sh = k - kNIfce, h3 = g.h[kNIfce], w3 = g.w[kNIfce];
-            const float* plane = a.dIf + (int64_t)sh * h3 * w3;
+            // grid k >= 4: the 2^(k-3) x 2^(k-3) grid-3 cells under (r, c), plane k-3 of Q;
+            // hyperlatent grid k = 7 + q: the grid of level 4 + q, plane 4 + q
+            const int lev = k < kL ? k : kHB + (k - kL);
+            const int sh = lev - kNIfce, h3 = g.h[kNIfce], w3 = g.w[kNIfce];
+            const float* plane = a.dIf + (int64_t)(k < kL ? sh : k - kNIfce) * h3 * w3;
             const int r0 = r << sh, c0 = c << sh;
             acc += sh == 1 ? block_sum_clipped<2>(plane, h3, w3, r0, c0)
                  : sh == 2 ? block_sum_clipped<4>(plane, h3, w3, r0, c0)
@@ -251,14 +256,15 @@ __global__ void __launch_bounds__(256, 4) k_gather_b(Batch<GatherArgs> b) {
 // moments, parameter) are loaded before the partials, so their round trip overlaps.  A job has
 // kReduceCtas CTAs.
 // ---------------------------------------------------------------------------------------------
-constexpr int kReduceCtas = (po::total + 31) / 32;
+constexpr int kReduceCtas = (po::total_h + 31) / 32;  // CTAs past the job's parameters return
 constexpr int kReduceThreads = 1024, kReduceWarps = kReduceThreads / 32;
 
 __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
     __shared__ float red[kReduceWarps][33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int p = cta * 32 + lane;
-    const bool adam = !a.grad_out && wid == 0 && p < po::total;
+    const int n_par = a.hyper ? po::total_h : po::total;
+    const bool adam = !a.grad_out && wid == 0 && p < n_par;
     int64_t step = 0;
     float m0 = 0.f, v0 = 0.f, p0 = 0.f;
     if (adam) {
@@ -268,13 +274,18 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
         p0 = a.params[p];
     }
     float acc = 0.f;
-    if (p < po::total) {
+    if (p < n_par) {
         const float* base;
         int64_t stride;
         int cnt;
+        const int arm_row = a.hyper ? po::arm_block_h : po::arm_block;
         if (p < po::up) {
             base = a.garm + p;
-            stride = po::arm_block;
+            stride = arm_row;
+            cnt = a.n_arm;
+        } else if (p >= po::total) {  // hyperlatent IFCE weights: entries 756.. of the ARM rows
+            base = a.garm + po::arm_block + (p - po::ifce_h);
+            stride = arm_row;
             cnt = a.n_arm;
         } else if (p < po::syn_w1) {
             const int st = (p - po::up) >> 2;
@@ -305,7 +316,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
     }
     red[wid][lane] = acc;
     __syncthreads();
-    if (wid != 0 || p >= po::total) return;
+    if (wid != 0 || p >= n_par) return;
     float gsum = 0.f;
 #pragma unroll
     for (int w = 0; w < kReduceWarps; ++w) gsum += red[w][lane];
@@ -396,14 +407,15 @@ __global__ void k_mark_base(const int64_t* step_dev, int64_t* base_step) { *base
 // the hash at (seed, step -2, p); bicubic taps; every other parameter, the moments and the step 0.
 // (Negative steps: the encoder's own draws use steps >= 0.)
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ float init_param(uint64_t seed, int p) {
-    int fan = 0;
+__device__ __forceinline__ float init_param(uint64_t seed, int p, int nh) {
+    int fan = 0;  // an IFCE's fan-in counts its hyperlatent inputs when there are some
     if (p >= po::arm_w1 && p < po::arm_b1) fan = 20;
     else if (p >= po::arm_w2 && p < po::arm_b2) fan = 16;
-    else if (p >= po::if_w0 && p < po::if_b0) fan = ifce_nin(0);
-    else if (p >= po::if_w1 && p < po::if_b1) fan = ifce_nin(1);
-    else if (p >= po::if_w2 && p < po::if_b2) fan = ifce_nin(2);
+    else if (p >= po::if_w0 && p < po::if_b0) fan = ifce_nin(0) + nh;
+    else if (p >= po::if_w1 && p < po::if_b1) fan = ifce_nin(1) + nh;
+    else if (p >= po::if_w2 && p < po::if_b2) fan = ifce_nin(2) + nh;
     else if (p >= po::syn_w1 && p < po::syn_b1) fan = 7;
+    else if (p >= po::ifce_h) fan = ifce_nin((p - po::ifce_h) / (kF * kNH)) + nh;
     if (fan) return 2.f * counter_uniform(seed, -2, p) / sqrtf((float)fan);
     if (p >= po::up && p < po::syn_w1) {  // Keys cubic (a = -0.75) at 1.75, 1.25, 0.75, 0.25
         const int j = (p - po::up) & 3;
@@ -412,7 +424,8 @@ __device__ __forceinline__ float init_param(uint64_t seed, int p) {
     return 0.f;
 }
 __global__ void k_init_state(const __grid_constant__ InitArgs a) {
-    const int64_t n_all = a.N + po::total;
+    const int n_par = a.nh ? po::total_h : po::total;
+    const int64_t n_all = a.N + n_par;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_all; e += (int64_t)gridDim.x * blockDim.x) {
         if (e < a.N) {
             a.y[e] = 0.01f * counter_gauss(a.seed, -1, e);
@@ -420,7 +433,7 @@ __global__ void k_init_state(const __grid_constant__ InitArgs a) {
             a.v_lat[e] = 0.f;
         } else {
             const int p = (int)(e - a.N);
-            a.params[p] = init_param(a.seed, p);
+            a.params[p] = init_param(a.seed, p, a.nh);
             a.m_par[p] = 0.f;
             a.v_par[p] = 0.f;
         }
@@ -490,6 +503,7 @@ ReduceArgs reduce_args(const Work& w, float* params, float* m, float* v, float* 
                        const Hp& hp, const int64_t* step_dev) {
     ReduceArgs a;
     a.gsoap = w.grad_params;
+    a.hyper = w.g.nh > 0 ? 1 : 0;
     a.garm = w.gpart_arm;
     a.gup = w.gpart_up;
     a.gsyn = w.gpart_syn;
@@ -528,7 +542,7 @@ FinishArgs finish_args(const Work& w, const Hp& hp, int have_arm, int have_conv,
 }
 
 int relax_ctas(const Work& w) { return grid_for(w.N, 256, 8); }
-int ifce_ctas(const Work& w) { return grid_for(32 * (int64_t)w.g.h[kNIfce] * w.g.w[kNIfce], 128, 16); }
+int ifce_ctas(const Work& w) { return grid_for(8 * (4 + w.g.nh) * (int64_t)w.g.h[kNIfce] * w.g.w[kNIfce], 128, 16); }
 int gather_ctas(const Work& w) { return grid_for(w.N, 256, 4); }  // one wave at 4 CTAs per SM
 int reduce_ctas() { return kReduceCtas; }
 
@@ -557,7 +571,7 @@ void launch_finish(const Work& w, const Hp& hp, int have_arm, int have_conv, dou
 }
 
 void launch_init_state(const InitArgs& a, cudaStream_t s) {
-    k_init_state<<<grid_for(a.N + po::total, 256, 8), 256, 0, s>>>(a);
+    k_init_state<<<grid_for(a.N + po::total_h, 256, 8), 256, 0, s>>>(a);
 }
 
 void launch_mark_base(const Work& w, const int64_t* step_dev, cudaStream_t s) {

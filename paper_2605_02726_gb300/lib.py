@@ -23,7 +23,7 @@ N_PARAMS = 1415
 class Arch(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("C", "H", "W", "L", "n_ctx", "ifce_dim", "ifce_grids",
                                               "arm_hidden", "arm_layers", "syn_hidden", "n_resconv",
-                                              "up_taps", "stabilizer")]
+                                              "up_taps", "stabilizer", "hyper_grids")]
 
 
 class HParams(ctypes.Structure):
@@ -173,10 +173,21 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def arch(H: int, W: int) -> Arch:
+N_PARAMS_H = 1451  # with hyperlatent grids: + the IFCE weights of their inputs
+N_HYPER_GRIDS = 3
+
+
+def arch(H: int, W: int, hyper: bool = False) -> Arch:
+    """The library's architecture for an H x W image; hyper: three hyperlatent grids (Sec. III-A3)."""
     a = Arch()
     _check(_lib.coolchic_arch_init(ctypes.byref(a), H, W), "arch_init")
+    a.hyper_grids = N_HYPER_GRIDS if hyper else 0
     return a
+
+
+def _hy(params) -> bool:
+    """A parameter vector of 1451 values carries the hyperlatent IFCE block."""
+    return int(params.numel()) == N_PARAMS_H
 
 
 CC_NOISE_UNIFORM, CC_NOISE_SOFTROUND = 0, 1
@@ -214,8 +225,8 @@ def soap_state_floats() -> int:
     return int(_lib.coolchic_soap_state_floats())
 
 
-def latent_count(H: int, W: int) -> int:
-    return int(_lib.coolchic_latent_count(ctypes.byref(arch(H, W))))
+def latent_count(H: int, W: int, hyper: bool = False) -> int:
+    return int(_lib.coolchic_latent_count(ctypes.byref(arch(H, W, hyper))))
 
 
 def kernel_launches(H: int, W: int, n_iters: int) -> int:
@@ -236,11 +247,12 @@ def param_blocks():
     return out
 
 
-def workspace(H: int, W: int, store_activations: bool = False, device=None, host_io: bool = False) -> torch.Tensor:
+def workspace(H: int, W: int, store_activations: bool = False, device=None, host_io: bool = False,
+              hyper: bool = False) -> torch.Tensor:
     """Device workspace for one job (256-byte aligned byte tensor); host_io adds the room
     encode_step_host needs."""
     flags = (1 if store_activations else 0) | (2 if host_io else 0)
-    n = int(_lib.coolchic_workspace_bytes(ctypes.byref(arch(H, W)), flags))
+    n = int(_lib.coolchic_workspace_bytes(ctypes.byref(arch(H, W, hyper)), flags))
     if n == 0:
         raise CoolChicError(_lib.coolchic_last_error().decode())
     buf = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
@@ -269,13 +281,14 @@ class EncoderState:
                      self.soap.data_ptr() if self.soap is not None else None)
 
     @staticmethod
-    def init(H: int, W: int, seed: int, device=None, stream=None) -> "EncoderState":
+    def init(H: int, W: int, seed: int, device=None, stream=None, hyper: bool = False, soap: bool = False) -> "EncoderState":
         """A fresh state initialised on the device by coolchic_init_state (seeded: latents
         0.01 N(0, 1), hidden weights U(+-1/sqrt(fan_in)), bicubic taps, the rest zero)."""
         dev = torch.device(device or "cuda")
-        a = arch(H, W)
+        a = arch(H, W, hyper)
         n_par = int(_lib.coolchic_param_count(ctypes.byref(a)))
-        st = EncoderState(torch.empty(latent_count(H, W), device=dev), torch.empty(n_par, device=dev))
+        st = EncoderState(torch.empty(latent_count(H, W, hyper), device=dev), torch.empty(n_par, device=dev),
+                          soap=soap)
         cs = st.c_state()
         _check(_lib.coolchic_init_state(ctypes.byref(a), int(seed), ctypes.byref(cs), _stream(stream)), "init_state")
         return st
@@ -290,7 +303,7 @@ class EncoderState:
 
 def encode_step(image, state: EncoderState, n_iters: int, *, H, W, hp: HParams, ws, rd=None, stream=None):
     """n_iters encoder iterations in place; rd (optional, float64 [n_iters, 3]) gets loss/rate/mse."""
-    a = arch(H, W)
+    a = arch(H, W, _hy(state.params))
     cs = state.c_state()
     _check(_lib.coolchic_encode_step(ctypes.byref(a), ctypes.byref(hp), _ptr(image), ctypes.byref(cs), n_iters,
                                      _ptr(rd), _ptr(ws), ws.numel(), _stream(stream)), "encode_step")
@@ -301,7 +314,7 @@ def encode_step_host(image_host, state: EncoderState, n_iters: int, *, H, W, hp:
     """encode_step on a host image (CPU tensor, pinned for an asynchronous copy); the last
     iteration's (loss, rate, mse) lands in rd_host (CPU float64 [3], nullable) once the stream has
     reached it.  ws must come from workspace(..., host_io=True)."""
-    a = arch(H, W)
+    a = arch(H, W, _hy(state.params))
     cs = state.c_state()
     _check(_lib.coolchic_encode_step_host(ctypes.byref(a), ctypes.byref(hp), _host_ptr(image_host), ctypes.byref(cs),
                                           n_iters, _host_ptr(rd_host), _ptr(ws), ws.numel(), _stream(stream)),
@@ -310,7 +323,7 @@ def encode_step_host(image_host, state: EncoderState, n_iters: int, *, H, W, hp:
 
 def forward(image, latents, params, *, H, W, hp: HParams, step=0, relax=CC_RELAX_NOISE, ws, store=False,
             rd=None, xhat=None, stream=None):
-    a = arch(H, W)
+    a = arch(H, W, _hy(params))
     _check(_lib.coolchic_forward(ctypes.byref(a), ctypes.byref(hp), _ptr(image), _ptr(latents), _ptr(params),
                                  int(step), relax, 1 if store else 0, _ptr(rd), _ptr(xhat), _ptr(ws), ws.numel(),
                                  _stream(stream)), "forward")
@@ -318,14 +331,14 @@ def forward(image, latents, params, *, H, W, hp: HParams, step=0, relax=CC_RELAX
 
 def backward(image, latents, params, grad_latents, grad_params, *, H, W, hp: HParams, step=0,
              relax=CC_RELAX_NOISE, ws, use_stored=False, grad_scale=1.0, stream=None):
-    a = arch(H, W)
+    a = arch(H, W, _hy(params))
     _check(_lib.coolchic_backward(ctypes.byref(a), ctypes.byref(hp), _ptr(image), _ptr(latents), _ptr(params),
                                   int(step), relax, 1 if use_stored else 0, float(grad_scale), _ptr(grad_latents),
                                   _ptr(grad_params), _ptr(ws), ws.numel(), _stream(stream)), "backward")
 
 
 def rate_distortion(image, latents, params, *, H, W, hp: HParams, step=0, relax=CC_RELAX_HARD, ws, stream=None):
-    a = arch(H, W)
+    a = arch(H, W, _hy(params))
     out = RD()
     _check(_lib.coolchic_rate_distortion(ctypes.byref(a), ctypes.byref(hp), _ptr(image), _ptr(latents),
                                          _ptr(params), int(step), relax, ctypes.byref(out), _ptr(ws), ws.numel(),
@@ -346,7 +359,7 @@ def rate_distortion_noalloc(image, latents, params, *, H, W, hp: HParams, step=0
 
 
 def decode_image(q_latents, params, *, H, W, ws, image_out=None, prob=None, mu_q=None, logb_q=None, stream=None):
-    a = arch(H, W)
+    a = arch(H, W, _hy(params))
     _check(_lib.coolchic_decode_image(ctypes.byref(a), _ptr(q_latents), _ptr(params), _ptr(image_out), _ptr(prob),
                                       _ptr(mu_q), _ptr(logb_q), _ptr(ws), ws.numel(), _stream(stream)),
            "decode_image")
@@ -366,9 +379,9 @@ class BatchEncoder:
             raise ValueError("empty batch")
         self.shapes = [(int(img.shape[1]), int(img.shape[2])) for img, _, _ in self.jobs]
         dev = device or self.jobs[0][0].device
-        self.workspaces = list(workspaces) if workspaces is not None else [workspace(H, W, device=dev)
-                                                                           for H, W in self.shapes]
-        archs = (Arch * n)(*[arch(H, W) for H, W in self.shapes])
+        self.workspaces = list(workspaces) if workspaces is not None else [
+            workspace(H, W, device=dev, hyper=_hy(st.params)) for (H, W), (_, st, _) in zip(self.shapes, self.jobs)]
+        archs = (Arch * n)(*[arch(H, W, _hy(st.params)) for (H, W), (_, st, _) in zip(self.shapes, self.jobs)])
         hps = (HParams * n)(*[hp for _, _, hp in self.jobs])
         images = (ctypes.c_void_p * n)(*[img.data_ptr() for img, _, _ in self.jobs])
         states = (State * n)(*[st.c_state() for _, st, _ in self.jobs])

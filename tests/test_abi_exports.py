@@ -42,7 +42,16 @@ def test_host_sizing_agrees_with_oracle_and_generator(lib):
     assert lib.raw().coolchic_param_count(ctypes.byref(a)) == oracle.N_PARAMS == inputs.N_PARAMS
     blocks = lib.param_blocks()
     assert [(n, o, l) for n, o, l in blocks] == [
-        (n, inputs.PARAM_OFFSETS[n][0], int(__import__("numpy").prod(s))) for n, s in inputs.PARAM_BLOCKS]
+        (n, inputs.PARAM_OFFSETS[n][0], int(__import__("numpy").prod(s))) for n, s in inputs.PARAM_BLOCKS] + [
+        (inputs.HYPER_BLOCK[0], inputs.N_PARAMS, 36)]
+    # with hyperlatent grids: three more grids (shapes of grids 4..6) and 36 more parameters
+    ah = lib.arch(512, 768, hyper=True)
+    assert lib.raw().coolchic_param_count(ctypes.byref(ah)) == oracle.N_PARAMS_H == inputs.N_PARAMS_H
+    for H, W in [(64, 64), (37, 53), (1, 1), (2048, 1365)]:
+        assert lib.latent_count(H, W, True) == oracle.latent_count(H, W, True) == inputs.latent_count(H, W, True)
+        assert [tuple(s) for s in oracle.grid_shapes(H, W, True)] == inputs.grid_shapes(H, W, hyper=True)
+    ah.hyper_grids = 2
+    assert lib.raw().coolchic_latent_count(ctypes.byref(ah)) == -1
 
 
 def test_argument_checks_fail_cleanly(lib):

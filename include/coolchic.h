@@ -230,6 +230,16 @@ int coolchic_batch_create(int32_t n_jobs, const cc_arch_t* archs, const cc_hpara
                           const float* const* images, const cc_state_t* states, void* const* workspaces,
                           const size_t* workspace_bytes, const cc_schedule_t* schedule,
                           int32_t rd_capacity, void* table, size_t table_bytes, cc_batch_t** batch);
+/* coolchic_batch_create for a caller that keeps the GPU busy while it plans (a serving loop):
+ * the plan is written to `host_staging` [host, pinned, coolchic_batch_table_bytes bytes] and
+ * copied to `table` by a cudaMemcpyAsync on `stream`, so the call returns without waiting for
+ * the device; host_staging and table must stay untouched until the stream has passed the copy,
+ * and the batch's first step must be ordered after it (same stream).  Nothing here blocks. */
+int coolchic_batch_create_async(int32_t n_jobs, const cc_arch_t* archs, const cc_hparams_t* hps,
+                                const float* const* images, const cc_state_t* states, void* const* workspaces,
+                                const size_t* workspace_bytes, const cc_schedule_t* schedule,
+                                int32_t rd_capacity, void* table, size_t table_bytes, void* host_staging,
+                                void* stream, cc_batch_t** batch);
 int coolchic_batch_step(cc_batch_t* batch, int32_t n_iters, void* stream);
 const cc_rd_t* coolchic_batch_records(const cc_batch_t* batch);
 int coolchic_batch_destroy(cc_batch_t* batch);

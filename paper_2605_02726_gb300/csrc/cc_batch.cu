@@ -95,10 +95,16 @@ size_t coolchic_batch_table_bytes(int32_t n_jobs, int32_t rd_capacity) {
     return table_bytes(n_jobs, rd_capacity);
 }
 
-int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t* hps, const float* const* images,
-                          const cc_state_t* states, void* const* workspaces, const size_t* ws_bytes,
-                          const cc_schedule_t* sched, int32_t rd_capacity, void* table, size_t table_size,
-                          cc_batch_t** out) {
+}  // extern "C"
+
+namespace cc {
+namespace {
+// Plans the batch; the table image is uploaded synchronously, or (host_staging non-null) written
+// to the pinned host_staging and copied asynchronously on `stream`.
+int batch_create_impl(int32_t n, const cc_arch_t* archs, const cc_hparams_t* hps, const float* const* images,
+                      const cc_state_t* states, void* const* workspaces, const size_t* ws_bytes,
+                      const cc_schedule_t* sched, int32_t rd_capacity, void* table, size_t table_size,
+                      void* host_staging, cudaStream_t stream, cc_batch_t** out) {
     if (n < 1 || !archs || !hps || !images || !states || !workspaces || !ws_bytes || !out || rd_capacity < 0)
         return set_error(CC_ERR_ARG, "batch_create: invalid arguments");
     if (!table || ((uintptr_t)table & 255)) return set_error(CC_ERR_WORKSPACE, "batch_create: table NULL or not 256-byte aligned");
@@ -228,13 +234,40 @@ int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t*
     place(b->finish, base);
     b->rd = rd_capacity > 0 ? reinterpret_cast<double*>(base + rd_off) : nullptr;
     b->table = base;
-    cudaError_t e = cudaMemcpy(table, tw.host.data(), tw.host.size(), cudaMemcpyHostToDevice);
+    cudaError_t e;
+    if (host_staging) {
+        std::memcpy(host_staging, tw.host.data(), tw.host.size());
+        e = cudaMemcpyAsync(table, host_staging, tw.host.size(), cudaMemcpyHostToDevice, stream);
+    } else {
+        e = cudaMemcpy(table, tw.host.data(), tw.host.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         delete b;
         return set_error(CC_ERR_CUDA, "batch_create: table upload: %s", cudaGetErrorString(e));
     }
     *out = b;
     return CC_OK;
+}
+}  // namespace
+}  // namespace cc
+
+extern "C" {
+
+int coolchic_batch_create(int32_t n, const cc_arch_t* archs, const cc_hparams_t* hps, const float* const* images,
+                          const cc_state_t* states, void* const* workspaces, const size_t* ws_bytes,
+                          const cc_schedule_t* sched, int32_t rd_capacity, void* table, size_t table_size,
+                          cc_batch_t** out) {
+    return batch_create_impl(n, archs, hps, images, states, workspaces, ws_bytes, sched, rd_capacity, table,
+                             table_size, nullptr, nullptr, out);
+}
+
+int coolchic_batch_create_async(int32_t n, const cc_arch_t* archs, const cc_hparams_t* hps,
+                                const float* const* images, const cc_state_t* states, void* const* workspaces,
+                                const size_t* ws_bytes, const cc_schedule_t* sched, int32_t rd_capacity, void* table,
+                                size_t table_size, void* host_staging, void* stream, cc_batch_t** out) {
+    if (!host_staging) return set_error(CC_ERR_ARG, "batch_create_async: NULL host staging buffer");
+    return batch_create_impl(n, archs, hps, images, states, workspaces, ws_bytes, sched, rd_capacity, table,
+                             table_size, host_staging, (cudaStream_t)stream, out);
 }
 
 int coolchic_batch_step(cc_batch_t* b, int32_t n_iters, void* stream) {

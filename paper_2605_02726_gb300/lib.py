@@ -80,6 +80,7 @@ def _load():
         "coolchic_rate_distortion_noalloc": (i32, [P(Arch), P(HParams), vp, vp, vp, i64, i32, P(RD), vp]),
         "coolchic_batch_table_bytes": (sz, [i32, i32]),
         "coolchic_batch_create": (i32, [i32, vp, vp, vp, vp, vp, vp, P(Schedule), i32, vp, sz, P(vp)]),
+        "coolchic_batch_create_async": (i32, [i32, vp, vp, vp, vp, vp, vp, P(Schedule), i32, vp, sz, vp, vp, P(vp)]),
         "coolchic_batch_step": (i32, [vp, i32, vp]),
         "coolchic_batch_records": (vp, [vp]),
         "coolchic_batch_destroy": (i32, [vp]),
@@ -106,7 +107,8 @@ EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count
             "coolchic_timing_disable", "coolchic_last_error", "coolchic_version",
             "coolchic_rate_distortion_noalloc", "coolchic_batch_table_bytes", "coolchic_batch_create",
             "coolchic_batch_step", "coolchic_batch_records", "coolchic_batch_destroy", "coolchic_measure_peak",
-            "coolchic_encode_step_host", "coolchic_soap_state_floats"]
+            "coolchic_encode_step_host", "coolchic_soap_state_floats",
+            "coolchic_batch_create_async"]
 
 KERNEL_ARM, KERNEL_SYN_BWD, KERNEL_CONV, KERNEL_SYN_FWD = 0, 1, 2, 3
 KERNEL_UP_FWD, KERNEL_UP_ADJ, KERNEL_GATHER = 4, 5, 6
@@ -372,7 +374,9 @@ class BatchEncoder:
     workspace; the plan table lives in a device buffer owned by this object.  `step(n)` is
     asynchronous; `graph(n)` captures n iterations in a CUDA graph for replay."""
 
-    def __init__(self, jobs, schedule=None, rd_capacity=1, device=None, workspaces=None):
+    def __init__(self, jobs, schedule=None, rd_capacity=1, device=None, workspaces=None, stream=None):
+        """stream: plan without blocking (coolchic_batch_create_async): the table is copied on
+        that stream from a pinned staging buffer, and the batch's steps must run on it."""
         self.jobs = list(jobs)
         n = len(self.jobs)
         if n == 0:
@@ -394,11 +398,18 @@ class BatchEncoder:
         self.rd_capacity = rd_capacity
         self.schedule = schedule
         handle = ctypes.c_void_p()
-        torch.cuda.synchronize(dev)
-        _check(_lib.coolchic_batch_create(n, archs, hps, images, states, wss, wsb,
-                                          ctypes.byref(schedule) if schedule is not None else None,
-                                          rd_capacity, ctypes.c_void_p(self.table.data_ptr()), tb,
-                                          ctypes.byref(handle)), "batch_create")
+        sched = ctypes.byref(schedule) if schedule is not None else None
+        if stream is None:
+            torch.cuda.synchronize(dev)
+            _check(_lib.coolchic_batch_create(n, archs, hps, images, states, wss, wsb, sched, rd_capacity,
+                                              ctypes.c_void_p(self.table.data_ptr()), tb, ctypes.byref(handle)),
+                   "batch_create")
+        else:
+            self.staging = torch.empty(tb, dtype=torch.uint8).pin_memory()  # kept alive with the batch
+            _check(_lib.coolchic_batch_create_async(n, archs, hps, images, states, wss, wsb, sched, rd_capacity,
+                                                    ctypes.c_void_p(self.table.data_ptr()), tb,
+                                                    ctypes.c_void_p(self.staging.data_ptr()), _stream(stream),
+                                                    ctypes.byref(handle)), "batch_create_async")
         self.handle = handle
 
     def step(self, n_iters=1, stream=None):

@@ -2,22 +2,31 @@
 
 Encode requests (an image, lambda, a seed, an iteration budget) arrive over time.  A request is
 admitted when its device memory (image, latents, parameters, Adam state, workspace) fits in the
-HBM budget next to the jobs already running; admitted jobs stay resident on the device and advance
-together: every tick runs `tick_iters` encoder iterations of all active jobs through the batched
-launches (one launch per kernel for the whole set).  A job leaves when it has done its iterations
-(its final state and loss are copied to the host) or is cancelled; its memory is released and the
-next queued requests are admitted at the following tick.  Each job's trajectory is the one it
-would have alone: jobs never share state, and a job's kernels see only its own buffers.
+HBM budget next to the jobs already resident; admitted jobs stay resident on the device and advance
+together: every tick runs up to `tick_iters` encoder iterations of all active jobs through the
+batched launches (one launch per kernel for the whole set).  A job leaves when it has done its
+iterations (its final state and last loss record are copied to the host) or is cancelled; its
+memory is released and queued requests are admitted.  Each job's trajectory is the one it would
+have alone: jobs never share state, and a job's kernels see only its own buffers.
 
-`python -m paper_2605_02726_gb300.serve` runs the Poisson-arrival benchmark (rates 2, 8, 32
-requests/s; sizes 512x768, 1024x1024, 2048x1365, 2048x2048 weighted .4/.3/.2/.1; lambda in
-{1e-4, 1e-3, 1e-2}; 5000 iterations per request; 80 GB budget) and prints one JSON line per rate
-with p50/p99 latency and images/s.
+Ticks are pipelined: `run` keeps up to two ticks queued on the GPU stream.  While tick t runs, the
+host retires tick t-1 (copies the finished jobs' results on a side stream ordered after that tick
+alone, releases their memory), admits new arrivals and plans tick t+1; a job's iteration count is
+known in advance, so the jobs that finish with tick t are left out of tick t+1 before t completes.
+A membership change builds the next plan with the non-blocking coolchic_batch_create_async (the
+plan is copied on the stream from a pinned buffer), so the GPU never waits for the host between
+ticks.  The latency of a request runs from its arrival to the host's retirement of its last tick.
+
+`python -m paper_2605_02726_gb300.serve` runs the Poisson-arrival benchmark (sizes 512x768,
+1024x1024, 2048x1365, 2048x2048 weighted .4/.3/.2/.1; lambda in {1e-4, 1e-3, 1e-2}; 80 GB budget;
+`--requests` per offered rate) and prints one JSON line per rate with p50/p99 latency, the
+offered and the served request rates and pixel-iterations per second.
 """
 from __future__ import annotations
 
 import argparse
 import collections
+import ctypes
 import json
 import math
 import time
@@ -33,11 +42,12 @@ def job_bytes(H: int, W: int) -> int:
     """Device bytes a resident job holds: image, state (latents, params, Adam moments, step),
     and its workspace."""
     n = cc.latent_count(H, W)
-    ws = int(cc._lib.coolchic_workspace_bytes(__import__("ctypes").byref(cc.arch(H, W)), 0))
+    ws = int(cc._lib.coolchic_workspace_bytes(ctypes.byref(cc.arch(H, W)), 0))
     return 4 * 3 * H * W + 4 * 3 * n + 4 * 3 * cc.N_PARAMS + 8 + ws + 512
 
 
 Request = collections.namedtuple("Request", "rid arrival H W lam seed iters image")
+Tick = collections.namedtuple("Tick", "event batch jobs n finishing")
 
 
 class Job:
@@ -48,28 +58,36 @@ class Job:
         self.state = cc.EncoderState(torch.tensor(lat, device=device), torch.tensor(par, device=device))
         self.hp = cc.hparams(lam=req.lam, seed=req.seed)
         self.ws = cc.workspace(req.H, req.W, device=device)
-        self.done_iters = 0
+        self.done_iters = 0     # iterations retired
+        self.planned = 0        # iterations queued on the GPU
         self.bytes = job_bytes(req.H, req.W)
         self.admitted = None
         self.finished = None
         self.last_rd = None
+        self.final = None
+        self.cancelled = False
 
 
 class EncodeServer:
-    def __init__(self, hbm_budget: int, tick_iters: int = 50, schedule=None, device="cuda"):
+    def __init__(self, hbm_budget: int, tick_iters: int = 50, schedule=None, device="cuda", max_inflight: int = 2):
         self.budget = int(hbm_budget)
         self.tick_iters = int(tick_iters)
         self.schedule = schedule
         self.device = torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device)
+        self.copy_stream = torch.cuda.Stream(self.device)
+        self.max_inflight = max(1, int(max_inflight))
         self.queue: collections.deque = collections.deque()
         self.active: list[Job] = []
         self.done: dict[int, Job] = {}
         self.failed: dict[int, str] = {}
+        self.inflight: collections.deque = collections.deque()
         self.in_use = 0
         self.peak_in_use = 0
         self.batch = None
         self.batch_key = None
         self.ticks = 0
+        self.plans = 0
         self._next = 0
 
     # -- request intake -----------------------------------------------------------------------
@@ -93,22 +111,27 @@ class EncodeServer:
         return rid
 
     def cancel(self, rid: int) -> bool:
+        """Cancel a queued or resident request; a resident one leaves at its next tick boundary
+        (its memory is released once the ticks already queued have retired)."""
         for q in list(self.queue):
             if q.rid == rid:
                 self.queue.remove(q)
                 self.failed[rid] = "cancelled"
                 return True
         for j in self.active:
-            if j.req.rid == rid:
-                self._release(j)
+            if j.req.rid == rid and not j.cancelled:
+                j.cancelled = True
                 self.failed[rid] = "cancelled"
+                if not any(j in t.jobs for t in self.inflight):
+                    self._release(j)
                 return True
         return False
 
     # -- scheduling ---------------------------------------------------------------------------
     def _release(self, job: Job):
-        self.active.remove(job)
-        self.in_use -= job.bytes
+        if job in self.active:
+            self.active.remove(job)
+            self.in_use -= job.bytes
 
     def _admit(self, now: float):
         while self.queue and self.queue[0].arrival <= now:
@@ -122,68 +145,110 @@ class EncodeServer:
             self.in_use += job.bytes
             self.peak_in_use = max(self.peak_in_use, self.in_use)
 
-    def _plan(self):
-        key = tuple(j.req.rid for j in self.active)
+    def _plan(self, jobs):
+        key = tuple(j.req.rid for j in jobs)
         if key != self.batch_key:
-            if self.batch is not None:
-                self.batch.close()
-            jobs = [(j.image, j.state, j.hp) for j in self.active]
-            self.batch = cc.BatchEncoder(jobs, schedule=self.schedule, rd_capacity=self.tick_iters,
-                                         workspaces=[j.ws for j in self.active])
+            # the previous plan stays alive in the ticks that use it; a new one is uploaded on the
+            # stream without blocking
+            self.batch = cc.BatchEncoder([(j.image, j.state, j.hp) for j in jobs], schedule=self.schedule,
+                                         rd_capacity=self.tick_iters, workspaces=[j.ws for j in jobs],
+                                         stream=self.stream)
             self.batch_key = key
+            self.plans += 1
         return self.batch
 
-    def tick(self, now: float) -> int:
-        """Admit what fits, run one tick of iterations on all active jobs, retire finished ones.
-        Returns the number of iterations run (0 when idle)."""
-        self._admit(now)
-        if not self.active:
+    def _launch(self) -> int:
+        """Queue one tick of the jobs that still have iterations; returns its iteration count."""
+        jobs = [j for j in self.active if j.planned < j.req.iters and not j.cancelled]
+        if not jobs:
             return 0
-        n = min(self.tick_iters, min(j.req.iters - j.done_iters for j in self.active))
-        b = self._plan()
-        b.step(n)
-        torch.cuda.synchronize(self.device)
-        rec = b.records()
-        t_end = time.perf_counter()
-        for q, j in enumerate(list(self.active)):
-            j.done_iters += n
-            if j.done_iters >= j.req.iters:
-                j.last_rd = rec[n - 1, q].cpu().numpy()
-                j.final = (j.state.latents.cpu(), j.state.params.cpu())
-                j.finished = t_end
-                self.done[j.req.rid] = j
-                self._release(j)
+        n = min(self.tick_iters, min(j.req.iters - j.planned for j in jobs))
+        b = self._plan(jobs)
+        b.step(n, stream=self.stream)
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        finishing = []
+        for j in jobs:
+            j.planned += n
+            if j.planned >= j.req.iters:
+                finishing.append(j)
+        self.inflight.append(Tick(ev, b, jobs, n, finishing))
         self.ticks += 1
         return n
 
+    def _retire(self, t: Tick):
+        """Tick t has completed on the GPU: copy the finished jobs' results (on a side stream
+        ordered after this tick only), release their memory."""
+        t_end = time.perf_counter()
+        for j in t.jobs:
+            j.done_iters += t.n
+        if t.finishing:
+            q = {j: t.jobs.index(j) for j in t.finishing}
+            with torch.cuda.stream(self.copy_stream):
+                self.copy_stream.wait_event(t.event)
+                rec = t.batch.records()
+                for j in t.finishing:
+                    j.last_rd = rec[t.n - 1, q[j]].cpu().numpy()
+                    j.final = (j.state.latents.cpu(), j.state.params.cpu())
+            for j in t.finishing:
+                j.finished = t_end
+                if not j.cancelled:
+                    self.done[j.req.rid] = j
+                self._release(j)
+        for j in list(self.active):  # cancelled jobs leave once no queued tick uses them
+            if j.cancelled and not any(j in u.jobs for u in self.inflight):
+                self._release(j)
+
+    def _retire_ready(self, block: bool = False):
+        while self.inflight and (block or self.inflight[0].event.query()):
+            t = self.inflight.popleft()
+            t.event.synchronize()
+            self._retire(t)
+            block = False
+
+    def tick(self, now: float) -> int:
+        """Synchronous tick: admit what fits, run one tick of all active jobs, retire it.
+        Returns the number of iterations run (0 when idle)."""
+        self._retire_ready(block=True) if self.inflight else None
+        self._admit(now)
+        n = self._launch()
+        while self.inflight:
+            self._retire_ready(block=True)
+        return n
+
     def run(self, requests, t0: float | None = None, max_seconds: float | None = None):
-        """Serve (arrival_offset_s, image, lam, seed, iters) requests in real time."""
+        """Serve (arrival_offset_s, image, lam, seed, iters) requests in real time, with up to
+        max_inflight ticks queued on the GPU."""
         t0 = time.perf_counter() if t0 is None else t0
         pending = sorted(requests, key=lambda r: r[0])
         k = 0
-        while k < len(pending) or self.queue or self.active:
+        while k < len(pending) or self.queue or self.active or self.inflight:
             now = time.perf_counter()
             while k < len(pending) and t0 + pending[k][0] <= now:
                 off, img, lam, seed, iters = pending[k]
                 self.submit(img, lam, seed, iters, arrival=t0 + off)
                 k += 1
-            ran = self.tick(now)
-            if ran == 0 and not self.active:
-                if k < len(pending):
-                    time.sleep(max(0.0, min(0.01, t0 + pending[k][0] - time.perf_counter())))
-                elif self.queue:
-                    continue
+            self._retire_ready()
+            self._admit(now)
+            if len(self.inflight) < self.max_inflight and self._launch():
+                continue
+            if self.inflight:
+                self._retire_ready(block=True)  # the GPU is busy with everything there is
+            elif k < len(pending):
+                time.sleep(max(0.0, min(0.005, t0 + pending[k][0] - time.perf_counter())))
+            elif self.queue and not self.active:
+                continue
             if max_seconds is not None and time.perf_counter() - t0 > max_seconds:
                 break
-        if self.batch is not None:
-            self.batch.close()
-            self.batch = None
+        while self.inflight:
+            self._retire_ready(block=True)
+        self.batch = None
 
     def latencies(self):
         return {rid: j.finished - j.req.arrival for rid, j in self.done.items()}
 
 
-def benchmark(rates=(2.0, 8.0, 32.0), n_requests=6, iters=5000, budget_gb=80.0, tick_iters=50, seed0=inputs.SEED0):
+def benchmark(rates=(1.0, 4.0, 32.0), n_requests=64, iters=1000, budget_gb=80.0, tick_iters=50, seed0=inputs.SEED0):
     out = []
     for rate in rates:
         reqs = []
@@ -196,11 +261,15 @@ def benchmark(rates=(2.0, 8.0, 32.0), n_requests=6, iters=5000, budget_gb=80.0, 
         wall = time.perf_counter() - t0
         lat = np.array(sorted(srv.latencies().values()))
         pix = sum(r[1].shape[1] * r[1].shape[2] for r in reqs)
+        span = max(r[0] for r in reqs) - min(r[0] for r in reqs)
         out.append({
             "rate_offered_per_s": rate, "requests": n_requests, "iters_per_request": iters,
-            "served": len(srv.done), "images_per_s": len(srv.done) / wall,
+            "offered_requests_per_s": (n_requests - 1) / span if span > 0 else None,
+            "offered_mpix_iter_per_s": pix * iters / span / 1e6 if span > 0 else None,
+            "served": len(srv.done), "served_requests_per_s": len(srv.done) / wall,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "mpix_iter_per_s": pix * iters / wall / 1e6, "wall_s": wall, "ticks": srv.ticks,
+            "min_latency_s": float(lat[0]), "max_latency_s": float(lat[-1]),
+            "mpix_iter_per_s": pix * iters / wall / 1e6, "wall_s": wall, "ticks": srv.ticks, "plans": srv.plans,
             "peak_hbm_gb": srv.peak_in_use / 2 ** 30, "budget_gb": budget_gb,
         })
     return out
@@ -208,9 +277,9 @@ def benchmark(rates=(2.0, 8.0, 32.0), n_requests=6, iters=5000, budget_gb=80.0, 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("--rates", default="2,8,32")
-    ap.add_argument("--requests", type=int, default=6)
-    ap.add_argument("--iters", type=int, default=5000)
+    ap.add_argument("--rates", default="1,4,32")
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--iters", type=int, default=1000)
     ap.add_argument("--budget-gb", type=float, default=80.0)
     ap.add_argument("--tick-iters", type=int, default=50)
     a = ap.parse_args()

@@ -339,6 +339,14 @@ int coolchic_measure_peak(int32_t which, float* sink, double* tflops_out, double
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* coolchic_last_error(void);
 
+/* Failure-detection test hook (no counterpart in the paper).  While `on` is non-zero, entropy-model
+ * launches made from then on (not the replay of a graph captured before) withhold the commit of
+ * their first tensor-core MMA group, so that every wait on its completion runs out after about a
+ * second: the kernel then frees its Tensor Memory and ends, the loss record of the call is NaN, and
+ * the blocking coolchic_rate_distortion returns CC_ERR_TIMEOUT; the context stays usable.  No fault,
+ * trap or hang is involved.  Returns CC_OK. */
+int coolchic_test_inject_stall(int32_t on);
+
 /* Library version string. */
 const char* coolchic_version(void);
 

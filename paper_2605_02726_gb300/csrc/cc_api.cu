@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -180,6 +181,7 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
         W.se_part = (double*)(base + o_sp);
         W.grad_params = (float*)(base + o_gp);
         W.base_step = (int64_t*)(base + o_bs);
+        W.status = (int*)(base + o_bs + 2 * sizeof(int64_t));
         if (flags & 1) {
             W.act_arm = (float*)(base + o_aa);
             W.act_syn = (float*)(base + o_as);
@@ -237,6 +239,8 @@ void tend(int id, cudaStream_t s) {
 
 size_t layout_job(const cc_arch_t* arch, int flags, char* base, Work* w) { return build_work(arch, flags, base, w); }
 int device_setup_checked() { return device_setup(); }
+std::atomic<int> g_inject_stall{0};
+int test_inject_stall() { return g_inject_stall.load(); }
 
 int set_error(int code, const char* fmt, ...) {
     char buf[512];
@@ -543,6 +547,11 @@ int64_t coolchic_kernel_launches(const cc_arch_t* a, int32_t n_iters) {
 
 int64_t coolchic_soap_state_floats(void) { return soap_state_floats(); }
 
+int coolchic_test_inject_stall(int32_t on) {
+    g_inject_stall.store(on ? 1 : 0);
+    return CC_OK;
+}
+
 size_t coolchic_workspace_bytes(const cc_arch_t* a, int32_t flags) {
     if (check_arch(a)) return 0;
     if (device_setup()) return 0;
@@ -696,13 +705,20 @@ int coolchic_rate_distortion(const cc_arch_t* arch, const cc_hparams_t* hp, cons
     cudaStream_t s = (cudaStream_t)stream;
     const Hp h = to_hp(hp);
     double* rd_dev = (double*)w.grad_params;  // 3 doubles of scratch
+    cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(int), s);
+    if (e != cudaSuccess) return fail(CC_ERR_CUDA, "rate_distortion: %s", cudaGetErrorString(e));
     run_forward(w, image, latents, params, nullptr, step, h, relax, PASS_FWD, PASS_FWD, PASS_FWD, 0.f, 0.f,
                 nullptr, s);
     launch_finish(w, h, 1, 1, rd_dev, nullptr, 0, 0, s);
     if ((rc = launched("rate_distortion"))) return rc;
-    cudaError_t e = cudaMemcpyAsync(rd_out, rd_dev, sizeof(cc_rd_t), cudaMemcpyDeviceToHost, s);
+    int status = 0;
+    e = cudaMemcpyAsync(rd_out, rd_dev, sizeof(cc_rd_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(CC_ERR_CUDA, "rate_distortion readback: %s", cudaGetErrorString(e));
+    if (status & 1)
+        return fail(CC_ERR_TIMEOUT, "rate_distortion: a wait of the entropy model on its tensor-core work ran out "
+                                    "(about a second); the result is NaN and the context remains usable");
     return CC_OK;
 }
 

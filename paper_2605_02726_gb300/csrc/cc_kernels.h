@@ -102,6 +102,7 @@ struct Work {
     double* se_part;   // [n_cta_conv]
     float* grad_params;// [1415] reduced parameter gradient
     int64_t* base_step;// step at the start of an encode call
+    int* status;       // bit 0: a bounded wait in the entropy model ran out (cleared by blocking calls)
     float* io_image;   // device copy of a host image [3][HW] (workspace flag bit 1, else null)
     double* io_record; // one loss record (loss, rate, mse) read back to the host (flag bit 1)
     int n_cta_arm, n_cta_syn, n_cta_conv;
@@ -250,9 +251,15 @@ struct ArmArgs {
     float* dR2;
     float* dYd;
     float* act;         // [34][N]: a1 (16), a2 (16), mu, s
-    float* gpart;       // [n_cta][756]
+    float* gpart;       // [n_cta][756, or 792 with hyperlatents]
     double* rate_part;  // [n_cta]
+    int* status;        // bit 0 set when a wait on the MMA completion ran out
+    int inject_stall;   // failure-detection tests: the first MMA group is never committed
+    int pad3_;
 };
+// Failure-detection test hook (coolchic_test_inject_stall): launches made while it is set withhold
+// the entropy model's first MMA commit, so that its bounded waits run out.
+int test_inject_stall();
 struct SynArgs {
     Geom g;
     int64_t HW;

@@ -89,6 +89,7 @@ def _load():
         "coolchic_timing_disable": (i32, []),
         "coolchic_measure_peak": (i32, [i32, vp, P(ctypes.c_double), P(ctypes.c_double), vp]),
         "coolchic_soap_state_floats": (i64, []),
+        "coolchic_test_inject_stall": (i32, [i32]),
         "coolchic_last_error": (ctypes.c_char_p, []),
         "coolchic_version": (ctypes.c_char_p, []),
     }
@@ -108,7 +109,7 @@ EXPORTED = ["coolchic_arch_init", "coolchic_latent_count", "coolchic_param_count
             "coolchic_rate_distortion_noalloc", "coolchic_batch_table_bytes", "coolchic_batch_create",
             "coolchic_batch_step", "coolchic_batch_records", "coolchic_batch_destroy", "coolchic_measure_peak",
             "coolchic_encode_step_host", "coolchic_soap_state_floats",
-            "coolchic_batch_create_async"]
+            "coolchic_batch_create_async", "coolchic_test_inject_stall"]
 
 KERNEL_ARM, KERNEL_SYN_BWD, KERNEL_CONV, KERNEL_SYN_FWD = 0, 1, 2, 3
 KERNEL_UP_FWD, KERNEL_UP_ADJ, KERNEL_GATHER = 4, 5, 6

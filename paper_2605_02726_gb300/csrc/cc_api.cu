@@ -112,7 +112,7 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     W.N = g.off[kG];
     W.HW = (int64_t)a->H * a->W;
     const int sms = num_sms();
-    W.n_cta_arm = arm_grid(W.N);
+    W.n_cta_arm = arm_grid(W.N, W.g.nh > 0);
     {
         int64_t rounds = (W.HW + kSynThreads - 1) / kSynThreads;
         W.n_cta_syn = (int)(rounds < 3 * sms ? rounds : 3 * sms);  // 3 resident CTAs per SM

@@ -50,22 +50,36 @@
 namespace cc {
 namespace {
 
-constexpr int kT = 128;  // threads per CTA = latents per tile = MMA M
-constexpr int kWarps = kT / 32;
-constexpr uint32_t kTmemCols = 128;
-// Tensor Memory columns: the accumulator (every product of a tile in turn, at most 32 columns),
-// the A operand's hi and lo copies (at most 24 columns each)
-constexpr uint32_t TM_D = 0, TM_AH = 32, TM_AL = 64;
+constexpr int kT = 128;  // threads of a group = latents per tile = MMA M
+// One CTA per SM of kGroups groups of 128 threads (four warps, one per Tensor Memory lane
+// quarter); each group works through its own tiles with its own 128 Tensor Memory columns and
+// mbarrier, and the groups share the weights in shared memory.  (Several CTAs per SM each
+// allocating Tensor Memory cost about 2.7 us per extra CTA at launch; one CTA allocates once.)
+template <bool HY>
+constexpr int kGroups = HY ? 3 : 4;  // (the hyperlatent form needs more registers per thread)
+constexpr uint32_t kTmemCols = 512;
+// Tensor Memory columns: the A operand's hi and lo copies (at most 24 columns each) at 0 and 32,
+// the accumulator of the tile's products (each in turn, at most 32 columns) at 96, and in the
+// columns left over (24..31, 56..95) the parameter-gradient tiles 0..11 of this thread, kept there
+// between work units so that they hold no registers outside the gradient phase
+constexpr uint32_t TM_AH = 0, TM_AL = 32, TM_D = 96;
+constexpr int kTmTiles = 12;  // gradient tiles kept in Tensor Memory (a 13th stays in registers)
+__device__ __forceinline__ uint32_t tm_acc_col(int pair) { return pair == 0 ? 24u : 56u + 8u * (pair - 1); }
 constexpr long long kWaitLimit = 1ll << 31;                         // clock cycles (about 1 s)
 
 // Shared memory (dynamic), byte offsets.  B operands (weights) are K-major [N][K], a hi and a lo
 // copy each.
-constexpr int B1_N = 32, B1_K = 24;  // rows 0..15: W1 with b1 at k = 20; rows 16, 17: Ws; rest zero
+// B1 and B4 are N = 32 operands whose rows 24..31 (accumulator columns 24..31) are never used: only
+// rows 0..23 are stored (leading byte offset 24 * 16), so the MMA reads rows 24..31 of a K chunk from
+// rows 0..7 of the next one (of the next buffer, for the last chunk), and those columns hold
+// whatever results; this keeps a CTA's shared memory small enough for four CTAs per SM.
+constexpr int B1_N = 32, B1_K = 24;  // rows 0..15: W1 with b1 at k = 20; rows 16, 17: Ws; 18..23 zero
 constexpr int B2_N = 16, B2_K = 16;  // W2
 constexpr int B3_N = 16, B3_K = 16;  // W2^T
 constexpr int B4_N = 32, B4_K = 24;  // [W1^T | Ws^T]: row f, k < 16: W1[k][f], k = 16, 17: Ws[k-16][f]
-constexpr uint32_t B1_BYTES = B1_N * B1_K * 4, B2_BYTES = B2_N * B2_K * 4, B3_BYTES = B3_N * B3_K * 4,
-                   B4_BYTES = B4_N * B4_K * 4;
+constexpr int B14_ROWS = 24;         // stored rows of B1 and B4
+constexpr uint32_t B1_BYTES = B14_ROWS * B1_K * 4, B2_BYTES = B2_N * B2_K * 4, B3_BYTES = B3_N * B3_K * 4,
+                   B4_BYTES = B14_ROWS * B4_K * 4;
 constexpr int kSld = 36;                                  // staging row stride (32 latents + 4)
 constexpr uint32_t SM_B1 = 0, SM_B2 = SM_B1 + 2 * B1_BYTES, SM_B3 = SM_B2 + 2 * B2_BYTES,
                    SM_B4 = SM_B3 + 2 * B3_BYTES, SM_ST = SM_B4 + 2 * B4_BYTES;
@@ -78,11 +92,13 @@ template <bool HY>
 struct ArmLayout {
     static constexpr int st_rows = HY ? 80 : 72;
     static constexpr uint32_t st_bytes = st_rows * kSld * 4;
-    static constexpr uint32_t misc = SM_ST + kWarps * st_bytes;
+    static constexpr int warps = kGroups<HY> * kT / 32;
+    static constexpr uint32_t misc = SM_ST + warps * st_bytes;
     static constexpr int ms_n = MS_IFH + (HY ? po::ifce_h_n : 0);
     static constexpr uint32_t total = misc + ms_n * 4;
     static constexpr int tiles = HY ? 13 : 12;
     static_assert(st_bytes % 16 == 0, "16-byte alignment of the staging tiles");
+    static_assert(total + 2048 <= 227 * 1024, "shared memory of one CTA");
 };
 static_assert(SM_ST % 16 == 0, "16-byte alignment of the staging tiles");
 
@@ -151,9 +167,9 @@ __device__ __forceinline__ void store_a(uint32_t t_row, const float* v) {
 // D = A . B^T over K (multiple of 8) for the three hi/lo passes, A from Tensor Memory; one
 // thread.  The B descriptors are built once; a k-step advances their start-address field
 // (address / 16, no carry out of it: shared memory stays below 256 KB).
-template <int N, int K>
+template <int ROWS, int K>
 __device__ __forceinline__ void mma_group(uint32_t tmem, uint32_t sB, uint32_t idesc) {
-    constexpr uint32_t b_lbo = N * 16, b_bytes = N * K * 4;
+    constexpr uint32_t b_lbo = ROWS * 16, b_bytes = ROWS * K * 4;
     const uint64_t bh = umma_desc(sB, b_lbo, 128), bl = umma_desc(sB + b_bytes, b_lbo, 128);
 #pragma unroll
     for (int ks = 0; ks < K / 8; ++ks) {
@@ -162,6 +178,35 @@ __device__ __forceinline__ void mma_group(uint32_t tmem, uint32_t sB, uint32_t i
         umma_tf32_ts(tmem + TM_D, tmem + TM_AL + 8 * ks, bh + bo, idesc, 1u);
         umma_tf32_ts(tmem + TM_D, tmem + TM_AH + 8 * ks, bl + bo, idesc, 1u);
     }
+}
+
+// The gradient tiles 0..11 of this thread from / to Tensor Memory (two tiles per 8 columns).
+template <int NT>
+__device__ __forceinline__ void acc_from_tmem(uint32_t t_row, float (&acc)[NT][4]) {
+    uint32_t r[kTmTiles * 4];
+#pragma unroll
+    for (int p = 0; p < kTmTiles / 2; ++p) {
+        uint32_t q[8];
+        tmem_ld8_nowait(t_row + tm_acc_col(p), q);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r[8 * p + e] = q[e];
+    }
+    tmem_wait_ld(r);
+#pragma unroll
+    for (int T = 0; T < kTmTiles; ++T)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[T][e] = __uint_as_float(r[4 * T + e]);
+}
+template <int NT>
+__device__ __forceinline__ void acc_to_tmem(uint32_t t_row, const float (&acc)[NT][4]) {
+#pragma unroll
+    for (int p = 0; p < kTmTiles / 2; ++p) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = acc[2 * p + (e >> 2)][e & 3];
+        tmem_st8(t_row + tm_acc_col(p), v);
+    }
+    tmem_wait_st();
 }
 
 template <int PASS, bool HY>
@@ -173,13 +218,15 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     constexpr uint32_t ST_BYTES = LY::st_bytes;
     constexpr int kRR = HY ? 16 : 8;        // rows of the IFCE-input block
     constexpr int kOneCol = HY ? 6 + kNH : 6;  // its column of ones
+    constexpr int NG = kGroups<HY>, NT = NG * kT, NW = NT / 32;
     extern __shared__ __align__(1024) unsigned char smem[];
     float* sMisc = reinterpret_cast<float*>(smem + LY::misc);
     __shared__ Geom g;
     __shared__ float rcp_w[kG];
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar[NG];
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int grp = wid >> 2, gtid = tid & (kT - 1);  // group, thread (= latent row) in the group
     float* st = reinterpret_cast<float*>(smem + SM_ST + wid * ST_BYTES);  // this warp's staging tile
 
     if (tid == 0) g = a.g;
@@ -191,18 +238,18 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     if (hyper)
         Ph = stage_params(a.params, po::ifce_h, po::ifce_h_n, reinterpret_cast<float*>(smem + SM_ST) + po::arm_block);
     // B operands: element (n, k) of each, hi and lo
-    for (int e = tid; e < B1_N * B1_K; e += kT) {
+    for (int e = tid; e < B14_ROWS * B1_K; e += NT) {
         const int n = e / B1_K, k = e - n * B1_K;
         float v = 0.f;
         if (n < 16) v = k < 20 ? P[po::arm_w1 + n * 20 + k] : (k == 20 ? P[po::arm_b1 + n] : 0.f);
         else if (n < 18 && k < 20) v = P[po::arm_ws + (n - 16) * 20 + k];
         float h, l;
         split_f(v, h, l);
-        const uint32_t off = SM_B1 + kmajor_off(B1_N, n, k);
+        const uint32_t off = SM_B1 + kmajor_off(B14_ROWS, n, k);
         *reinterpret_cast<float*>(smem + off) = h;
         *reinterpret_cast<float*>(smem + off + B1_BYTES) = l;
     }
-    for (int e = tid; e < 16 * 16; e += kT) {
+    for (int e = tid; e < 16 * 16; e += NT) {
         const int n = e >> 4, k = e & 15;
         float h, l;
         split_f(P[po::arm_w2 + n * 16 + k], h, l);  // B2[n][k] = W2[n][k]
@@ -213,17 +260,17 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         *reinterpret_cast<float*>(smem + off) = h;
         *reinterpret_cast<float*>(smem + off + B3_BYTES) = l;
     }
-    for (int e = tid; e < B4_N * B4_K; e += kT) {
+    for (int e = tid; e < B14_ROWS * B4_K; e += NT) {
         const int n = e / B4_K, k = e - n * B4_K;  // B4[f][o] = W1[o][f], B4[f][16 + o] = Ws[o][f]
         float v = 0.f;
         if (n < 20) v = k < 16 ? P[po::arm_w1 + k * 20 + n] : (k < 18 ? P[po::arm_ws + (k - 16) * 20 + n] : 0.f);
         float h, l;
         split_f(v, h, l);
-        const uint32_t off = SM_B4 + kmajor_off(B4_N, n, k);
+        const uint32_t off = SM_B4 + kmajor_off(B14_ROWS, n, k);
         *reinterpret_cast<float*>(smem + off) = h;
         *reinterpret_cast<float*>(smem + off + B4_BYTES) = l;
     }
-    for (int j = tid; j < LY::ms_n; j += kT) {
+    for (int j = tid; j < LY::ms_n; j += NT) {
         float v;
         if (j < MS_W3) v = P[po::if_w0 + j];
         else if (j < MS_B2) v = P[po::arm_w3 + (j - MS_W3)];
@@ -233,9 +280,9 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         else v = hyper ? Ph[po::ifce_h + (j - MS_IFH)] : 0.f;
         sMisc[j] = v;
     }
-    const uint32_t mbar = smem_u32(&s_mbar);
-    if (tid == 0) {
-        mbar_init(mbar, 1);
+    const uint32_t mbar = smem_u32(&s_mbar[grp]);
+    if (tid < NG) {
+        mbar_init(smem_u32(&s_mbar[tid]), 1);
         mbar_init_fence();
     }
     if (wid == 0) tmem_alloc(smem_u32(&s_tmem), kTmemCols);
@@ -243,31 +290,33 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     tc_fence_before();
     __syncthreads();  // (the staged parameters are dead from here: the staging area is reused)
     tc_fence_after();
-    const uint32_t tmem = s_tmem;
-    const uint32_t t_row = tmem + ((uint32_t)(wid * 32) << 16);  // this warp's lanes
+    const uint32_t tmem = s_tmem + (uint32_t)(grp * kT);  // this group's 128 columns
+    const uint32_t t_row = tmem + ((uint32_t)((wid & 3) * 32) << 16);  // this warp's lanes
     const uint32_t sbase = smem_u32(smem);  // (B operand descriptors)
     uint32_t phase = 0;
     bool bad = false;
 
     // CTA 0 computes the coarse forward upsampling stages (it takes no tiles when there are other
     // CTAs), staged through the staging area; each stage ends with a barrier.
-    //   Tiles: with C CTAs in all, no CTA takes more than Q = ceil(tiles / C); CTAs 1.. take tiles
-    // [0, U1) round-robin (U1 = min(tiles, Q * (C - 1))) and CTA 0 only the rest.
+    //   Tiles, over the V = C * NG groups of the C CTAs: no group takes more than
+    // Q = ceil(tiles / V); the groups of CTAs 1.. take tiles [0, U1) round-robin
+    // (U1 = min(tiles, Q * (V - NG))) and the groups of CTA 0 only the rest.
     const int64_t N = a.N;
     const int n_tiles = (int)((N + kT - 1) / kT);
-    int t_first = cta, t_step = ncta, t_end = n_tiles;
+    int t_first = cta * NG + grp, t_step = ncta * NG, t_end = n_tiles;
     if (a.upc_on) {
-        if (cta == 0) coarse_upsampling(a, reinterpret_cast<float*>(smem + SM_ST), (int)(kWarps * ST_BYTES / 4));
+        if (cta == 0) coarse_upsampling(a, reinterpret_cast<float*>(smem + SM_ST), (int)(NW * ST_BYTES / 4));
         if (ncta > 1) {
-            const int q_max = (int)(((int64_t)n_tiles + ncta - 1) / ncta);
-            const int u1 = (int)std::min<int64_t>(n_tiles, (int64_t)q_max * (ncta - 1));
+            const int64_t v = (int64_t)ncta * NG;
+            const int64_t q_max = (n_tiles + v - 1) / v;
+            const int u1 = (int)std::min<int64_t>(n_tiles, q_max * (v - NG));
             if (cta > 0) {
-                t_first = cta - 1;
-                t_step = ncta - 1;
+                t_first = (cta - 1) * NG + grp;
+                t_step = (ncta - 1) * NG;
                 t_end = u1;
             } else {
-                t_first = u1;
-                t_step = 1;
+                t_first = u1 + grp;
+                t_step = NG;
             }
         }
     }
@@ -275,11 +324,12 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         st[46 * kSld + lane] = 0.f;
         st[47 * kSld + lane] = 0.f;
     }
-    float acc[kTiles][4];
-#pragma unroll
-    for (int T = 0; T < kTiles; ++T)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[T][q] = 0.f;
+    // gradient tile 12 (hyperlatent IFCE weights) in registers, tiles 0..11 in Tensor Memory
+    float acc12[4] = {0.f, 0.f, 0.f, 0.f};
+    if (BWD) {
+        const float zero[kTmTiles][4] = {};
+        acc_to_tmem(t_row, zero);
+    }
     float rate_acc = 0.f;
     const float4* W3v = reinterpret_cast<const float4*>(sMisc + MS_W3);  // W3 [2][16] as 8 float4
     const float4* B2v = reinterpret_cast<const float4*>(sMisc + MS_B2);  // b2 as 4 float4
@@ -292,15 +342,15 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         if (!ok) bad = true;
         tc_fence_after();
     };
-    // barrier before an MMA group: Tensor Memory stores and loads of every warp ordered before
-    // it; true when some thread of the CTA has given up
+    // barrier of the group before an MMA group: Tensor Memory stores and loads of its four warps
+    // ordered before it; true when some thread of the group has given up
     auto pre_mma = [&]() {
         tc_fence_before();
-        return __syncthreads_or(bad ? 1 : 0) != 0;
+        return group_sync_or(1 + grp, bad);
     };
 
     for (int tile = t_first; tile < t_end; tile += t_step) {
-        const int64_t i0 = (int64_t)tile * kT + tid;
+        const int64_t i0 = (int64_t)tile * kT + gtid;
         const bool valid = i0 < N;
         const int64_t i = valid ? i0 : N - 1;
         const int k = grid_of(g, i);
@@ -379,9 +429,9 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             // ---- layer 1 and the stabilizer: D = c . [W1 | b1 ; Ws]^T
             store_a<24>(t_row, cx);
             if (pre_mma()) break;
-            if (tid == 0 && !a.inject_stall) {  // (the failure-detection test hook withholds it)
+            if (gtid == 0 && !a.inject_stall) {  // (the failure-detection test hook withholds it)
                 tc_fence_after();
-                mma_group<B1_N, B1_K>(tmem, sbase + SM_B1, umma_idesc_tf32(kT, B1_N));
+                mma_group<B14_ROWS, B1_K>(tmem, sbase + SM_B1, umma_idesc_tf32(kT, B1_N));
                 umma_commit(mbar);
             }
             wait_mma();
@@ -397,7 +447,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             // ---- layer 2: D = h1 . W2^T
             store_a<16>(t_row, h1);
             if (pre_mma()) break;
-            if (tid == 0) {
+            if (gtid == 0) {
                 tc_fence_after();
                 mma_group<B2_N, B2_K>(tmem, sbase + SM_B2, umma_idesc_tf32(kT, B2_N));
                 umma_commit(mbar);
@@ -457,7 +507,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         // ---- dA1 = (dA2 . W2) masked by a1 > 0: D = da2 . (W2^T)^T
         store_a<16>(t_row, da2);
         if (pre_mma()) break;
-        if (tid == 0) {
+        if (gtid == 0) {
             tc_fence_after();
             mma_group<B3_N, B3_K>(tmem, sbase + SM_B3, umma_idesc_tf32(kT, B3_N));
             umma_commit(mbar);
@@ -483,9 +533,9 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             store_a<24>(t_row, ua);
         }
         if (pre_mma()) break;
-        if (tid == 0) {
+        if (gtid == 0) {
             tc_fence_after();
-            mma_group<B4_N, B4_K>(tmem, sbase + SM_B4, umma_idesc_tf32(kT, B4_N));
+            mma_group<B14_ROWS, B4_K>(tmem, sbase + SM_B4, umma_idesc_tf32(kT, B4_N));
             umma_commit(mbar);
         }
         wait_mma();
@@ -531,6 +581,12 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         // (second, 0-3), (second, 4-7).  The three hi/lo passes of every tile are issued pass by
         // pass, so that no MMA waits on the one just before it.
         {
+            float acc[kTiles][4];
+            acc_from_tmem(t_row, acc);
+            if constexpr (HY) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[kTiles - 1][q] = acc12[q];
+            }
             const int mi = lane >> 3, ri = lane & 7;
             auto afrag = [&](const float* arow, int row0) {
                 uint32_t rr[4];
@@ -549,7 +605,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 split_u(rr[3], fb.h[1], fb.l[1]);
             };
             // first fill: the gradient factors x the context (tiles 0-2, 5, 6-8)
-#pragma unroll
+#pragma unroll 1
             for (int ks = 0; ks < 4; ++ks) {
                 const int k0 = ks * 8;
                 const float* arow = st + (ri + (mi & 1) * 8) * kSld + k0 + (mi >> 1) * 4;
@@ -582,7 +638,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             for (int j = kOneCol + 1; j < kRR; ++j) st[(R_R + j) * kSld + lane] = 0.f;
             __syncwarp();
             // the gradient factors x h1, h2, r (tiles 3-4, 9-10, 11)
-#pragma unroll
+#pragma unroll 1
             for (int ks = 0; ks < 4; ++ks) {
                 const int k0 = ks * 8;
                 const float* arow = st + (ri + (mi & 1) * 8) * kSld + k0 + (mi >> 1) * 4;
@@ -603,6 +659,11 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
 #pragma unroll
                 for (int q = 0; q < NT2; ++q) mma1(acc[TT[q]], TA[q]->h, TB[q]->h[0], TB[q]->h[1]);
             }
+            acc_to_tmem(t_row, acc);
+            if constexpr (HY) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc12[q] = acc[kTiles - 1][q];
+            }
         }
         __syncwarp();
     }
@@ -611,7 +672,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
     // rate partial of this CTA (NaN when a wait ran out)
     {
         float v[1] = {rate_acc};
-        __shared__ float scratch[kT / 32];
+        __shared__ float scratch[NW];
         block_sum<1>(v, scratch);
         if (tid == 0) a.rate_part[cta] = bad ? (double)__int_as_float(0x7fc00000) : (double)v[0];
         if (tid == 0 && bad && a.status) atomicOr(a.status, 1);
@@ -620,11 +681,19 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         mbar_wait_bounded(mbar, phase ^ 1u, kWaitLimit);
         tc_fence_after();
     }
+    float acc[kTiles][4];
+    if constexpr (BWD) {
+        acc_from_tmem(t_row, acc);
+        if constexpr (HY) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[kTiles - 1][q] = acc12[q];
+        }
+    }
     tc_fence_before();
     __syncthreads();
-    if (wid == 0) tmem_dealloc(tmem, kTmemCols);
+    if (wid == 0) tmem_dealloc(s_tmem, kTmemCols);
     if constexpr (BWD) {
-        // the 4 warps' gradient tiles, added in warp order
+        // the warps' gradient tiles, added in warp order
         float* sAcc = reinterpret_cast<float*>(smem + SM_ST);  // [warp][T][lane][4]
 #pragma unroll
         for (int T = 0; T < kTiles; ++T)
@@ -632,7 +701,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             for (int q = 0; q < 4; ++q) sAcc[((wid * kTiles + T) * 32 + lane) * 4 + q] = acc[T][q];
         __syncthreads();
         float* gp = a.gpart + (int64_t)cta * (hyper ? po::arm_block_h : po::arm_block);
-        for (int e = tid; e < kTiles * 32 * 4; e += kT) {
+        for (int e = tid; e < kTiles * 32 * 4; e += NT) {
             const int T = e >> 7, l = (e >> 2) & 31, q = e & 3;
             const int row = (l >> 2) + (q >= 2 ? 8 : 0), col = 2 * (l & 3) + (q & 1);
             int idx = wgrad_index<HY>(T, row, col);
@@ -642,7 +711,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 idx = po::arm_block + (idx - po::ifce_h);
             }
             float sum = 0.f;
-            for (int wv = 0; wv < kWarps; ++wv) sum += sAcc[((wv * kTiles + T) * 32 + l) * 4 + q];
+            for (int wv = 0; wv < NW; ++wv) sum += sAcc[((wv * kTiles + T) * 32 + l) * 4 + q];
             gp[idx] = sum;
             if (idx == po::arm_b3 || idx == po::arm_b3 + 1) gp[po::arm_bs + (idx - po::arm_b3)] = sum;
         }
@@ -650,13 +719,13 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
 }
 
 template <int PASS, bool HY>
-__global__ void __launch_bounds__(kT, 3) k_arm(const __grid_constant__ ArmArgs a) {
+__global__ void __launch_bounds__(kGroups<HY> * kT, 1) k_arm(const __grid_constant__ ArmArgs a) {
     __shared__ ArmArgs sa;
     param_fetch(a, sa);
     arm_body<PASS, HY>(sa, blockIdx.x, gridDim.x);
 }
 template <int PASS, bool HY>
-__global__ void __launch_bounds__(kT, 3) k_arm_b(Batch<ArmArgs> b) {
+__global__ void __launch_bounds__(kGroups<HY> * kT, 1) k_arm_b(Batch<ArmArgs> b) {
     __shared__ ArmArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
@@ -678,10 +747,11 @@ size_t arm_smem_bytes(int pass, bool hyper) {
     return hyper ? ArmLayout<true>::total : ArmLayout<false>::total;
 }
 
-int arm_grid(int64_t N) {
-    const int64_t tiles = (N + kT - 1) / kT;
-    const int64_t cap = (int64_t)num_sms() * 3;  // 3 resident CTAs per SM
-    return (int)(tiles < cap ? (tiles < 1 ? 1 : tiles) : cap);
+int arm_grid(int64_t N, bool hyper) {
+    const int64_t groups = hyper ? kGroups<true> : kGroups<false>;
+    const int64_t ctas = ((N + kT - 1) / kT + groups - 1) / groups;
+    const int64_t cap = num_sms();  // one CTA per SM
+    return (int)(ctas < cap ? (ctas < 1 ? 1 : ctas) : cap);
 }
 
 ArmArgs arm_args(const Work& w, const float* params, float grad_scale) {
@@ -714,10 +784,10 @@ void launch_arm_t(const Work& w, const ArmArgs& a, int pass, cudaStream_t s) {
     const size_t sm = arm_smem_bytes(pass, HY);
     const int grid = w.n_cta_arm;
     switch (pass) {
-        case PASS_FWD: launch_pdl(k_arm<PASS_FWD, HY>, grid, kT, sm, s, a); break;
-        case PASS_FWD_STORE: launch_pdl(k_arm<PASS_FWD_STORE, HY>, grid, kT, sm, s, a); break;
-        case PASS_FWD_BWD: launch_pdl(k_arm<PASS_FWD_BWD, HY>, grid, kT, sm, s, a); break;
-        default: launch_pdl(k_arm<PASS_BWD_LOAD, HY>, grid, kT, sm, s, a); break;
+        case PASS_FWD: launch_pdl(k_arm<PASS_FWD, HY>, grid, kGroups<HY> * kT, sm, s, a); break;
+        case PASS_FWD_STORE: launch_pdl(k_arm<PASS_FWD_STORE, HY>, grid, kGroups<HY> * kT, sm, s, a); break;
+        case PASS_FWD_BWD: launch_pdl(k_arm<PASS_FWD_BWD, HY>, grid, kGroups<HY> * kT, sm, s, a); break;
+        default: launch_pdl(k_arm<PASS_BWD_LOAD, HY>, grid, kGroups<HY> * kT, sm, s, a); break;
     }
 }
 
@@ -734,15 +804,15 @@ template <bool HY>
 void launch_arm_b_t(const Batch<ArmArgs>& b, int pass, cudaStream_t s) {
     const size_t sm = arm_smem_bytes(pass, HY);
     switch (pass) {
-        case PASS_FWD: launch_pdl(k_arm_b<PASS_FWD, HY>, b.total_ctas, kT, sm, s, b); break;
-        case PASS_FWD_STORE: launch_pdl(k_arm_b<PASS_FWD_STORE, HY>, b.total_ctas, kT, sm, s, b); break;
-        case PASS_FWD_BWD: launch_pdl(k_arm_b<PASS_FWD_BWD, HY>, b.total_ctas, kT, sm, s, b); break;
-        default: launch_pdl(k_arm_b<PASS_BWD_LOAD, HY>, b.total_ctas, kT, sm, s, b); break;
+        case PASS_FWD: launch_pdl(k_arm_b<PASS_FWD, HY>, b.total_ctas, kGroups<HY> * kT, sm, s, b); break;
+        case PASS_FWD_STORE: launch_pdl(k_arm_b<PASS_FWD_STORE, HY>, b.total_ctas, kGroups<HY> * kT, sm, s, b); break;
+        case PASS_FWD_BWD: launch_pdl(k_arm_b<PASS_FWD_BWD, HY>, b.total_ctas, kGroups<HY> * kT, sm, s, b); break;
+        default: launch_pdl(k_arm_b<PASS_BWD_LOAD, HY>, b.total_ctas, kGroups<HY> * kT, sm, s, b); break;
     }
 }
 
-void launch_arm_b(const Batch<ArmArgs>& b, int pass, bool any_hyper, cudaStream_t s) {
-    if (any_hyper)
+void launch_arm_b(const Batch<ArmArgs>& b, int pass, bool hyper, cudaStream_t s) {
+    if (hyper)
         launch_arm_b_t<true>(b, pass, s);
     else
         launch_arm_b_t<false>(b, pass, s);

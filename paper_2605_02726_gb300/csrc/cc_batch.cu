@@ -20,7 +20,7 @@ struct cc_batch {
     int rd_capacity = 0;
     char* table = nullptr;  // device
     cc::Batch<cc::RelaxArgs> relax;
-    cc::Batch<cc::ArmArgs> arm;
+    cc::Batch<cc::ArmArgs> arm, arm_h;  // jobs without / with hyperlatent grids (two kernel forms)
     cc::Batch<cc::UpFwdArgs> upf[cc::kL];  // index m = 1..5
     cc::Batch<cc::SynArgs> synf, synb;
     cc::Batch<cc::ConvArgs> conv;
@@ -31,7 +31,6 @@ struct cc_batch {
     cc::Batch<cc::ReduceArgs> reduce;
     cc::Batch<cc::SoapArgs> soap;  // launched when some job uses CC_OPT_SOAP
     bool any_soap = false;
-    bool any_hyper = false;  // some job has hyperlatent grids: the entropy model's general form
     cc::Batch<cc::FinishArgs> finish;
     double* rd = nullptr;  // device [rd_capacity][n][3]
 };
@@ -53,7 +52,7 @@ struct TableWriter {
 template <typename A>
 Batch<A> put(TableWriter& tw, const std::vector<A>& args, const std::vector<int>& ctas, const std::vector<int>& order) {
     static_assert(sizeof(A) <= 512, "table_bytes assumes argument structs of at most 512 bytes");
-    const int n = (int)args.size();
+    const int n = (int)order.size();  // the jobs of this table, in CTA order
     const size_t oa = tw.take(sizeof(A) * n), ob = tw.take(sizeof(int) * (n + 1));
     std::vector<int> begin(n + 1, 0);
     for (int q = 0; q < n; ++q) begin[q + 1] = begin[q] + ctas[order[q]];
@@ -79,8 +78,8 @@ int scaled(int cap, float f) {
 }
 
 size_t table_bytes(int n, int rd_capacity) {
-    // upper bound: 22 kernel tables of at most 512-byte args plus CTA arrays, and the records
-    return (size_t)22 * ((size_t)512 * n + 256 + sizeof(int) * (n + 1) + 256) + (size_t)rd_capacity * n * 3 * sizeof(double) + 4096;
+    // upper bound: 23 kernel tables of at most 512-byte args plus CTA arrays, and the records
+    return (size_t)23 * ((size_t)512 * n + 256 + sizeof(int) * (n + 1) + 256) + (size_t)rd_capacity * n * 3 * sizeof(double) + 4096;
 }
 
 }  // namespace
@@ -170,8 +169,19 @@ int batch_create_impl(int32_t n, const cc_arch_t* archs, const cc_hparams_t* hps
     }
     b->relax = fill([&](int j) { return relax_args(W[j], states[j].latents, states[j].step, 0, H[j], kRelaxNoise); },
                     [&](int j) { return scaled(relax_ctas(W[j]), sc.other); });
-    b->arm = fill([&](int j) { return arm_args(W[j], states[j].params, H[j].lambda / (float)W[j].HW); },
-                  [&](int j) { return W[j].n_cta_arm; });
+    {  // the entropy model: jobs with hyperlatent grids run its other form (three thread groups per
+       // CTA instead of four), so the two sets of jobs get a table and a launch each; a job's bits
+       // are then those of its single-image launch whatever the mix
+        std::vector<ArmArgs> args(n);
+        std::vector<int> o_plain, o_hyper;
+        for (int j = 0; j < n; ++j) {
+            args[j] = arm_args(W[j], states[j].params, H[j].lambda / (float)W[j].HW);
+            ctas[j] = W[j].n_cta_arm;
+        }
+        for (int j : order) (W[j].g.nh > 0 ? o_hyper : o_plain).push_back(j);
+        b->arm = put(tw, args, ctas, o_plain);
+        b->arm_h = put(tw, args, ctas, o_hyper);
+    }
     for (int m = kL - 2; m >= 1; --m)
         b->upf[m] = fill([&](int j) { return up_fwd_args(W[j], states[j].params, m); },
                          [&](int j) { return scaled(up_fwd_ctas(W[j], m), sc.other); });
@@ -196,7 +206,6 @@ int batch_create_impl(int32_t n, const cc_arch_t* archs, const cc_hparams_t* hps
                    [&](int) { return kSoapBlocks; });
     for (int j = 0; j < n; ++j) {
         b->any_soap |= H[j].nn_opt == 1;
-        b->any_hyper |= W[j].g.nh > 0;
     }
     b->finish = fill([&](int j) {
                          // record pointer: offset of this job's first slot inside the table (fixed up below)
@@ -221,6 +230,7 @@ int batch_create_impl(int32_t n, const cc_arch_t* archs, const cc_hparams_t* hps
     }
     place(b->relax, base);
     place(b->arm, base);
+    place(b->arm_h, base);
     for (int m = 1; m <= kL - 2; ++m) place(b->upf[m], base);
     place(b->synf, base);
     place(b->conv, base);
@@ -278,7 +288,8 @@ int coolchic_batch_step(cc_batch_t* b, int32_t n_iters, void* stream) {
     if (b->rd) launch_mark_base_b(b->finish, s);
     for (int it = 0; it < n_iters; ++it) {
         if (it == 0) launch_relax_b(b->relax, s);  // later iterations: relaxed by the previous Adam update
-        launch_arm_b(b->arm, PASS_FWD_BWD, b->any_hyper, s);
+        if (b->arm.njobs > 0) launch_arm_b(b->arm, PASS_FWD_BWD, false, s);
+        if (b->arm_h.njobs > 0) launch_arm_b(b->arm_h, PASS_FWD_BWD, true, s);
         for (int m = kUpArmLo - 1; m >= 1; --m) launch_up_fwd_b(b->upf[m], s);  // the rest in the entropy-model launch
         launch_syn_fwd_b(b->synf, s);
         launch_conv_b(b->conv, s);

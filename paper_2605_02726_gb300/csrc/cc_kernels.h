@@ -425,7 +425,7 @@ void launch_init_state(const InitArgs& a, cudaStream_t s);
 
 // sizes that the workspace layout depends on
 size_t arm_smem_bytes(int pass, bool hyper);
-int arm_grid(int64_t N);
+int arm_grid(int64_t N, bool hyper);
 int conv_tiles(int H, int W);
 int up_adj_ctas(int nch, int hs, int ws);
 void arm_init_attributes();
@@ -454,7 +454,7 @@ int ifce_ctas(const Work& w);
 int gather_ctas(const Work& w);
 int reduce_ctas();
 void launch_relax_b(const Batch<RelaxArgs>& b, cudaStream_t s);
-void launch_arm_b(const Batch<ArmArgs>& b, int pass, bool any_hyper, cudaStream_t s);
+void launch_arm_b(const Batch<ArmArgs>& b, int pass, bool hyper, cudaStream_t s);  // hyper: the kernel form of jobs with hyperlatent grids
 void launch_up_fwd_b(const Batch<UpFwdArgs>& b, cudaStream_t s);
 void launch_syn_fwd_b(const Batch<SynArgs>& b, cudaStream_t s);
 void launch_conv_b(const Batch<ConvArgs>& b, cudaStream_t s);

@@ -46,7 +46,7 @@ size_t layout(const cc_arch_t* a, char* base, Work* out, double** rd) {
     w.g = make_geom(a->H, a->W);
     w.N = w.g.off[kL];
     w.HW = (int64_t)a->H * a->W;
-    w.n_cta_arm = arm_grid(w.N);
+    w.n_cta_arm = arm_grid(w.N, w.g.nh > 0);
     const int64_t tiles = conv_tiles(a->H, a->W), cap = 2 * (int64_t)num_sms();
     w.n_cta_conv = (int)(tiles < cap ? tiles : cap);
     size_t off = 0;

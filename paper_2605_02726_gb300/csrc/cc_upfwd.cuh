@@ -39,10 +39,12 @@ __device__ __forceinline__ void up_fwd_body(const UpFwdArgs& a, int cta, int nct
 }
 
 // A whole forward stage in one CTA (the coarse stages): the input channels are staged in shared
-// memory `sm` (capacity `cap` floats) when they fit, else read from global memory with coherent
-// loads (the previous stage wrote them in the same kernel); warps take output rows, lanes x.  The
-// arithmetic is the per-element expression of up_fwd_body, so the values are the same bits.  Ends
-// with a barrier: dst is then visible to the whole CTA and `sm` free.
+// memory `sm` (capacity `cap` floats) by asynchronous copies when they fit, else read from global
+// memory (the previous stage wrote them in the same CTA); warps take output rows, lanes x, and a
+// lane computes four outputs of its row at once (x, x + 32, x + 64, x + 96), so that one warp per
+// SM sub-partition still has independent chains to interleave.  The arithmetic is the
+// per-element expression of up_fwd_body, so the values are the same bits.  Ends with a barrier:
+// dst is then visible to the whole CTA and `sm` free.
 __device__ __forceinline__ void up_fwd_stage_cta(const UpFwdArgs& a, float* sm, int cap) {
     const float tp[4] = {a.taps[0], a.taps[1], a.taps[2], a.taps[3]};
     const int nin = a.hs * a.ws;
@@ -50,8 +52,9 @@ __device__ __forceinline__ void up_fwd_stage_cta(const UpFwdArgs& a, float* sm, 
     if (staged) {
         for (int j = 0; j < a.nch; ++j) {
             const float* src = j == 0 ? a.src0 : a.srcup + (int64_t)(j - 1) * nin;
-            for (int e = threadIdx.x; e < nin; e += blockDim.x) sm[j * nin + e] = src[e];
+            for (int e = threadIdx.x; e < nin; e += blockDim.x) cp_async4(sm + j * nin + e, src + e);
         }
+        cp_async_wait_all();
         __syncthreads();
     }
     const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -61,21 +64,30 @@ __device__ __forceinline__ void up_fwd_stage_cta(const UpFwdArgs& a, float* sm, 
         const int fy = poly_first(y);
         float wy[4];
         poly_w(y, tp, wy);
+        const float* r[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) r[p] = S + clampi(fy + p, 0, a.hs - 1) * a.ws;
         float* drow = a.dst + ((int64_t)j * a.ht + y) * a.wt;
-        for (int x = lane; x < a.wt; x += 32) {
-            const int fx = poly_first(x);
-            float wx[4];
-            poly_w(x, tp, wx);
-            float acc = 0.f;
+        for (int x0 = lane; x0 < a.wt; x0 += 128) {
+            float acc[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const float* r = S + clampi(fy + p, 0, a.hs - 1) * a.ws;
-                float rs = 0.f;
+            for (int u = 0; u < 4; ++u) {
+                const int x = x0 + 32 * u < a.wt ? x0 + 32 * u : x0;  // (out-of-row lanes recompute x0)
+                const int fx = poly_first(x);
+                float wx[4];
+                poly_w(x, tp, wx);
+                acc[u] = 0.f;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) rs = fmaf(wx[q], r[clampi(fx + q, 0, a.ws - 1)], rs);
-                acc = fmaf(wy[p], rs, acc);
+                for (int p = 0; p < 4; ++p) {
+                    float rs = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) rs = fmaf(wx[q], r[p][clampi(fx + q, 0, a.ws - 1)], rs);
+                    acc[u] = fmaf(wy[p], rs, acc[u]);
+                }
             }
-            drow[x] = acc;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (x0 + 32 * u < a.wt) drow[x0 + 32 * u] = acc[u];
         }
     }
     __syncthreads();

@@ -49,6 +49,27 @@ def plain(jobs, iters):
     return time.perf_counter() - t0, torch.stack(out).cpu().numpy()
 
 
+def plain_by_size(jobs, iters):
+    """Plain-path rate of each distinct image size alone (Mpixel-iterations/s): how far one image
+    of that size fills the GPU by itself, the ceiling that batching works against."""
+    rates = {}
+    for img, st, hp in jobs:
+        H, W = img.shape[1], img.shape[2]
+        key = f"{H}x{W}"
+        if key in rates:
+            continue
+        s = st.clone()
+        ws = cc.workspace(H, W)
+        rd = torch.zeros(iters, 3, dtype=torch.float64, device="cuda")
+        cc.encode_step(img, s, 5, H=H, W=W, hp=hp, ws=ws, rd=rd)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cc.encode_step(img, s, iters, H=H, W=W, hp=hp, ws=ws, rd=rd)
+        torch.cuda.synchronize()
+        rates[key] = H * W * iters / (time.perf_counter() - t0) / 1e6
+    return rates
+
+
 def batched(jobs, iters, schedule, graph_iters=10):
     be = cc.BatchEncoder(jobs, schedule=schedule, rd_capacity=graph_iters)
     g = be.graph(graph_iters)
@@ -81,12 +102,14 @@ def main():
     batch_jobs = [(img, st.clone(), hp) for img, st, hp in jobs]
     t_batch, l_batch = batched(batch_jobs, a.iters, sched)
     rel = float(np.max(np.abs(l_batch - l_plain) / np.abs(l_plain)))
+    by_size = plain_by_size(jobs, min(a.iters, 500))
     print(json.dumps({
         "workload": f"{a.images} images {sorted(set(tuple(img.shape[1:]) for img, _, _ in jobs))}, {a.iters} iterations",
         "megapixels": pix / 1e6,
         "plain_mpix_iter_per_s": pix * a.iters / t_plain / 1e6,
         "batched_mpix_iter_per_s": pix * a.iters / t_batch / 1e6,
         "speedup": t_plain / t_batch,
+        "plain_alone_mpix_iter_per_s": by_size,
         "schedule": list(sched.as_tuple()),
         "autotune_ms": {",".join(map(str, k)): v for k, v in timings.items()},
         "final_loss_max_rel_diff": rel,

@@ -8,7 +8,8 @@
 // gives dL/dc; context gradients are written as 16 planes dS[n][i] and gathered by their source
 // latent later (fixed order, no atomics).
 //
-// Work unit: a tile of 128 consecutive latents, one per thread of the CTA.  The dense products of
+// Work unit: a tile of 128 consecutive latents, one per thread of a 128-thread group (a CTA is one
+// per SM and holds four groups, three with hyperlatents).  The dense products of
 // a tile run as tcgen05 MMAs with M = 128 (the tile's latents): the activation operand A in Tensor
 // Memory (each thread stores its own row), the weights B in shared memory in the canonical
 // K-major layout, the accumulator in Tensor Memory:
@@ -18,30 +19,32 @@
 //             (N = 32, 20 used)
 // Every product is split x = hi + lo (hi = the 10 explicit mantissa bits a TF32 operand carries,
 // lo = x - hi) and accumulated as Ahi.Bhi + Alo.Bhi + Ahi.Blo, which keeps FP32-level accuracy.
-// One thread issues a tile's MMAs and commits them to an mbarrier; every thread then reads its
+// One thread of the group issues a tile's MMAs and commits them to the group's mbarrier; every
+// thread of the group then reads its
 // own row of the accumulator with tcgen05.ld and does the element-wise work (bias, ReLU, the
 // 16 -> 2 output layer, the Laplace mass and its derivatives) in FP32 on its own latent.
 //
 // Parameter gradients are sums over latents of outer products, i.e. GEMMs with K = latents:
 // each warp writes its 32 latents' factors transposed into a private [feature][latent] shared
-// tile and runs 12 m16n8 output tiles of mma.sync (TF32, hi/lo) over K = 32, accumulating in
-// registers for the whole kernel: W1 and b1, W2, b2, Ws and b3 = bs, W3, the IFCE weights.  The
-// tile holds 72 feature rows and is filled twice per work unit (the gradient factors with the
-// context, then the same gradient factors with h1, h2 and the IFCE inputs), which keeps the
-// shared memory of a CTA small enough for three CTAs per SM.
-// The 4 warps' accumulators are added in a fixed order at the end: one partial gradient per CTA.
+// tile and runs 10 m16n8 output tiles of mma.sync (TF32, hi/lo) over K = 32: W1 and b1, W2, b2, Ws
+// and b3 = bs, W3, the IFCE weights.  The accumulators stay in the group's spare Tensor Memory
+// columns between work units (loaded for the gradient phase, stored after it), so that they hold
+// no registers during the rest of the tile.  The tile holds 72 feature rows and is filled twice
+// per work unit (the gradient factors with the context, then the same gradient factors with h1,
+// h2 and the IFCE inputs), which keeps the shared memory of a CTA within its 227 KB.
+// The warps' accumulators are added in a fixed order at the end: one partial gradient per CTA.
 //
-// Every wait on the mbarrier is bounded (about a second); a CTA whose wait runs out stops, waits
-// (again bounded) for its MMAs in flight, frees its Tensor Memory and writes a NaN rate partial,
-// so that the loss of the call is NaN instead of the GPU hanging.
+// Every wait on the mbarrier is bounded (about a second); a group whose wait runs out stops, waits
+// (again bounded) for its MMAs in flight, the CTA frees its Tensor Memory and writes a NaN rate
+// partial and sets the status word, so that the loss of the call is NaN instead of the GPU hanging.
 //
 // With hyperlatent grids (Sec. III-A3, Eq. 6; the HYPER instantiation), their latents are coded
 // like the others (spatial context only), and the IFCEs of grids 0..2 take three more inputs, the
 // co-located hyperlatents; their gradients go to IFCE-input planes nin..nin+2 of the grid, their
-// weights' gradients to entries 756..791 of the CTA's partial row.
+// weights' gradients to entries 756..791 of the CTA's partial row (an 11th gradient tile).
 //
 // The first CTA also computes the coarse forward upsampling stages 6..4 (it needs none of the
-// entropy model's results, and the other CTAs take the latents), so that they cost no launch.
+// entropy model's results, and the other CTAs take the latents first), so that they cost no launch.
 #include "cc_kernels.h"
 #include "cc_mma.cuh"
 #include "cc_tc.cuh"
@@ -60,10 +63,10 @@ constexpr int kGroups = HY ? 3 : 4;  // (the hyperlatent form needs more registe
 constexpr uint32_t kTmemCols = 512;
 // Tensor Memory columns: the A operand's hi and lo copies (at most 24 columns each) at 0 and 32,
 // the accumulator of the tile's products (each in turn, at most 32 columns) at 96, and in the
-// columns left over (24..31, 56..95) the parameter-gradient tiles 0..11 of this thread, kept there
+// columns left over (24..31, 56..87) the parameter-gradient tiles 0..9 of this thread, kept there
 // between work units so that they hold no registers outside the gradient phase
 constexpr uint32_t TM_AH = 0, TM_AL = 32, TM_D = 96;
-constexpr int kTmTiles = 12;  // gradient tiles kept in Tensor Memory (a 13th stays in registers)
+constexpr int kTmTiles = 10;  // gradient tiles kept in Tensor Memory (an 11th stays in registers)
 __device__ __forceinline__ uint32_t tm_acc_col(int pair) { return pair == 0 ? 24u : 56u + 8u * (pair - 1); }
 constexpr long long kWaitLimit = 1ll << 31;                         // clock cycles (about 1 s)
 
@@ -96,7 +99,7 @@ struct ArmLayout {
     static constexpr uint32_t misc = SM_ST + warps * st_bytes;
     static constexpr int ms_n = MS_IFH + (HY ? po::ifce_h_n : 0);
     static constexpr uint32_t total = misc + ms_n * 4;
-    static constexpr int tiles = HY ? 13 : 12;
+    static constexpr int tiles = HY ? 11 : 10;
     static_assert(st_bytes % 16 == 0, "16-byte alignment of the staging tiles");
     static_assert(total + 2048 <= 227 * 1024, "shared memory of one CTA");
 };
@@ -114,6 +117,11 @@ constexpr int R_H2 = 0, R_H1 = 48, R_R = 64;
 
 // Parameter index of gradient tile T, row, column (-1: padding); with hyperlatents, an index
 // past po::total stands for entry (index - po::total + 756) of the CTA's partial row.
+//   tiles 0-2: da1 x c (rows: hidden unit, columns: context feature; c[20] = 1 gives b1)
+//   tiles 3-4: da2 x h1;  tile 5: da2 x c[16..23] (column 4, c[20] = 1: b2)
+//   tiles 6-7: c[0..15], c[16..23] x (dmu, dlogb, ...) (rows: context feature, columns: output;
+//              the transposed form, so that these two-row products take two tiles, not three)
+//   tile 8: h2 x (dmu, dlogb, ...);  tiles 9(-10): IFCE output gradients x IFCE inputs
 template <bool HY>
 __device__ int wgrad_index(int T, int row, int col) {
     if (T <= 2) {  // da1 x c
@@ -122,15 +130,15 @@ __device__ int wgrad_index(int T, int row, int col) {
     }
     if (T <= 4) return po::arm_w2 + row * 16 + (T - 3) * 8 + col;  // da2 x h1
     if (T == 5) return col == 4 ? po::arm_b2 + row : -1;            // da2 x one
-    if (T <= 8) {                                                   // (dmu, dlogb) x c
-        if (row >= 2) return -1;
-        const int f = (T - 6) * 8 + col;
-        return f < 20 ? po::arm_ws + row * 20 + f : (f == 20 ? po::arm_b3 + row : -1);
+    if (T <= 7) {                                                   // c x (dmu, dlogb)
+        if (col >= 2 || (T == 7 && row >= 8)) return -1;
+        const int f = (T - 6) * 16 + row;
+        return f < 20 ? po::arm_ws + col * 20 + f : (f == 20 ? po::arm_b3 + col : -1);
     }
-    if (T <= 10) return row < 2 ? po::arm_w3 + row * 16 + (T - 9) * 8 + col : -1;  // (dmu, dlogb) x h2
-    if (row < 2 || row >= 14) return -1;  // T == 11 (12): IFCE output gradients x IFCE inputs
+    if (T == 8) return col < 2 ? po::arm_w3 + col * 16 + row : -1;  // h2 x (dmu, dlogb)
+    if (row < 2 || row >= 14) return -1;  // T == 9 (10): IFCE output gradients x IFCE inputs
     const int k = (row - 2) >> 2, o = (row - 2) & 3, nin = ifce_nin(k);
-    const int j = (T - 11) * 8 + col;  // column of the IFCE-input block
+    const int j = (T - 9) * 8 + col;  // column of the IFCE-input block
     if (j < nin) return ifce_w_off(k) + o * nin + j;
     if (HY && j >= 6 && j < 6 + kNH) return po::ifce_h + (k * kF + o) * kNH + (j - 6);
     if (j == (HY ? 6 + kNH : 6)) return ifce_b_off(k) + o;
@@ -180,7 +188,7 @@ __device__ __forceinline__ void mma_group(uint32_t tmem, uint32_t sB, uint32_t i
     }
 }
 
-// The gradient tiles 0..11 of this thread from / to Tensor Memory (two tiles per 8 columns).
+// The gradient tiles 0..9 of this thread from / to Tensor Memory (two tiles per 8 columns).
 template <int NT>
 __device__ __forceinline__ void acc_from_tmem(uint32_t t_row, float (&acc)[NT][4]) {
     uint32_t r[kTmTiles * 4];
@@ -324,8 +332,8 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         st[46 * kSld + lane] = 0.f;
         st[47 * kSld + lane] = 0.f;
     }
-    // gradient tile 12 (hyperlatent IFCE weights) in registers, tiles 0..11 in Tensor Memory
-    float acc12[4] = {0.f, 0.f, 0.f, 0.f};
+    // gradient tile 10 (hyperlatent IFCE weights) in registers, tiles 0..9 in Tensor Memory
+    float acc_h[4] = {0.f, 0.f, 0.f, 0.f};
     if (BWD) {
         const float zero[kTmTiles][4] = {};
         acc_to_tmem(t_row, zero);
@@ -585,7 +593,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             acc_from_tmem(t_row, acc);
             if constexpr (HY) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[kTiles - 1][q] = acc12[q];
+                for (int q = 0; q < 4; ++q) acc[kTiles - 1][q] = acc_h[q];
             }
             const int mi = lane >> 3, ri = lane & 7;
             auto afrag = [&](const float* arow, int row0) {
@@ -604,7 +612,20 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 split_u(rr[2], fb.h[0], fb.l[0]);
                 split_u(rr[3], fb.h[1], fb.l[1]);
             };
-            // first fill: the gradient factors x the context (tiles 0-2, 5, 6-8)
+            // two B fragments (rows r..r+7 and r+8..r+15) as one A fragment of rows r..r+15, and
+            // the first eight rows of an A fragment as a B fragment (the register layouts coincide)
+            auto stack_b = [](const AFrag& x, const AFrag& y) {
+                AFrag f;
+                f.h[0] = x.h[0], f.h[1] = y.h[0], f.h[2] = x.h[1], f.h[3] = y.h[1];
+                f.l[0] = x.l[0], f.l[1] = y.l[0], f.l[2] = x.l[1], f.l[3] = y.l[1];
+                return f;
+            };
+            auto a_as_b = [](const AFrag& u) {
+                AFrag f = u;
+                f.h[1] = u.h[2], f.l[1] = u.l[2];
+                return f;
+            };
+            // first fill: the gradient factors x the context (tiles 0-2, 5, 6-7)
 #pragma unroll 1
             for (int ks = 0; ks < 4; ++ks) {
                 const int k0 = ks * 8;
@@ -614,15 +635,16 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 AFrag V0, V1, V2, Vx;
                 bpair(brow, R_C, R_C + 8, V0, V1);
                 bpair(brow, R_C + 16, R_C + 16, V2, Vx);
-                const AFrag* TA[7] = {&U0, &U0, &U0, &U1, &U2, &U2, &U2};
-                const AFrag* TB[7] = {&V0, &V1, &V2, &V2, &V0, &V1, &V2};
-                constexpr int TT[7] = {0, 1, 2, 5, 6, 7, 8};
+                const AFrag C01 = stack_b(V0, V1), C2 = stack_b(V2, Vx), U2b = a_as_b(U2);
+                const AFrag* TA[6] = {&U0, &U0, &U0, &U1, &C01, &C2};
+                const AFrag* TB[6] = {&V0, &V1, &V2, &V2, &U2b, &U2b};
+                constexpr int TT[6] = {0, 1, 2, 5, 6, 7};
 #pragma unroll
-                for (int q = 0; q < 7; ++q) mma1(acc[TT[q]], TA[q]->l, TB[q]->h[0], TB[q]->h[1]);
+                for (int q = 0; q < 6; ++q) mma1(acc[TT[q]], TA[q]->l, TB[q]->h[0], TB[q]->h[1]);
 #pragma unroll
-                for (int q = 0; q < 7; ++q) mma1(acc[TT[q]], TA[q]->h, TB[q]->l[0], TB[q]->l[1]);
+                for (int q = 0; q < 6; ++q) mma1(acc[TT[q]], TA[q]->h, TB[q]->l[0], TB[q]->l[1]);
 #pragma unroll
-                for (int q = 0; q < 7; ++q) mma1(acc[TT[q]], TA[q]->h, TB[q]->h[0], TB[q]->h[1]);
+                for (int q = 0; q < 6; ++q) mma1(acc[TT[q]], TA[q]->h, TB[q]->h[0], TB[q]->h[1]);
             }
             __syncwarp();
             // second fill: h2, h1 and the IFCE inputs in the rows of da1 and the context
@@ -637,7 +659,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
 #pragma unroll
             for (int j = kOneCol + 1; j < kRR; ++j) st[(R_R + j) * kSld + lane] = 0.f;
             __syncwarp();
-            // the gradient factors x h1, h2, r (tiles 3-4, 9-10, 11)
+            // the gradient factors x h1, h2, r (tiles 3-4, 8, 9(-10))
 #pragma unroll 1
             for (int ks = 0; ks < 4; ++ks) {
                 const int k0 = ks * 8;
@@ -648,10 +670,11 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
                 bpair(brow, R_H1, R_H1 + 8, H1a, H1b);
                 bpair(brow, R_H2, R_H2 + 8, H2a, H2b);
                 bpair(brow, R_R, R_R + (HY ? 8 : 0), Rr, Rr2);
-                constexpr int NT2 = HY ? 6 : 5;
-                const AFrag* TA[6] = {&U1, &U1, &U2, &U2, &U2, &U2};
-                const AFrag* TB[6] = {&H1a, &H1b, &H2a, &H2b, &Rr, &Rr2};
-                constexpr int TT[6] = {3, 4, 9, 10, 11, 12};
+                constexpr int NT2 = HY ? 5 : 4;
+                const AFrag H2 = stack_b(H2a, H2b), U2b = a_as_b(U2);
+                const AFrag* TA[5] = {&U1, &U1, &H2, &U2, &U2};
+                const AFrag* TB[5] = {&H1a, &H1b, &U2b, &Rr, &Rr2};
+                constexpr int TT[5] = {3, 4, 8, 9, 10};
 #pragma unroll
                 for (int q = 0; q < NT2; ++q) mma1(acc[TT[q]], TA[q]->l, TB[q]->h[0], TB[q]->h[1]);
 #pragma unroll
@@ -662,7 +685,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
             acc_to_tmem(t_row, acc);
             if constexpr (HY) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc12[q] = acc[kTiles - 1][q];
+                for (int q = 0; q < 4; ++q) acc_h[q] = acc[kTiles - 1][q];
             }
         }
         __syncwarp();
@@ -686,7 +709,7 @@ __device__ __forceinline__ void arm_body(const ArmArgs& a, int cta, int ncta) {
         acc_from_tmem(t_row, acc);
         if constexpr (HY) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[kTiles - 1][q] = acc12[q];
+            for (int q = 0; q < 4; ++q) acc[kTiles - 1][q] = acc_h[q];
         }
     }
     tc_fence_before();

@@ -115,7 +115,7 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
     W.n_cta_arm = arm_grid(W.N, W.g.nh > 0);
     {
         int64_t rounds = (W.HW + kSynThreads - 1) / kSynThreads;
-        W.n_cta_syn = (int)(rounds < 3 * sms ? rounds : 3 * sms);  // 3 resident CTAs per SM
+        W.n_cta_syn = (int)(rounds < 4 * sms ? rounds : 4 * sms);  // 4 resident CTAs per SM (synthesis adjoint)
         int64_t tiles = conv_tiles(a->H, a->W);
         W.n_cta_conv = (int)(tiles < 2 * sms ? tiles : 2 * sms);
     }

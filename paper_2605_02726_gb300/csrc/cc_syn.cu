@@ -105,19 +105,17 @@ __device__ __forceinline__ float dense_ch(const SynArgs& a, const Samp& s, int j
 // short and latency-bound, and a thread per pixel keeps the register count, hence the number of
 // resident warps, where the tensor-core form cannot).
 // ---------------------------------------------------------------------------------------------
-constexpr int ss_w1 = 0;    // [40][8] (7 used, 8th = bias b1)
-constexpr int ss_w2 = 320;  // [3][40]
-constexpr int ss_ws = 440;  // [3][8]  (7 used, 8th = b2 + bs)
-constexpr int ss_total = 464;
+// per hidden unit o, 12 floats: W1[o][0..6], b1[o], W2[0..2][o], 0 (three 16-byte loads)
+constexpr int ss_unit = 0;   // [40][12]
+constexpr int ss_ws = 480;   // [3][8]  (7 used, 8th = b2 + bs)
+constexpr int ss_total = 504;
 
 __device__ __forceinline__ void load_syn_weights(const float* P, float* sW) {
     for (int j = threadIdx.x; j < ss_total; j += blockDim.x) {
         float v;
-        if (j < ss_w2) {
-            const int o = j >> 3, i = j & 7;
-            v = i < 7 ? P[po::syn_w1 + o * 7 + i] : P[po::syn_b1 + o];
-        } else if (j < ss_ws) {
-            v = P[po::syn_w2 + (j - ss_w2)];
+        if (j < ss_ws) {
+            const int o = j / 12, i = j - o * 12;
+            v = i < 7 ? P[po::syn_w1 + o * 7 + i] : i == 7 ? P[po::syn_b1 + o] : i < 11 ? P[po::syn_w2 + (i - 8) * kSH + o] : 0.f;
         } else {
             const int o = (j - ss_ws) >> 3, i = (j - ss_ws) & 7;
             v = i < 7 ? P[po::syn_ws + o * 7 + i] : P[po::syn_b2 + o] + P[po::syn_bs + o];
@@ -152,8 +150,9 @@ __device__ __forceinline__ void syn_fwd_body(const SynArgs& a, int cta, int ncta
         }
 #pragma unroll 4
         for (int o = 0; o < kSH; ++o) {
-            const float4 w0 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8);
-            const float4 w1 = *reinterpret_cast<const float4*>(sW + ss_w1 + o * 8 + 4);
+            const float4 w0 = *reinterpret_cast<const float4*>(sW + ss_unit + o * 12);
+            const float4 w1 = *reinterpret_cast<const float4*>(sW + ss_unit + o * 12 + 4);
+            const float4 w2 = *reinterpret_cast<const float4*>(sW + ss_unit + o * 12 + 8);
             float acc = w1.w;
             acc = fmaf(w0.x, z[0], acc);
             acc = fmaf(w0.y, z[1], acc);
@@ -164,9 +163,9 @@ __device__ __forceinline__ void syn_fwd_body(const SynArgs& a, int cta, int ncta
             acc = fmaf(w1.z, z[6], acc);
             if (PASS == PASS_FWD_STORE) a.act[(int64_t)o * a.HW + p] = acc;
             const float h = gelu_f(acc);
-            t0 = fmaf(sW[ss_w2 + o], h, t0);
-            t1 = fmaf(sW[ss_w2 + kSH + o], h, t1);
-            t2 = fmaf(sW[ss_w2 + 2 * kSH + o], h, t2);
+            t0 = fmaf(w2.x, h, t0);
+            t1 = fmaf(w2.y, h, t1);
+            t2 = fmaf(w2.z, h, t2);
         }
         a.t[p] = t0;
         a.t[a.HW + p] = t1;
@@ -385,12 +384,12 @@ __global__ void __launch_bounds__(kSynThreads, 8) k_syn_fwd_b(Batch<SynArgs> b) 
     syn_fwd_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
 }
 template <int PASS>
-__global__ void __launch_bounds__(kSynThreads, 3) k_syn_bwd(const __grid_constant__ SynArgs a) {
+__global__ void __launch_bounds__(kSynThreads, 4) k_syn_bwd(const __grid_constant__ SynArgs a) {
     pdl_enter();
     syn_bwd_body<PASS>(a, blockIdx.x, gridDim.x);
 }
 template <int PASS>
-__global__ void __launch_bounds__(kSynThreads, 3) k_syn_bwd_b(Batch<SynArgs> b) {
+__global__ void __launch_bounds__(kSynThreads, 4) k_syn_bwd_b(Batch<SynArgs> b) {
     __shared__ SynArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);

@@ -199,10 +199,15 @@ int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const fl
 /* coolchic_encode_step for a caller whose image and result live in host memory (the call an
  * application makes end to end): the image is copied from `image_host` [host, 3*H*W FP32; pinned
  * memory makes the copy asynchronous] into the workspace, the n_iters >= 1 iterations run on
- * it, and the record (loss, rate, mse) of the last iteration is copied to `rd_last_host` [host,
- * nullable].  Both copies are ordered on `stream`: synchronise it before reading rd_last_host.
- * The workspace must hold coolchic_workspace_bytes(arch, CC_WS_HOST_IO) bytes.  The iterations
- * are those of coolchic_encode_step (Sec. IV-A..B), with its graph replay of short calls. */
+ * it, and the record (loss, rate, mse) of the last iteration lands in `rd_last_host` [host,
+ * nullable].  The image copy runs on a stream of the library's, after the work enqueued on
+ * `stream` before the call and beside the iteration's first kernels (which do not read the
+ * image), and the convolutions wait for it; `image_host` must stay unchanged until the call's
+ * work on `stream` is done.  A pinned `rd_last_host` is written by the last kernel directly,
+ * any other host buffer by a copy on `stream`; either way, synchronise `stream` before reading
+ * it.  The workspace must hold coolchic_workspace_bytes(arch, CC_WS_HOST_IO) bytes.  The
+ * iterations are those of coolchic_encode_step (Sec. IV-A..B), with its graph replay of short
+ * calls. */
 int coolchic_encode_step_host(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image_host,
                               const cc_state_t* state, int32_t n_iters, cc_rd_t* rd_last_host,
                               void* workspace, size_t workspace_bytes, void* stream);

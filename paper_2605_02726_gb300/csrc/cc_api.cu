@@ -268,7 +268,7 @@ int num_sms() {
 static void run_forward(const Work& w, const float* image, const float* latents, const float* params,
                         const int64_t* step_dev, int64_t step_host, const Hp& hp, int relax, int arm_pass,
                         int syn_pass, int conv_pass, float arm_gscale, float conv_gscale, float* xhat, cudaStream_t s,
-                        bool relaxed_already = false) {
+                        bool relaxed_already = false, cudaEvent_t image_ready = nullptr) {
     if (!relaxed_already) launch_relax(w, latents, step_dev, step_host, hp, relax, s);
     tbeg(CC_KERNEL_ARM, s);
     launch_arm(w, params, arm_pass, arm_gscale, s);
@@ -279,6 +279,9 @@ static void run_forward(const Work& w, const float* image, const float* latents,
     tbeg(CC_KERNEL_SYN_FWD, s);
     launch_syn_forward(w, params, syn_pass, s);
     tend(CC_KERNEL_SYN_FWD, s);
+    // the convolutions are the first kernels to read the image: a copy in flight on another stream
+    // (coolchic_encode_step_host) joins here
+    if (image_ready) cudaStreamWaitEvent(s, image_ready, 0);
     tbeg(CC_KERNEL_CONV, s);
     launch_conv(w, params, image, conv_pass, conv_gscale, xhat, s);
     tend(CC_KERNEL_CONV, s);
@@ -322,18 +325,36 @@ static void up_adjoint_timed(const Work& w, const float* params, cudaStream_t s)
 
 namespace {
 
+// The image of a host-buffer call, copied on a side stream while the first kernels of the call
+// (relaxation, entropy model, forward upsampling and synthesis, which do not read it) run: the
+// copy starts once the stream has reached the call (fork) and the convolutions wait for it (join).
+struct HostCopy {
+    const float* src;  // host
+    float* dst;        // device (the workspace's image area)
+    size_t bytes;
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
+
 // The launches of n_iters encoder iterations (validated arguments) on stream s.
 int encode_enqueue(const Work& w, const cc_hparams_t* hp, const float* image, const cc_state_t* st, int32_t n_iters,
-                   cc_rd_t* rd_per_iter, cudaStream_t s) {
+                   cc_rd_t* rd_per_iter, cudaStream_t s, const HostCopy* hc = nullptr) {
     int rc = CC_OK;
     const Hp h = to_hp(hp);
     const float arm_gs = hp->lambda / (float)w.HW;
     const float conv_gs = 2.f / (3.f * (float)w.HW);
+    if (hc) {
+        cudaError_t e = cudaEventRecord(hc->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hc->side, hc->fork, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hc->dst, hc->src, hc->bytes, cudaMemcpyHostToDevice, hc->side);
+        if (e == cudaSuccess) e = cudaEventRecord(hc->join, hc->side);
+        if (e != cudaSuccess) return fail(CC_ERR_CUDA, "encode_step_host: image copy: %s", cudaGetErrorString(e));
+    }
     if (rd_per_iter) launch_mark_base(w, st->step, s);
     for (int it = 0; it < n_iters; ++it) {
         // the relaxed latents of iterations after the first come from the previous Adam update
         run_forward(w, image, st->latents, st->params, st->step, 0, h, kRelaxNoise, PASS_FWD_BWD, PASS_FWD,
-                    PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s, it > 0);
+                    PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s, it > 0, it == 0 && hc ? hc->join : nullptr);
         syn_backward_timed(w, st->params, PASS_FWD_BWD, s);
         up_adjoint_timed(w, st->params, s);
         tbeg(CC_KERNEL_GATHER, s);
@@ -368,13 +389,15 @@ struct GraphEntry {
 std::mutex g_graph_mu;
 std::vector<GraphEntry> g_graphs;  // most recently used last
 std::vector<cudaStream_t> g_cap_streams;
+std::mutex g_io_mu;
+std::vector<cudaStream_t> g_io_streams;  // side streams of the eager host-buffer copies
 
 template <typename T>
 void key_put(std::string& k, const T& v) {
     k.append(reinterpret_cast<const char*>(&v), sizeof(v));
 }
 std::string encode_key(int dev, const cc_arch_t* a, const cc_hparams_t* hp, const float* image, const cc_state_t* st,
-                       int32_t n_iters, const cc_rd_t* rd, const void* ws, size_t ws_bytes) {
+                       int32_t n_iters, const cc_rd_t* rd, const void* ws, size_t ws_bytes, const float* host_src) {
     std::string k;
     for (int32_t v : {dev, a->C, a->H, a->W, a->L, a->n_ctx, a->ifce_dim, a->ifce_grids, a->arm_hidden, a->arm_layers,
                       a->syn_hidden, a->n_resconv, a->up_taps, a->stabilizer, n_iters, hp->noise_mode, hp->nn_optimizer,
@@ -387,7 +410,7 @@ std::string encode_key(int dev, const cc_arch_t* a, const cc_hparams_t* hp, cons
     key_put(k, hp->n_main);
     for (const void* p : {(const void*)image, (const void*)st->latents, (const void*)st->params, (const void*)st->m_lat,
                           (const void*)st->v_lat, (const void*)st->m_par, (const void*)st->v_par, (const void*)st->step,
-                          (const void*)st->soap, (const void*)rd, ws})
+                          (const void*)st->soap, (const void*)rd, ws, (const void*)host_src})
         key_put(k, p);
     key_put(k, ws_bytes);
     return k;
@@ -404,9 +427,17 @@ bool timing_recording() {
     return g_tm.kernel >= 0 && g_tm.used < g_tm.cap;
 }
 
+// Side stream and events of the image copy inside a captured graph (used under g_graph_mu only).
+struct CaptureCopy {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::vector<CaptureCopy> g_cap_copy;
+
 // The graph of this call (captured on first use), or nullptr if capture is not possible here.
+// host_src: the call's host image, copied inside the graph (a memcpy node beside its first kernels).
 GraphEntry* encode_graph(int dev, const std::string& key, const Work& w, const cc_hparams_t* hp, const float* image,
-                             const cc_state_t* st, int32_t n_iters, cc_rd_t* rd) {
+                             const cc_state_t* st, int32_t n_iters, cc_rd_t* rd, const float* host_src) {
     for (size_t i = 0; i < g_graphs.size(); ++i)
         if (g_graphs[i].key == key) {
             GraphEntry e = g_graphs[i];
@@ -421,11 +452,24 @@ GraphEntry* encode_graph(int dev, const std::string& key, const Work& w, const c
         return nullptr;
     }
     cudaStream_t cs = g_cap_streams[dev];
+    HostCopy hc{};
+    if (host_src) {
+        if ((int)g_cap_copy.size() <= dev) g_cap_copy.resize(dev + 1);
+        CaptureCopy& cc = g_cap_copy[dev];
+        if (!cc.side && (cudaStreamCreateWithFlags(&cc.side, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&cc.fork, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&cc.join, cudaEventDisableTiming) != cudaSuccess)) {
+            cc = CaptureCopy{};
+            cudaGetLastError();
+            return nullptr;
+        }
+        hc = HostCopy{host_src, const_cast<float*>(image), (size_t)3 * w.HW * sizeof(float), cc.side, cc.fork, cc.join};
+    }
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
-    const int rc = encode_enqueue(w, hp, image, st, n_iters, rd, cs);
+    const int rc = encode_enqueue(w, hp, image, st, n_iters, rd, cs, host_src ? &hc : nullptr);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &g);
     cudaGraphExec_t ex = nullptr;
@@ -564,9 +608,11 @@ namespace cc {
 namespace {
 // The iterations of a checked encode_step call: replayed from the library's graph of the call
 // where that applies, launched eagerly otherwise.
+// host_src (non-null): the image is in host memory and is copied to `image` (device) by the call,
+// overlapped with its first kernels.
 int encode_dispatch(const Work& w, const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
                     const cc_state_t* st, int32_t n_iters, cc_rd_t* rd_per_iter, void* ws, size_t ws_bytes,
-                    cudaStream_t s) {
+                    cudaStream_t s, const float* host_src = nullptr) {
     // inside the caller's own stream capture the launches go into the caller's graph directly
     cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) {
@@ -576,16 +622,40 @@ int encode_dispatch(const Work& w, const cc_arch_t* arch, const cc_hparams_t* hp
     if (n_iters <= kGraphMaxIters && graphs_enabled() && cst == cudaStreamCaptureStatusNone && !timing_recording()) {
         int dev = 0;
         cudaGetDevice(&dev);
-        const std::string key = encode_key(dev, arch, hp, image, st, n_iters, rd_per_iter, ws, ws_bytes);
+        const std::string key = encode_key(dev, arch, hp, image, st, n_iters, rd_per_iter, ws, ws_bytes, host_src);
         std::lock_guard<std::mutex> lk(g_graph_mu);
-        if (GraphEntry* ge = encode_graph(dev, key, w, hp, image, st, n_iters, rd_per_iter)) {
+        if (GraphEntry* ge = encode_graph(dev, key, w, hp, image, st, n_iters, rd_per_iter, host_src)) {
             cudaError_t e = cudaGraphLaunch(ge->exec, s);
             if (e == cudaSuccess) e = cudaEventRecord(ge->done, s);
             if (e != cudaSuccess) return fail(CC_ERR_CUDA, "encode_step: graph launch: %s", cudaGetErrorString(e));
             return CC_OK;
         }
     }
-    return encode_enqueue(w, hp, image, st, n_iters, rd_per_iter, s);
+    if (!host_src) return encode_enqueue(w, hp, image, st, n_iters, rd_per_iter, s);
+    // eagerly: a side stream of the device and events of this call
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaStream_t side = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_io_mu);
+        if ((int)g_io_streams.size() <= dev) g_io_streams.resize(dev + 1, nullptr);
+        if (!g_io_streams[dev] && cudaStreamCreateWithFlags(&g_io_streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+            g_io_streams[dev] = nullptr;
+            cudaGetLastError();
+        }
+        side = g_io_streams[dev];
+    }
+    HostCopy hc{host_src, const_cast<float*>(image), (size_t)3 * w.HW * sizeof(float), side, nullptr, nullptr};
+    if (!side || cudaEventCreateWithFlags(&hc.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&hc.join, cudaEventDisableTiming) != cudaSuccess) {
+        if (hc.fork) cudaEventDestroy(hc.fork);
+        cudaGetLastError();
+        return fail(CC_ERR_CUDA, "encode_step_host: no copy stream or event");
+    }
+    const int rc = encode_enqueue(w, hp, image, st, n_iters, rd_per_iter, s, &hc);
+    cudaEventDestroy(hc.fork);  // (released once their pending work is done)
+    cudaEventDestroy(hc.join);
+    return rc;
 }
 
 int check_state(const cc_state_t* st, const cc_hparams_t* hp) {
@@ -623,15 +693,26 @@ int coolchic_encode_step_host(const cc_arch_t* arch, const cc_hparams_t* hp, con
     if ((rc = check_state(st, hp))) return rc;
     if (n_iters < 1) return fail(CC_ERR_ARG, "encode_step_host: n_iters must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(w.io_image, image_host, (size_t)3 * w.HW * sizeof(float), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return fail(CC_ERR_CUDA, "encode_step_host: image copy: %s", cudaGetErrorString(e));
-    if (n_iters > 1 && (rc = encode_dispatch(w, arch, hp, w.io_image, st, n_iters - 1, nullptr, ws, ws_bytes, s)))
-        return rc;
-    if ((rc = encode_dispatch(w, arch, hp, w.io_image, st, 1, rd_last_host ? (cc_rd_t*)w.io_record : nullptr, ws,
-                              ws_bytes, s)))
-        return rc;
+    // A pinned (page-locked or registered) record buffer is written by the last kernel directly through
+    // its device-side address; any other host buffer gets the record by a copy after the call.
+    cc_rd_t* rd_direct = nullptr;
     if (rd_last_host) {
-        e = cudaMemcpyAsync(rd_last_host, w.io_record, sizeof(cc_rd_t), cudaMemcpyDeviceToHost, s);
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, rd_last_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer)
+            rd_direct = static_cast<cc_rd_t*>(at.devicePointer);
+        cudaGetLastError();
+    }
+    // the image copy rides with the first dispatched iterations (overlapped with their first kernels)
+    if (n_iters > 1 && (rc = encode_dispatch(w, arch, hp, w.io_image, st, n_iters - 1, nullptr, ws, ws_bytes, s,
+                                             image_host)))
+        return rc;
+    cc_rd_t* rd_dev = rd_direct ? rd_direct : (rd_last_host ? (cc_rd_t*)w.io_record : nullptr);
+    if ((rc = encode_dispatch(w, arch, hp, w.io_image, st, 1, rd_dev, ws, ws_bytes, s,
+                              n_iters > 1 ? nullptr : image_host)))
+        return rc;
+    if (rd_last_host && !rd_direct) {
+        const cudaError_t e = cudaMemcpyAsync(rd_last_host, w.io_record, sizeof(cc_rd_t), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return fail(CC_ERR_CUDA, "encode_step_host: record copy: %s", cudaGetErrorString(e));
     }
     return CC_OK;

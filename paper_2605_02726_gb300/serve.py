@@ -248,7 +248,7 @@ class EncodeServer:
         return {rid: j.finished - j.req.arrival for rid, j in self.done.items()}
 
 
-def benchmark(rates=(1.0, 4.0, 32.0), n_requests=64, iters=1000, budget_gb=80.0, tick_iters=50, seed0=inputs.SEED0):
+def benchmark(rates=(2.0, 8.0, 32.0), n_requests=64, iters=5000, budget_gb=80.0, tick_iters=50, seed0=inputs.SEED0):
     out = []
     for rate in rates:
         reqs = []
@@ -277,9 +277,9 @@ def benchmark(rates=(1.0, 4.0, 32.0), n_requests=64, iters=1000, budget_gb=80.0,
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("--rates", default="1,4,32")
+    ap.add_argument("--rates", default="2,8,32")
     ap.add_argument("--requests", type=int, default=64)
-    ap.add_argument("--iters", type=int, default=1000)
+    ap.add_argument("--iters", type=int, default=5000)
     ap.add_argument("--budget-gb", type=float, default=80.0)
     ap.add_argument("--tick-iters", type=int, default=50)
     a = ap.parse_args()

@@ -1,8 +1,9 @@
 """Continuous-batching encode server.
 
 Encode requests (an image, lambda, a seed, an iteration budget) arrive over time.  A request is
-admitted when its device memory (image, latents, parameters, Adam state, workspace) fits in the
-HBM budget next to the jobs already resident; admitted jobs stay resident on the device and advance
+admitted, first come first served, when a slot is free (at most `slots` jobs still have iterations
+to run; 0 = no limit) and its device memory (image, latents, parameters, Adam state, workspace) fits
+in the HBM budget next to the jobs already resident; admitted jobs stay resident on the device and advance
 together: every tick runs up to `tick_iters` encoder iterations of all active jobs through the
 batched launches (one launch per kernel for the whole set).  A job leaves when it has done its
 iterations (its final state and last loss record are copied to the host) or is cancelled; its
@@ -17,10 +18,14 @@ A membership change builds the next plan with the non-blocking coolchic_batch_cr
 plan is copied on the stream from a pinned buffer), so the GPU never waits for the host between
 ticks.  The latency of a request runs from its arrival to the host's retirement of its last tick.
 
+Slots: a few jobs of a megapixel or more already keep the GPU busy, so admitting every request that
+fits in memory only makes all of them share the GPU and finish together, late; a few slots let the
+jobs at the head of the queue finish first at about the same throughput.
+
 `python -m paper_2605_02726_gb300.serve` runs the Poisson-arrival benchmark (sizes 512x768,
 1024x1024, 2048x1365, 2048x2048 weighted .4/.3/.2/.1; lambda in {1e-4, 1e-3, 1e-2}; 80 GB budget;
-`--requests` per offered rate) and prints one JSON line per rate with p50/p99 latency, the
-offered and the served request rates and pixel-iterations per second.
+`--requests` per offered rate, `--slots`) and prints one JSON line per rate with p50/p99 latency,
+the offered and the served request rates and pixel-iterations per second.
 """
 from __future__ import annotations
 
@@ -69,8 +74,10 @@ class Job:
 
 
 class EncodeServer:
-    def __init__(self, hbm_budget: int, tick_iters: int = 50, schedule=None, device="cuda", max_inflight: int = 2):
+    def __init__(self, hbm_budget: int, tick_iters: int = 50, schedule=None, device="cuda", max_inflight: int = 2,
+                 slots: int = 0):
         self.budget = int(hbm_budget)
+        self.slots = max(0, int(slots))  # jobs with iterations left at most (0: memory alone decides)
         self.tick_iters = int(tick_iters)
         self.schedule = schedule
         self.device = torch.device(device)
@@ -133,8 +140,14 @@ class EncodeServer:
             self.active.remove(job)
             self.in_use -= job.bytes
 
+    def _running(self) -> int:
+        # jobs that still have iterations to queue (a job whose last tick is queued frees its slot)
+        return sum(1 for j in self.active if j.planned < j.req.iters and not j.cancelled)
+
     def _admit(self, now: float):
         while self.queue and self.queue[0].arrival <= now:
+            if self.slots and self._running() >= self.slots:
+                break  # FIFO: wait for a slot
             need = job_bytes(self.queue[0].H, self.queue[0].W)
             if self.in_use + need > self.budget:
                 break  # FIFO: wait for memory
@@ -248,14 +261,15 @@ class EncodeServer:
         return {rid: j.finished - j.req.arrival for rid, j in self.done.items()}
 
 
-def benchmark(rates=(2.0, 8.0, 32.0), n_requests=64, iters=5000, budget_gb=80.0, tick_iters=50, seed0=inputs.SEED0):
+def benchmark(rates=(2.0, 8.0, 32.0), n_requests=64, iters=5000, budget_gb=80.0, tick_iters=50, slots=8,
+              seed0=inputs.SEED0):
     out = []
     for rate in rates:
         reqs = []
         for q, (t, (H, W), lam) in enumerate(inputs.serve_requests(rate, n_requests, seed0)):
             img = torch.tensor(inputs.image(H, W, seed=seed0 + 1000 + q, texture_sigma=0.02))
             reqs.append((t, img, lam, seed0 + 7 * q, iters))
-        srv = EncodeServer(int(budget_gb * 2 ** 30), tick_iters=tick_iters)
+        srv = EncodeServer(int(budget_gb * 2 ** 30), tick_iters=tick_iters, slots=slots)
         t0 = time.perf_counter()
         srv.run(reqs, t0=t0)
         wall = time.perf_counter() - t0
@@ -270,7 +284,7 @@ def benchmark(rates=(2.0, 8.0, 32.0), n_requests=64, iters=5000, budget_gb=80.0,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "min_latency_s": float(lat[0]), "max_latency_s": float(lat[-1]),
             "mpix_iter_per_s": pix * iters / wall / 1e6, "wall_s": wall, "ticks": srv.ticks, "plans": srv.plans,
-            "peak_hbm_gb": srv.peak_in_use / 2 ** 30, "budget_gb": budget_gb,
+            "peak_hbm_gb": srv.peak_in_use / 2 ** 30, "budget_gb": budget_gb, "slots": slots,
         })
     return out
 
@@ -282,6 +296,8 @@ if __name__ == "__main__":
     ap.add_argument("--iters", type=int, default=5000)
     ap.add_argument("--budget-gb", type=float, default=80.0)
     ap.add_argument("--tick-iters", type=int, default=50)
+    ap.add_argument("--slots", type=int, default=8, help="jobs running at once at most (0: as many as fit in memory)")
     a = ap.parse_args()
-    for line in benchmark(tuple(float(r) for r in a.rates.split(",")), a.requests, a.iters, a.budget_gb, a.tick_iters):
+    for line in benchmark(tuple(float(r) for r in a.rates.split(",")), a.requests, a.iters, a.budget_gb, a.tick_iters,
+                          a.slots):
         print(json.dumps(line), flush=True)

@@ -59,6 +59,30 @@ def test_small_budget_admits_one_job_at_a_time(cc):
         assert a1 >= f0 - 1e-3  # one at a time
 
 
+def test_slots_bound_the_running_jobs_and_keep_arrival_order(cc):
+    from paper_2605_02726_gb300.serve import EncodeServer
+    reqs = _requests(12, [0.0] * 6, SIZES + [(24, 24), (33, 21)])
+    srv = EncodeServer(hbm_budget=8 << 30, tick_iters=4, slots=2)
+    seen = []
+    orig = srv._launch
+
+    def launch():
+        n = orig()
+        if n:
+            seen.append(len(srv.inflight[-1].jobs))  # jobs in the tick just queued
+        return n
+
+    srv._launch = launch
+    srv.run(reqs)
+    assert len(srv.done) == len(reqs) and not srv.failed
+    assert max(seen) <= 2
+    admitted = [srv.done[rid].admitted for rid in range(len(reqs))]
+    assert admitted == sorted(admitted)  # first come, first served
+    for rid in (0, 5):  # the results are still each job's own
+        lat, par = _alone(cc, reqs[rid])
+        assert torch.equal(srv.done[rid].final[0], lat) and torch.equal(srv.done[rid].final[1], par)
+
+
 def test_rejections_and_cancellation_leave_other_jobs_intact(cc):
     from paper_2605_02726_gb300.serve import EncodeServer
     reqs = _requests(12, [0.0, 0.0, 0.0, 0.0])

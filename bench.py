@@ -44,9 +44,9 @@ IFCE_NIN = (6, 5, 4)
 # the peak measured in the same run (coolchic_measure_peak), which is the roofline denominator.
 FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch of the entropy-model kernel, from the full ncu capture of
-# the current kernel at 512 x 768 (cold caches: 2.17 MB read, 0.21 MB written; the 33.5 MB of
+# the current kernel at 512 x 768 (cold caches: 2.17 MB read, 0.41 MB written; the 33.5 MB of
 # context-gradient planes it writes are still in L2 when the launch ends).
-ARM_TRAFFIC_BYTES = 2.37e6
+ARM_TRAFFIC_BYTES = 2.58e6
 # Algorithmic work of one whole encoder iteration per pixel: 1522 forward MAC per pixel (ARM 864,
 # IFCE 30, upsampling 45, synthesis 1x1 421, 3x3 convs 162), the adjoint and the parameter
 # gradients twice that again, 2 FLOP per MAC.

@@ -323,6 +323,15 @@ static void up_adjoint_timed(const Work& w, const float* params, cudaStream_t s)
     tend(CC_KERNEL_UP_ADJ, s);
 }
 
+// Whether encoder iterations drop dead synthesis scratch from L2 (COOLCHIC_DISCARD=0 turns it off).
+bool discard_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("COOLCHIC_DISCARD");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 namespace {
 
 // The image of a host-buffer call, copied on a side stream while the first kernels of the call
@@ -337,9 +346,11 @@ struct HostCopy {
 };
 
 // The launches of n_iters encoder iterations (validated arguments) on stream s.
-int encode_enqueue(const Work& w, const cc_hparams_t* hp, const float* image, const cc_state_t* st, int32_t n_iters,
+int encode_enqueue(const Work& w_in, const cc_hparams_t* hp, const float* image, const cc_state_t* st, int32_t n_iters,
                    cc_rd_t* rd_per_iter, cudaStream_t s, const HostCopy* hc = nullptr) {
     int rc = CC_OK;
+    Work w = w_in;
+    w.discard_dead = discard_enabled() ? 1 : 0;  // synthesis scratch read for the last time is dropped from L2
     const Hp h = to_hp(hp);
     const float arm_gs = hp->lambda / (float)w.HW;
     const float conv_gs = 2.f / (3.f * (float)w.HW);

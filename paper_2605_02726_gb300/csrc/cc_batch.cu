@@ -136,6 +136,7 @@ int batch_create_impl(int32_t n, const cc_arch_t* archs, const cc_hparams_t* hps
         if (ws_bytes[j] < need)
             return set_error(CC_ERR_WORKSPACE, "batch_create: job %d workspace has %zu bytes, needs %zu", j, ws_bytes[j], need);
         layout_job(&archs[j], 0, (char*)workspaces[j], &W[j]);
+        W[j].discard_dead = discard_enabled() ? 1 : 0;  // encoder iterations, as in coolchic_encode_step
         H[j] = hp_from(&h);
     }
     // largest jobs first in the CTA space

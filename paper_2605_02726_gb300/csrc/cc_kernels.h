@@ -106,6 +106,7 @@ struct Work {
     float* io_image;   // device copy of a host image [3][HW] (workspace flag bit 1, else null)
     double* io_record; // one loss record (loss, rate, mse) read back to the host (flag bit 1)
     int n_cta_arm, n_cta_syn, n_cta_conv;
+    int discard_dead;  // encoder iterations: drop the L2 lines of synthesis scratch after its last read
     int n_cta_up[kL];  // CTAs of the upsampling-adjoint kernel of stage s = 1..6
 };
 
@@ -260,6 +261,29 @@ struct ArmArgs {
 // Failure-detection test hook (coolchic_test_inject_stall): launches made while it is set withhold
 // the entropy model's first MMA commit, so that its bounded waits run out.
 int test_inject_stall();
+// Workspace ranges that are dead when a kernel starts (kernels before it have read them for the
+// last time this iteration; the next iteration writes them before reading): the kernel drops their
+// L2 lines with discard.global.L2, so they are neither written back to DRAM nor left to displace
+// data that is still live (the context-gradient planes, which the gather reads after the synthesis
+// chain).  Slots with n = 0 are unused; every range starts on a 256-byte boundary and its last line
+// lies within its own padding.  Set only for encoder iterations (coolchic_encode_step, batches);
+// COOLCHIC_DISCARD=0 turns it off.
+bool discard_enabled();
+struct DeadRanges {
+    float* p[4];
+    int64_t n[4];  // floats
+};
+__device__ __forceinline__ void discard_dead(const DeadRanges& d, int cta, int ncta) {
+    const int64_t t0 = (int64_t)cta * blockDim.x + threadIdx.x, nt = (int64_t)ncta * blockDim.x;
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+        if (d.n[r] <= 0) continue;
+        const char* b = reinterpret_cast<const char*>(d.p[r]);
+        const int64_t lines = (d.n[r] * 4 + 127) / 128;
+        for (int64_t l = t0; l < lines; l += nt) asm volatile("discard.global.L2 [%0], 128;" ::"l"(b + l * 128) : "memory");
+    }
+}
+
 struct SynArgs {
     Geom g;
     int64_t HW;
@@ -273,6 +297,7 @@ struct SynArgs {
     float* dz;        // [6][HW]
     float* zden;      // [6][HW] dense latents of grids 1..6: written by the forward, read by the adjoint
     float* gpart;     // [n_cta][467]
+    DeadRanges dead;  // the adjoint: t (read last by the convolutions)
 };
 struct ConvArgs {
     int H, W;
@@ -297,6 +322,7 @@ struct UpAdjArgs {
     const float* taps;
     int hs, ws, ht, wt, nch;
     int ty;              // tile height in input rows (2..kUpTYMax)
+    DeadRanges dead;     // stage 1: the dense latents and dt (read last by the synthesis adjoint); stage 2: dz
 };
 struct IfceArgs {
     Geom g;

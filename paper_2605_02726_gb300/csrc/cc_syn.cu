@@ -198,6 +198,7 @@ __device__ int syn_wgrad_index(int T, int row, int col, int* second) {  // relat
 
 template <int PASS>
 __device__ __forceinline__ void syn_bwd_body(const SynArgs& a, int cta, int ncta) {
+    discard_dead(a.dead, cta, ncta);
     extern __shared__ float4 smem4[];
     float4* sFr = smem4;
     float* sStage = reinterpret_cast<float*>(smem4 + FR_N * 32);
@@ -422,6 +423,11 @@ SynArgs syn_args(const Work& w, const float* params) {
     a.dz = w.dz;
     a.zden = w.zden;
     a.gpart = w.gpart_syn;
+    a.dead = DeadRanges{};
+    if (w.discard_dead) {
+        a.dead.p[0] = w.t;
+        a.dead.n[0] = 3 * w.HW;
+    }
     return a;
 }
 

@@ -113,6 +113,7 @@ __device__ __forceinline__ void up_adj_pass_a(const UpAdjArgs& a, const float* s
 }
 
 __device__ __forceinline__ void up_adj_body(const UpAdjArgs& a, int cta, int ncta) {
+    discard_dead(a.dead, cta, ncta);
     extern __shared__ float smem_up[];
     float* sD = smem_up;                                // [2ty+6][kUpDC]
     float* sT = sD + (2 * kUpTYMax + 6) * kUpDC;        // [ty][kUpDC]
@@ -258,6 +259,16 @@ UpAdjArgs up_adj_args(const Work& w, const float* params, int st) {  // stage st
     a.wt = g.w[st - 1];
     a.nch = kL - st;
     a.ty = up_adj_ty(a.nch, a.hs, a.ws);
+    a.dead = DeadRanges{};
+    if (w.discard_dead && st == 1 && w.zden) {  // read last by the synthesis adjoint
+        a.dead.p[0] = w.zden;
+        a.dead.n[0] = 6 * w.HW;
+        a.dead.p[1] = w.dt;
+        a.dead.n[1] = 3 * w.HW;
+    } else if (w.discard_dead && st == 2) {  // read last by stage 1
+        a.dead.p[0] = w.dz;
+        a.dead.n[0] = 6 * w.HW;
+    }
     return a;
 }
 

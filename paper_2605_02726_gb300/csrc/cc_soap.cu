@@ -13,7 +13,13 @@
 // Eigenvectors are the columns of Q, by decreasing eigenvalue, each with its entry of largest
 // magnitude positive.  They come from the cyclic Jacobi method in its parallel (round-robin)
 // ordering: in each of the n - 1 rounds of a sweep, n / 2 disjoint index pairs are rotated at
-// once (the symmetric Schur 2 x 2 rotation of Golub and Van Loan), columns then rows.
+// once (the symmetric Schur 2 x 2 rotation of Golub and Van Loan), columns then rows; sweeps stop
+// once the off-diagonal mass is at the level of FP32 rounding (at most kJacobiSweeps).  A refresh
+// after the first starts from the previous eigenbasis Q (Jacobi on Q^T L Q, accumulating onto Q):
+// the preconditioner moves little between refreshes, so that matrix is nearly diagonal and one or
+// two sweeps finish it, where a cold start takes six to twelve.  Either way the result is an
+// eigenbasis of the new L to FP32 accuracy; where eigenvalues coincide (the null space of a
+// rank-deficient L) the basis is not unique and depends on the start.
 //
 // One CTA per block; every matrix of a block (at most 40 x 40) lives in shared memory.  M and V
 // are the block's slots of the parameter moment arrays; L, R, Q_L, Q_R are in the caller's SOAP
@@ -23,7 +29,7 @@
 namespace cc {
 namespace {
 
-constexpr int kSoapThreads = 256;
+constexpr int kSoapThreads = 512;
 constexpr int kSoapMaxDim = 40;
 constexpr int kJacobiSweeps = 12;
 
@@ -71,18 +77,41 @@ __device__ void sm_gemm(int m, int n, int k, const float* A, bool ta, const floa
 }
 
 // Eigenvectors of the symmetric n x n matrix A (destroyed) into Q (columns, by decreasing
-// eigenvalue, canonical signs); V, cs, sn, lam, rank are scratch.  Whole CTA.
-__device__ void sm_sym_eig(int n, float* A, float* Q, float* V, float* cs, float* sn, float* lam, int* rank) {
+// eigenvalue, canonical signs).  warm: Q holds an orthogonal basis on entry and A has already been
+// rotated into it (A = Q^T L Q); the rotations then accumulate onto Q; otherwise they start from the
+// identity.  V, cs, sn, lam, rank, pq are scratch.  Whole CTA.
+__device__ void sm_sym_eig(int n, float* A, float* Q, float* V, float* cs, float* sn, float* lam, int* rank,
+                           bool warm, int* pq) {
     const int n2 = n + (n & 1);  // a padding index (no row, no column) when n is odd
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e / n == e % n) ? 1.f : 0.f;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = warm ? Q[e] : ((e / n == e % n) ? 1.f : 0.f);
     __syncthreads();
     const int np = n2 / 2;
+    // Threshold Jacobi: an off-diagonal entry at or below 1e-6 of the Frobenius norm of A (which the
+    // rotations preserve; a few times the FP32 rounding that the rotations themselves leave behind) is
+    // treated as zero, and the sweeps stop after one that rotates nothing.  The eigenvectors then
+    // carry an error of about 1e-6 |A| / gap, against the 2^-23 |A| / gap of exact convergence.
+    __shared__ float s_nrm[kSoapThreads / 32];
+    __shared__ int s_rot;
+    float skip;
+    {
+        float t = 0.f;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) t += A[e] * A[e];
+        t = warp_sum(t);
+        if ((threadIdx.x & 31) == 0) s_nrm[threadIdx.x >> 5] = t;
+        __syncthreads();
+        float tot = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_nrm[w];
+        skip = 1e-6f * sqrtf(tot);
+    }
 #pragma unroll 1
     for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+        if (threadIdx.x == 0) s_rot = 0;
+        __syncthreads();
 #pragma unroll 1
         for (int r = 0; r < n2 - 1; ++r) {
-            // round r of the circle method: index n2-1 stays, the others turn
-            auto pair_of = [&](int k, int& p, int& q) {
+            // round r of the circle method: index n2-1 stays, the others turn; the pairs go to pq
+            for (int k = threadIdx.x; k < np; k += blockDim.x) {
+                int p, q;
                 if (k == 0) {
                     p = r;
                     q = n2 - 1;
@@ -95,14 +124,13 @@ __device__ void sm_sym_eig(int n, float* A, float* Q, float* V, float* cs, float
                     p = q;
                     q = t;
                 }
-            };
-            for (int k = threadIdx.x; k < np; k += blockDim.x) {
-                int p, q;
-                pair_of(k, p, q);
+                pq[2 * k] = p;
+                pq[2 * k + 1] = q;
                 float c = 1.f, s = 0.f;
                 if (q < n) {
                     const float apq = A[p * n + q];
-                    if (apq != 0.f) {
+                    if (fabsf(apq) > skip) {
+                        s_rot = 1;
                         const float tau = (A[q * n + q] - A[p * n + p]) / (2.f * apq);
                         const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
                         c = rsqrtf(1.f + t * t);
@@ -113,34 +141,40 @@ __device__ void sm_sym_eig(int n, float* A, float* Q, float* V, float* cs, float
                 sn[k] = s;
             }
             __syncthreads();
-            // columns p, q of A and V, every row
-            for (int e = threadIdx.x; e < np * n; e += blockDim.x) {
-                const int k = e / n, row = e - k * n;
-                int p, q;
-                pair_of(k, p, q);
-                if (q >= n) continue;
-                const float c = cs[k], s = sn[k];
-                const float akp = A[row * n + p], akq = A[row * n + q];
-                A[row * n + p] = c * akp - s * akq;
-                A[row * n + q] = s * akp + c * akq;
-                const float vkp = V[row * n + p], vkq = V[row * n + q];
-                V[row * n + p] = c * vkp - s * vkq;
-                V[row * n + q] = s * vkp + c * vkq;
-            }
-            __syncthreads();
-            // rows p, q of A, every column
-            for (int e = threadIdx.x; e < np * n; e += blockDim.x) {
-                const int k = e / n, col = e - k * n;
-                int p, q;
-                pair_of(k, p, q);
-                if (q >= n) continue;
-                const float c = cs[k], s = sn[k];
-                const float apk = A[p * n + col], aqk = A[q * n + col];
-                A[p * n + col] = c * apk - s * aqk;
-                A[q * n + col] = s * apk + c * aqk;
+            // A <- J^T A J and V <- V J in one pass: thread (a, b) rotates the 2 x 2 block of A on
+            // rows {p_a, q_a} and columns {p_b, q_b} (each entry read and written once); thread
+            // (row, b) rotates columns p_b, q_b of V on that row.  (q >= n: the padding index of an
+            // odd n, no row or column.)
+            for (int e = threadIdx.x; e < np * np + n * np; e += blockDim.x) {
+                if (e < np * np) {
+                    const int ka = e / np, kb = e - ka * np;
+                    const int pa = pq[2 * ka], qa = pq[2 * ka + 1], pb = pq[2 * kb], qb = pq[2 * kb + 1];
+                    const float ca = cs[ka], sa = sn[ka], cb = cs[kb], sb = sn[kb];
+                    const bool ra = qa < n, rb = qb < n;
+                    const float x00 = A[pa * n + pb], x01 = rb ? A[pa * n + qb] : 0.f;
+                    const float x10 = ra ? A[qa * n + pb] : 0.f, x11 = ra && rb ? A[qa * n + qb] : 0.f;
+                    // columns: (x_p, x_q) <- (c x_p - s x_q, s x_p + c x_q), then the same on rows
+                    const float y00 = cb * x00 - sb * x01, y01 = sb * x00 + cb * x01;
+                    const float y10 = cb * x10 - sb * x11, y11 = sb * x10 + cb * x11;
+                    A[pa * n + pb] = ca * y00 - sa * y10;
+                    if (rb) A[pa * n + qb] = ca * y01 - sa * y11;
+                    if (ra) A[qa * n + pb] = sa * y00 + ca * y10;
+                    if (ra && rb) A[qa * n + qb] = sa * y01 + ca * y11;
+                } else {
+                    const int f = e - np * np, kb = f / n, row = f - kb * n;
+                    const int p = pq[2 * kb], q = pq[2 * kb + 1];
+                    if (q >= n) continue;
+                    const float c = cs[kb], s = sn[kb];
+                    const float vkp = V[row * n + p], vkq = V[row * n + q];
+                    V[row * n + p] = c * vkp - s * vkq;
+                    V[row * n + q] = s * vkp + c * vkq;
+                }
             }
             __syncthreads();
         }
+        const bool done = s_rot == 0;
+        __syncthreads();  // (every thread has read the flag before it is reset)
+        if (done) break;
     }
     // order by decreasing eigenvalue (ties by index), canonical sign
     for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = A[i * n + i];
@@ -170,7 +204,7 @@ __device__ __forceinline__ void soap_body(const SoapArgs& a, int b) {
     __shared__ float G[kMN], Wt[kMN], M[kMN], V[kMN], T[kMN], Gr[kMN], Mr[kMN];
     __shared__ float L[kSq], R[kSq], QL[kSq], QR[kSq], GG[kSq], S1[kSq];
     __shared__ float cs[kSoapMaxDim], sn[kSoapMaxDim], lam[kSoapMaxDim];
-    __shared__ int rank[kSoapMaxDim];
+    __shared__ int rank[kSoapMaxDim], pq[kSoapMaxDim + 2];
     __shared__ int64_t s_step;
     if (threadIdx.x == 0) s_step = *a.step_dev;
     float* st = a.soap + B.state;
@@ -230,12 +264,24 @@ __device__ __forceinline__ void soap_body(const SoapArgs& a, int b) {
         refresh = a.hp.sfreq > 0 && s % a.hp.sfreq == 0;
     }
     if (refresh) {
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) S1[e] = L[e];
-        __syncthreads();
-        sm_sym_eig(m, S1, QL, GG, cs, sn, lam, rank);
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) S1[e] = R[e];
-        __syncthreads();
-        sm_sym_eig(n, S1, QR, GG, cs, sn, lam, rank);
+        // warm start (s > 0): rotate the new preconditioner into the previous eigenbasis first
+        const bool warm = s > 0;
+        if (warm) {
+            sm_gemm(m, m, m, QL, true, L, false, GG);
+            sm_gemm(m, m, m, GG, false, QL, false, S1);
+        } else {
+            for (int e = threadIdx.x; e < m * m; e += blockDim.x) S1[e] = L[e];
+            __syncthreads();
+        }
+        sm_sym_eig(m, S1, QL, GG, cs, sn, lam, rank, warm, pq);
+        if (warm) {
+            sm_gemm(n, n, n, QR, true, R, false, GG);
+            sm_gemm(n, n, n, GG, false, QR, false, S1);
+        } else {
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) S1[e] = R[e];
+            __syncthreads();
+        }
+        sm_sym_eig(n, S1, QR, GG, cs, sn, lam, rank, warm, pq);
     }
     for (int e = threadIdx.x; e < mn; e += blockDim.x) {
         a.params[B.off + e] = Wt[e];

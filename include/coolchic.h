@@ -202,7 +202,7 @@ int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const fl
  * it, and the record (loss, rate, mse) of the last iteration lands in `rd_last_host` [host,
  * nullable].  The image copy runs on a stream of the library's, after the work enqueued on
  * `stream` before the call and beside the iteration's first kernels (which do not read the
- * image), and the convolutions wait for it; `image_host` must stay unchanged until the call's
+ * image), and the synthesis forward waits for it; `image_host` must stay unchanged until the call's
  * work on `stream` is done.  A pinned `rd_last_host` is written by the last kernel directly,
  * any other host buffer by a copy on `stream`; either way, synchronise `stream` before reading
  * it.  The workspace must hold coolchic_workspace_bytes(arch, CC_WS_HOST_IO) bytes.  The

@@ -276,12 +276,14 @@ static void run_forward(const Work& w, const float* image, const float* latents,
     tbeg(CC_KERNEL_UP_FWD, s);
     launch_up_forward(w, params, kUpArmLo - 1, s);
     tend(CC_KERNEL_UP_FWD, s);
+    // A copy of the image in flight on another stream (coolchic_encode_step_host) joins here, before
+    // the synthesis forward: the convolutions after it are the first kernels to read the image, but a
+    // wait right before them would also cut their dependent-launch overlap with the synthesis forward
+    // (9 us per iteration at 512 x 768), and the copy (about 30 us) is done long before either.
+    if (image_ready) cudaStreamWaitEvent(s, image_ready, 0);
     tbeg(CC_KERNEL_SYN_FWD, s);
     launch_syn_forward(w, params, syn_pass, s);
     tend(CC_KERNEL_SYN_FWD, s);
-    // the convolutions are the first kernels to read the image: a copy in flight on another stream
-    // (coolchic_encode_step_host) joins here
-    if (image_ready) cudaStreamWaitEvent(s, image_ready, 0);
     tbeg(CC_KERNEL_CONV, s);
     launch_conv(w, params, image, conv_pass, conv_gscale, xhat, s);
     tend(CC_KERNEL_CONV, s);
@@ -335,8 +337,8 @@ bool discard_enabled() {
 namespace {
 
 // The image of a host-buffer call, copied on a side stream while the first kernels of the call
-// (relaxation, entropy model, forward upsampling and synthesis, which do not read it) run: the
-// copy starts once the stream has reached the call (fork) and the convolutions wait for it (join).
+// (relaxation, entropy model, forward upsampling, which do not read it) run: the copy starts once
+// the stream has reached the call (fork) and the synthesis forward waits for it (join).
 struct HostCopy {
     const float* src;  // host
     float* dst;        // device (the workspace's image area)

@@ -191,7 +191,11 @@ int64_t coolchic_kernel_launches(const cc_arch_t* arch, int32_t n_iters);
  * captured into a CUDA graph of the library's own on its first occurrence with given arguments
  * (all values and pointers), which later identical calls replay (at most 16 kept; not while
  * kernel timing records or the caller's stream is capturing; environment COOLCHIC_GRAPHS=0 turns
- * this off); longer calls launch eagerly.  n_iters = 0 launches nothing. */
+ * this off); longer calls launch eagerly.  Workspace buffers that an iteration has read for the
+ * last time (the synthesis output before the convolutions, the kept dense latents and their
+ * gradients) are dropped from L2 without being written back (discard.global.L2; environment
+ * COOLCHIC_DISCARD=0 turns this off), so the workspace holds nothing readable between calls.
+ * n_iters = 0 launches nothing. */
 int coolchic_encode_step(const cc_arch_t* arch, const cc_hparams_t* hp, const float* image,
                          const cc_state_t* state, int32_t n_iters, cc_rd_t* rd_per_iter,
                          void* workspace, size_t workspace_bytes, void* stream);

@@ -274,7 +274,12 @@ static void run_forward(const Work& w, const float* image, const float* latents,
     launch_arm(w, params, arm_pass, arm_gscale, s);
     tend(CC_KERNEL_ARM, s);
     tbeg(CC_KERNEL_UP_FWD, s);
-    launch_up_forward(w, params, kUpArmLo - 1, s);
+    if (w.ifce_early) {  // encoder iterations: the IFCE cell sums ride with the first stage
+        launch_up_fwd_ifce(w, params, kUpArmLo - 1, s);
+        if (kUpArmLo - 2 >= 1) launch_up_forward(w, params, kUpArmLo - 2, s);
+    } else {
+        launch_up_forward(w, params, kUpArmLo - 1, s);
+    }
     tend(CC_KERNEL_UP_FWD, s);
     // A copy of the image in flight on another stream (coolchic_encode_step_host) joins here, before
     // the synthesis forward: the convolutions after it are the first kernels to read the image, but a
@@ -353,6 +358,7 @@ int encode_enqueue(const Work& w_in, const cc_hparams_t* hp, const float* image,
     int rc = CC_OK;
     Work w = w_in;
     w.discard_dead = discard_enabled() ? 1 : 0;  // synthesis scratch read for the last time is dropped from L2
+    w.ifce_early = 1;                            // the IFCE cell sums in the first forward upsampling launch
     const Hp h = to_hp(hp);
     const float arm_gs = hp->lambda / (float)w.HW;
     const float conv_gs = 2.f / (3.f * (float)w.HW);
@@ -596,9 +602,9 @@ int64_t coolchic_kernel_launches(const cc_arch_t* a, int32_t n_iters) {
     if (n_iters < 0) return fail(CC_ERR_ARG, "n_iters must be >= 0"), -1;
     if (n_iters == 0) return 0;
     // per iteration: entropy model (with the coarse forward upsampling stages), synthesis forward,
-    // convs, synthesis adjoint, IFCE, gather, reduce, finish, forward upsampling stages 2..kUpArmLo
-    // and adjoint stages 1..6; relax once per call
-    const int64_t per_iter = 8 + (kUpArmLo - 1) + (kL - 1);
+    // convs, synthesis adjoint, gather, reduce, finish, forward upsampling stages 2..kUpArmLo (the
+    // first of them with the IFCE cell sums) and adjoint stages 1..6; relax once per call
+    const int64_t per_iter = 7 + (kUpArmLo - 1) + (kL - 1);
     return 1 + per_iter * n_iters;
 }
 

@@ -107,6 +107,7 @@ struct Work {
     double* io_record; // one loss record (loss, rate, mse) read back to the host (flag bit 1)
     int n_cta_arm, n_cta_syn, n_cta_conv;
     int discard_dead;  // encoder iterations: drop the L2 lines of synthesis scratch after its last read
+    int ifce_early;    // encoder iterations: the IFCE cell sums run in the first forward upsampling launch
     int n_cta_up[kL];  // CTAs of the upsampling-adjoint kernel of stage s = 1..6
 };
 
@@ -477,6 +478,9 @@ int relax_ctas(const Work& w);
 int up_fwd_ctas(const Work& w, int m);
 int syn_fwd_ctas(const Work& w);
 int ifce_ctas(const Work& w);
+// the first forward upsampling stage after the entropy model (output up[m]) and the IFCE cell sums
+// in one launch (encoder iterations)
+void launch_up_fwd_ifce(const Work& w, const float* params, int m, cudaStream_t s);
 int gather_ctas(const Work& w);
 int reduce_ctas();
 void launch_relax_b(const Batch<RelaxArgs>& b, cudaStream_t s);

@@ -3,6 +3,7 @@
 // Each kernel has a body over (arguments, CTA index within the job, CTA count of the job), a
 // single-job entry and a multi-job entry.
 #include "cc_kernels.h"
+#include "cc_upfwd.cuh"
 
 namespace cc {
 namespace {
@@ -106,6 +107,19 @@ __global__ void k_ifce_cells_b(Batch<IfceArgs> b) {
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
     ifce_body(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
+}
+// Encoder iterations: the first forward upsampling stage after the entropy model and the IFCE cell
+// sums in one launch.  CTAs [0, n_up) run the stage, the others the cell sums, which read only the
+// entropy model's IFCE-input gradients and are read only by the gather; the iteration's chain of
+// dependent launches is one launch shorter.  Both bodies are light (few registers, no shared
+// memory), so sharing one launch configuration costs neither of them occupancy.
+__global__ void __launch_bounds__(kUpThreads) k_up_fwd_ifce(const __grid_constant__ UpFwdArgs u,
+                                                            const __grid_constant__ IfceArgs f, int n_up) {
+    pdl_enter();
+    if ((int)blockIdx.x < n_up)
+        up_fwd_body(u, blockIdx.x, n_up);
+    else
+        ifce_body(f, blockIdx.x - n_up, gridDim.x - n_up);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -552,10 +566,16 @@ void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_
     launch_pdl(k_relax, relax_ctas(w), 256, 0, s, relax_args(w, y, step_dev, step_host, hp, relax));
 }
 
+void launch_up_fwd_ifce(const Work& w, const float* params, int m, cudaStream_t s) {
+    const int n_up = up_fwd_ctas(w, m);
+    const int n_if = grid_for(8 * (4 + w.g.nh) * (int64_t)w.g.h[kNIfce] * w.g.w[kNIfce], kUpThreads, 8);
+    launch_pdl(k_up_fwd_ifce, n_up + n_if, kUpThreads, 0, s, up_fwd_args(w, params, m), ifce_args(w), n_up);
+}
+
 void launch_gather(const Work& w, const float* params, int relax, float* grad_out, float* y, float* m, float* v,
                    const Hp& hp, const int64_t* step_dev, int64_t step_host, cudaStream_t s, bool relax_next) {
     (void)params;
-    launch_pdl(k_ifce_cells, ifce_ctas(w), 128, 0, s, ifce_args(w));
+    if (!w.ifce_early) launch_pdl(k_ifce_cells, ifce_ctas(w), 128, 0, s, ifce_args(w));
     launch_pdl(k_gather, gather_ctas(w), 256, 0, s,
                gather_args(w, relax, grad_out, y, m, v, hp, step_dev, step_host, relax_next));
 }

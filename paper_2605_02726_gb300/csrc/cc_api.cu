@@ -376,11 +376,12 @@ int encode_enqueue(const Work& w_in, const cc_hparams_t* hp, const float* image,
                     PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s, it > 0, it == 0 && hc ? hc->join : nullptr);
         syn_backward_timed(w, st->params, PASS_FWD_BWD, s);
         up_adjoint_timed(w, st->params, s);
+        // the parameter reduction beside the gather, one launch (the IFCE cell sums ran with the
+        // forward upsampling)
         tbeg(CC_KERNEL_GATHER, s);
-        launch_gather(w, st->params, kRelaxNoise, nullptr, st->latents, st->m_lat, st->v_lat, h, st->step, 0, s,
-                      it + 1 < n_iters);
+        launch_gather_reduce(w, st->latents, st->m_lat, st->v_lat, st->params, st->m_par, st->v_par, h, st->step, s,
+                             it + 1 < n_iters);
         tend(CC_KERNEL_GATHER, s);
-        launch_param_reduce(w, st->params, st->m_par, st->v_par, nullptr, 1.f, h, st->step, s);
         if (h.nn_opt == CC_OPT_SOAP) launch_soap(w, st->params, st->m_par, st->v_par, st->soap, h, st->step, s);
         launch_finish(w, h, 1, 1, (double*)rd_per_iter, st->step, 0, 1, s);
         if ((rc = launched("encode_step"))) return rc;
@@ -602,9 +603,10 @@ int64_t coolchic_kernel_launches(const cc_arch_t* a, int32_t n_iters) {
     if (n_iters < 0) return fail(CC_ERR_ARG, "n_iters must be >= 0"), -1;
     if (n_iters == 0) return 0;
     // per iteration: entropy model (with the coarse forward upsampling stages), synthesis forward,
-    // convs, synthesis adjoint, gather, reduce, finish, forward upsampling stages 2..kUpArmLo (the
-    // first of them with the IFCE cell sums) and adjoint stages 1..6; relax once per call
-    const int64_t per_iter = 7 + (kUpArmLo - 1) + (kL - 1);
+    // convs, synthesis adjoint, gather with the parameter reduction, finish, forward upsampling stages
+    // 2..kUpArmLo (the first of them with the IFCE cell sums) and adjoint stages 1..6; relax once per
+    // call (with SOAP, one more launch per iteration)
+    const int64_t per_iter = 6 + (kUpArmLo - 1) + (kL - 1);
     return 1 + per_iter * n_iters;
 }
 

@@ -478,6 +478,9 @@ int relax_ctas(const Work& w);
 int up_fwd_ctas(const Work& w, int m);
 int syn_fwd_ctas(const Work& w);
 int ifce_ctas(const Work& w);
+// encoder iterations: the parameter reduction and the latent gather (with Adam) in one launch
+void launch_gather_reduce(const Work& w, float* y, float* m_lat, float* v_lat, float* params, float* m_par,
+                          float* v_par, const Hp& hp, const int64_t* step_dev, cudaStream_t s, bool relax_next);
 // the first forward upsampling stage after the entropy model (output up[m]) and the IFCE cell sums
 // in one launch (encoder iterations)
 void launch_up_fwd_ifce(const Work& w, const float* params, int m, cudaStream_t s);

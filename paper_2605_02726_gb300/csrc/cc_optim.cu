@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_b(Batch<GatherArgs> b) {
 // kReduceCtas CTAs.
 // ---------------------------------------------------------------------------------------------
 constexpr int kReduceCtas = (po::total_h + 31) / 32;  // CTAs past the job's parameters return
-constexpr int kReduceThreads = 1024, kReduceWarps = kReduceThreads / 32;
+constexpr int kReduceThreads = 256, kReduceWarps = kReduceThreads / 32;  // (the gather's CTA size: see k_gather_reduce)
 
 __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int cta) {
     __shared__ float red[kReduceWarps][33];
@@ -361,6 +361,24 @@ __global__ void __launch_bounds__(kReduceThreads) k_param_reduce_b(Batch<ReduceA
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
     reduce_body(sa, blockIdx.x - b.cta_begin[j]);
+}
+
+// Encoder iterations: the parameter reduction (the first kReduceCtas CTAs) and the latent gather (the
+// others) in one launch.  The reduction reads only the per-CTA partial gradients, all written before
+// the gather, and neither part reads what the other writes, so the reduction runs beside the gather
+// instead of after it: one launch fewer on the iteration's dependent chain.  The reduction CTAs come
+// first so that the launch stays one wave at the gather's four CTAs per SM.
+__global__ void __launch_bounds__(256, 4) k_gather_reduce(const __grid_constant__ GatherArgs g,
+                                                          const __grid_constant__ ReduceArgs r) {
+    if ((int)blockIdx.x < kReduceCtas) {
+        __shared__ ReduceArgs sr;
+        param_fetch(r, sr);
+        reduce_body(sr, blockIdx.x);
+    } else {
+        __shared__ GatherArgs sg;
+        param_fetch(g, sg);
+        gather_body(sg, blockIdx.x - kReduceCtas, gridDim.x - kReduceCtas);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -578,6 +596,15 @@ void launch_gather(const Work& w, const float* params, int relax, float* grad_ou
     if (!w.ifce_early) launch_pdl(k_ifce_cells, ifce_ctas(w), 128, 0, s, ifce_args(w));
     launch_pdl(k_gather, gather_ctas(w), 256, 0, s,
                gather_args(w, relax, grad_out, y, m, v, hp, step_dev, step_host, relax_next));
+}
+
+void launch_gather_reduce(const Work& w, float* y, float* m_lat, float* v_lat, float* params, float* m_par,
+                          float* v_par, const Hp& hp, const int64_t* step_dev, cudaStream_t s, bool relax_next) {
+    static_assert(kReduceThreads == 256, "the reduction shares the gather's CTA size");
+    const int ng = gather_ctas(w) > kReduceCtas + 1 ? gather_ctas(w) - kReduceCtas : 1;
+    launch_pdl(k_gather_reduce, kReduceCtas + ng, 256, 0, s,
+               gather_args(w, kRelaxNoise, nullptr, y, m_lat, v_lat, hp, step_dev, 0, relax_next),
+               reduce_args(w, params, m_par, v_par, nullptr, 1.f, hp, step_dev));
 }
 
 void launch_param_reduce(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,

@@ -181,6 +181,7 @@ size_t build_work(const cc_arch_t* a, int flags, char* base, Work* w) {
         W.se_part = (double*)(base + o_sp);
         W.grad_params = (float*)(base + o_gp);
         W.base_step = (int64_t*)(base + o_bs);
+        W.step_snap = (int64_t*)(base + o_bs + sizeof(int64_t));
         W.status = (int*)(base + o_bs + 2 * sizeof(int64_t));
         if (flags & 1) {
             W.act_arm = (float*)(base + o_aa);
@@ -275,7 +276,7 @@ static void run_forward(const Work& w, const float* image, const float* latents,
     tend(CC_KERNEL_ARM, s);
     tbeg(CC_KERNEL_UP_FWD, s);
     if (w.ifce_early) {  // encoder iterations: the IFCE cell sums ride with the first stage
-        launch_up_fwd_ifce(w, params, kUpArmLo - 1, s);
+        launch_up_fwd_ifce(w, params, kUpArmLo - 1, step_dev, s);
         if (kUpArmLo - 2 >= 1) launch_up_forward(w, params, kUpArmLo - 2, s);
     } else {
         launch_up_forward(w, params, kUpArmLo - 1, s);
@@ -376,14 +377,14 @@ int encode_enqueue(const Work& w_in, const cc_hparams_t* hp, const float* image,
                     PASS_FWD_BWD, arm_gs, conv_gs, nullptr, s, it > 0, it == 0 && hc ? hc->join : nullptr);
         syn_backward_timed(w, st->params, PASS_FWD_BWD, s);
         up_adjoint_timed(w, st->params, s);
-        // the parameter reduction beside the gather, one launch (the IFCE cell sums ran with the
-        // forward upsampling)
+        // the parameter reduction, the loss record with the step increment and the gather in one
+        // launch (the IFCE cell sums ran with the forward upsampling); it and SOAP read the step
+        // from the snapshot that the forward upsampling took
         tbeg(CC_KERNEL_GATHER, s);
-        launch_gather_reduce(w, st->latents, st->m_lat, st->v_lat, st->params, st->m_par, st->v_par, h, st->step, s,
-                             it + 1 < n_iters);
+        launch_gather_reduce(w, st->latents, st->m_lat, st->v_lat, st->params, st->m_par, st->v_par, h, st->step,
+                             (double*)rd_per_iter, s, it + 1 < n_iters);
         tend(CC_KERNEL_GATHER, s);
-        if (h.nn_opt == CC_OPT_SOAP) launch_soap(w, st->params, st->m_par, st->v_par, st->soap, h, st->step, s);
-        launch_finish(w, h, 1, 1, (double*)rd_per_iter, st->step, 0, 1, s);
+        if (h.nn_opt == CC_OPT_SOAP) launch_soap(w, st->params, st->m_par, st->v_par, st->soap, h, w.step_snap, s);
         if ((rc = launched("encode_step"))) return rc;
     }
     return CC_OK;
@@ -603,10 +604,10 @@ int64_t coolchic_kernel_launches(const cc_arch_t* a, int32_t n_iters) {
     if (n_iters < 0) return fail(CC_ERR_ARG, "n_iters must be >= 0"), -1;
     if (n_iters == 0) return 0;
     // per iteration: entropy model (with the coarse forward upsampling stages), synthesis forward,
-    // convs, synthesis adjoint, gather with the parameter reduction, finish, forward upsampling stages
-    // 2..kUpArmLo (the first of them with the IFCE cell sums) and adjoint stages 1..6; relax once per
-    // call (with SOAP, one more launch per iteration)
-    const int64_t per_iter = 6 + (kUpArmLo - 1) + (kL - 1);
+    // convs, synthesis adjoint, gather with the parameter reduction and the finish, forward
+    // upsampling stages 2..kUpArmLo (the first of them with the IFCE cell sums) and adjoint stages
+    // 1..6; relax once per call (with SOAP, one more launch per iteration)
+    const int64_t per_iter = 5 + (kUpArmLo - 1) + (kL - 1);
     return 1 + per_iter * n_iters;
 }
 

@@ -102,6 +102,7 @@ struct Work {
     double* se_part;   // [n_cta_conv]
     float* grad_params;// [1415] reduced parameter gradient
     int64_t* base_step;// step at the start of an encode call
+    int64_t* step_snap;// encoder iterations: the step as the iteration's forward launches saw it
     int* status;       // bit 0: a bounded wait in the entropy model ran out (cleared by blocking calls)
     float* io_image;   // device copy of a host image [3][HW] (workspace flag bit 1, else null)
     double* io_record; // one loss record (loss, rate, mse) read back to the host (flag bit 1)
@@ -478,12 +479,16 @@ int relax_ctas(const Work& w);
 int up_fwd_ctas(const Work& w, int m);
 int syn_fwd_ctas(const Work& w);
 int ifce_ctas(const Work& w);
-// encoder iterations: the parameter reduction and the latent gather (with Adam) in one launch
+// encoder iterations: the parameter reduction, the loss record with the step increment (the finish,
+// reading w.rate_part and w.se_part; rd_out as in launch_finish) and the latent gather (with Adam)
+// in one launch.  The reduction and the gather read the step from w.step_snap, which the
+// iteration's launch_up_fwd_ifce wrote, so that the finish may increment *step_dev beside them.
 void launch_gather_reduce(const Work& w, float* y, float* m_lat, float* v_lat, float* params, float* m_par,
-                          float* v_par, const Hp& hp, const int64_t* step_dev, cudaStream_t s, bool relax_next);
+                          float* v_par, const Hp& hp, int64_t* step_dev, double* rd_out, cudaStream_t s,
+                          bool relax_next);
 // the first forward upsampling stage after the entropy model (output up[m]) and the IFCE cell sums
-// in one launch (encoder iterations)
-void launch_up_fwd_ifce(const Work& w, const float* params, int m, cudaStream_t s);
+// in one launch (encoder iterations); its first thread also copies *step_dev to w.step_snap
+void launch_up_fwd_ifce(const Work& w, const float* params, int m, const int64_t* step_dev, cudaStream_t s);
 int gather_ctas(const Work& w);
 int reduce_ctas();
 void launch_relax_b(const Batch<RelaxArgs>& b, cudaStream_t s);

@@ -113,9 +113,13 @@ __global__ void k_ifce_cells_b(Batch<IfceArgs> b) {
 // entropy model's IFCE-input gradients and are read only by the gather; the iteration's chain of
 // dependent launches is one launch shorter.  Both bodies are light (few registers, no shared
 // memory), so sharing one launch configuration costs neither of them occupancy.
+// The launch's first thread also copies the step to the iteration's snapshot (every earlier
+// launch of the iteration has completed: the step is the one this iteration updates with).
 __global__ void __launch_bounds__(kUpThreads) k_up_fwd_ifce(const __grid_constant__ UpFwdArgs u,
-                                                            const __grid_constant__ IfceArgs f, int n_up) {
+                                                            const __grid_constant__ IfceArgs f, int n_up,
+                                                            const int64_t* step_dev, int64_t* step_snap) {
     pdl_enter();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *step_snap = *step_dev;
     if ((int)blockIdx.x < n_up)
         up_fwd_body(u, blockIdx.x, n_up);
     else
@@ -363,24 +367,6 @@ __global__ void __launch_bounds__(kReduceThreads) k_param_reduce_b(Batch<ReduceA
     reduce_body(sa, blockIdx.x - b.cta_begin[j]);
 }
 
-// Encoder iterations: the parameter reduction (the first kReduceCtas CTAs) and the latent gather (the
-// others) in one launch.  The reduction reads only the per-CTA partial gradients, all written before
-// the gather, and neither part reads what the other writes, so the reduction runs beside the gather
-// instead of after it: one launch fewer on the iteration's dependent chain.  The reduction CTAs come
-// first so that the launch stays one wave at the gather's four CTAs per SM.
-__global__ void __launch_bounds__(256, 4) k_gather_reduce(const __grid_constant__ GatherArgs g,
-                                                          const __grid_constant__ ReduceArgs r) {
-    if ((int)blockIdx.x < kReduceCtas) {
-        __shared__ ReduceArgs sr;
-        param_fetch(r, sr);
-        reduce_body(sr, blockIdx.x);
-    } else {
-        __shared__ GatherArgs sg;
-        param_fetch(g, sg);
-        gather_body(sg, blockIdx.x - kReduceCtas, gridDim.x - kReduceCtas);
-    }
-}
-
 // ---------------------------------------------------------------------------------------------
 // Loss record in FP64 from the rate and squared-error partials; optional history slot
 // rd[(step - base) * rd_stride]; optional step increment.  One CTA of 256 threads per job.
@@ -428,6 +414,31 @@ __global__ void k_finish_b(Batch<FinishArgs> b) {
     __shared__ FinishArgs sa;
     batch_fetch(b.args, blockIdx.x, sa);
     finish_body(sa);
+}
+
+// Encoder iterations: the parameter reduction (the first kReduceCtas CTAs), the loss record with the
+// step increment (the next CTA) and the latent gather (the others) in one launch.  The reduction
+// reads only the per-CTA partial gradients and the record only the rate and squared-error partials,
+// all written before the gather, and no part reads what another writes: the reduction and the
+// gather read the step from the iteration's snapshot, not from the word the finish increments.  So
+// they run beside the gather instead of after it: two launches fewer on the iteration's dependent
+// chain.  The reduction CTAs and the finish come first so that the launch stays one wave at the
+// gather's four CTAs per SM.
+__global__ void __launch_bounds__(256, 4) k_gather_reduce(const __grid_constant__ GatherArgs g,
+                                                          const __grid_constant__ ReduceArgs r,
+                                                          const __grid_constant__ FinishArgs f) {
+    if ((int)blockIdx.x < kReduceCtas) {
+        __shared__ ReduceArgs sr;
+        param_fetch(r, sr);
+        reduce_body(sr, blockIdx.x);
+    } else if ((int)blockIdx.x == kReduceCtas) {
+        pdl_enter();
+        finish_body(f);
+    } else {
+        __shared__ GatherArgs sg;
+        param_fetch(g, sg);
+        gather_body(sg, blockIdx.x - (kReduceCtas + 1), gridDim.x - (kReduceCtas + 1));
+    }
 }
 
 __global__ void k_mark_base(const int64_t* step_dev, int64_t* base_step) { *base_step = *step_dev; }
@@ -584,10 +595,11 @@ void launch_relax(const Work& w, const float* y, const int64_t* step_dev, int64_
     launch_pdl(k_relax, relax_ctas(w), 256, 0, s, relax_args(w, y, step_dev, step_host, hp, relax));
 }
 
-void launch_up_fwd_ifce(const Work& w, const float* params, int m, cudaStream_t s) {
+void launch_up_fwd_ifce(const Work& w, const float* params, int m, const int64_t* step_dev, cudaStream_t s) {
     const int n_up = up_fwd_ctas(w, m);
     const int n_if = grid_for(8 * (4 + w.g.nh) * (int64_t)w.g.h[kNIfce] * w.g.w[kNIfce], kUpThreads, 8);
-    launch_pdl(k_up_fwd_ifce, n_up + n_if, kUpThreads, 0, s, up_fwd_args(w, params, m), ifce_args(w), n_up);
+    launch_pdl(k_up_fwd_ifce, n_up + n_if, kUpThreads, 0, s, up_fwd_args(w, params, m), ifce_args(w), n_up, step_dev,
+               w.step_snap);
 }
 
 void launch_gather(const Work& w, const float* params, int relax, float* grad_out, float* y, float* m, float* v,
@@ -599,12 +611,15 @@ void launch_gather(const Work& w, const float* params, int relax, float* grad_ou
 }
 
 void launch_gather_reduce(const Work& w, float* y, float* m_lat, float* v_lat, float* params, float* m_par,
-                          float* v_par, const Hp& hp, const int64_t* step_dev, cudaStream_t s, bool relax_next) {
+                          float* v_par, const Hp& hp, int64_t* step_dev, double* rd_out, cudaStream_t s,
+                          bool relax_next) {
     static_assert(kReduceThreads == 256, "the reduction shares the gather's CTA size");
-    const int ng = gather_ctas(w) > kReduceCtas + 1 ? gather_ctas(w) - kReduceCtas : 1;
-    launch_pdl(k_gather_reduce, kReduceCtas + ng, 256, 0, s,
-               gather_args(w, kRelaxNoise, nullptr, y, m_lat, v_lat, hp, step_dev, 0, relax_next),
-               reduce_args(w, params, m_par, v_par, nullptr, 1.f, hp, step_dev));
+    constexpr int lead = kReduceCtas + 1;  // the reduction's CTAs and the finish
+    const int ng = gather_ctas(w) > lead + 1 ? gather_ctas(w) - lead : 1;
+    launch_pdl(k_gather_reduce, lead + ng, 256, 0, s,
+               gather_args(w, kRelaxNoise, nullptr, y, m_lat, v_lat, hp, w.step_snap, 0, relax_next),
+               reduce_args(w, params, m_par, v_par, nullptr, 1.f, hp, w.step_snap),
+               finish_args(w, hp, 1, 1, rd_out, 3, step_dev, 0, 1));
 }
 
 void launch_param_reduce(const Work& w, float* params, float* m, float* v, float* grad_out, float out_scale,

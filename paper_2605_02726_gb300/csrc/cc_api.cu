@@ -50,6 +50,7 @@ int device_setup() {
     if (!g_attr_done[dev]) {
         arm_init_attributes();
         synth_init_attributes();
+        conv_init_attributes();
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(CC_ERR_CUDA, "kernel attribute setup: %s", cudaGetErrorString(e));
         g_attr_done[dev] = 1;

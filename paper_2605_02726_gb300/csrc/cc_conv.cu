@@ -1,9 +1,9 @@
 // Residual 3x3 convolutions of the synthesis (Sec. III-B, Table II: two 3 -> 3 post-filters),
-// the distortion (Eq. 10) and their adjoint, on 16x32 pixel tiles with recomputed halos.
+// the distortion (Eq. 10) and their adjoint, on 22x32 pixel tiles with recomputed halos.
 //   x1 = t + b1 + conv1(t),  xh = x1 + b2 + conv2(x1)   (replicate padding, cross-correlation)
 //   D = mean (xh - x)^2;  dxh = 2 (xh - x) / (3HW);  dx1 = dxh + conv2^T(dxh);  dt = dx1 + conv1^T(dx1)
 //
-// All tiles of a CTA live in one frame of 24 x 40 cells whose origin is (ty0 - 4, tx0 - 4): t on
+// All tiles of a CTA live in one frame of 30 x 40 cells whose origin is (ty0 - 4, tx0 - 4): t on
 // the whole frame (halo 4), x1 on halo 3, the image and then dxh on halo 2, dx1 on halo 1, dt on
 // the core.  Tiles of t and x1 are replicate-padded (cells outside the image hold the clamped
 // value), so the forward stencils and the weight-gradient correlations need no clamps.
@@ -22,13 +22,18 @@
 namespace cc {
 namespace {
 
-constexpr int kTH = kConvTH, kTW = kConvTW;  // core 16 x 32
+// Core 22 x 32: at 512x768 that is 576 tiles, at most two per CTA at two CTAs per SM (16 x 32 tiles
+// gave 768, three rounds for 160 CTAs and two for the rest), and 12% fewer stencil cells per CTA
+// for the halos recomputed.  The four frame buffers (52 KB) are in dynamic shared memory.
+constexpr int kTH = kConvTH, kTW = kConvTW;
 constexpr int kThreads = 256;
 constexpr int SW = kTW + 8;               // 40 frame columns
-constexpr int T_R0 = 0, T_NR = kTH + 8;  // frame rows held by each buffer: t 0..23
-constexpr int X_R0 = 1, X_NR = kTH + 6;  // x1 1..22
-constexpr int D_R0 = 2, D_NR = kTH + 4;  // image / dxh 2..21
-constexpr int E_R0 = 3, E_NR = kTH + 2;  // dx1 3..20
+constexpr int T_R0 = 0, T_NR = kTH + 8;  // frame rows held by each buffer: t 0..kTH+7
+constexpr int X_R0 = 1, X_NR = kTH + 6;  // x1 1..kTH+6
+constexpr int D_R0 = 2, D_NR = kTH + 4;  // image / dxh 2..kTH+5
+constexpr int E_R0 = 3, E_NR = kTH + 2;  // dx1 3..kTH+4
+constexpr int kFrameFloats = 3 * (T_NR + X_NR + D_NR + E_NR) * SW;
+static_assert(kTH % 2 == 0, "two-row strips");
 constexpr int kTasks = 18;               // (conv, out, in) weight-gradient tasks
 
 __device__ __forceinline__ void conv_pairs(int q, int n, int (&src)[3], int (&tap)[3]) {
@@ -138,10 +143,11 @@ template <int PASS>
 __device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) {
     constexpr bool BWD = pass_bwd(PASS);
     __shared__ ConvW sW;
-    __shared__ float sT[3][T_NR][SW];
-    __shared__ float sX[3][X_NR][SW];
-    __shared__ float sD[3][D_NR][SW];
-    __shared__ float sE[3][E_NR][SW];
+    extern __shared__ __align__(16) float sFrame[];  // kFrameFloats
+    float (*sT)[T_NR][SW] = reinterpret_cast<float (*)[T_NR][SW]>(sFrame);
+    float (*sX)[X_NR][SW] = reinterpret_cast<float (*)[X_NR][SW]>(sFrame + 3 * T_NR * SW);
+    float (*sD)[D_NR][SW] = reinterpret_cast<float (*)[D_NR][SW]>(sFrame + 3 * (T_NR + X_NR) * SW);
+    float (*sE)[E_NR][SW] = reinterpret_cast<float (*)[E_NR][SW]>(sFrame + 3 * (T_NR + X_NR + D_NR) * SW);
     __shared__ double sSe[kThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     for (int j = tid; j < 2 * 81; j += kThreads) {
@@ -191,7 +197,7 @@ __device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) 
             cp_async_wait_all();
         }
         __syncthreads();
-        // x1 on halo 3: frame rows 1..22, columns 1..38
+        // x1 on halo 3: frame rows 1..kTH+6, columns 1..kTW+6
         {
             constexpr int NC = kTW + 6, NT = (X_NR / 2) * NC;
             for (int task = tid; task < NT; task += kThreads) {
@@ -218,7 +224,7 @@ __device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) 
             }
             __syncthreads();
         }
-        // xh, distortion and dxh on halo 2: frame rows 2..21, columns 2..37
+        // xh, distortion and dxh on halo 2: frame rows 2..kTH+5, columns 2..kTW+5
         {
             constexpr int NC = kTW + 4, NT = (D_NR / 2) * NC;
             float sef = 0.f;
@@ -248,7 +254,7 @@ __device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) 
         }
         if (!BWD) continue;
         __syncthreads();
-        // dx1 = dxh + conv2^T(dxh) on halo 1: frame rows 3..20, columns 3..36
+        // dx1 = dxh + conv2^T(dxh) on halo 1: frame rows 3..kTH+4, columns 3..kTW+4
         {
             constexpr int NC = kTW + 2, NT = (E_NR / 2) * NC;
             for (int task = tid; task < NT; task += kThreads) {
@@ -274,7 +280,7 @@ __device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) 
             }
         }
         __syncthreads();
-        // dt = dx1 + conv1^T(dx1) on the core: frame rows 4..19, columns 4..35
+        // dt = dx1 + conv1^T(dx1) on the core: frame rows 4..kTH+3, columns 4..kTW+3
         {
             constexpr int NC = kTW, NT = (kTH / 2) * NC;
             for (int task = tid; task < NT; task += kThreads) {
@@ -310,7 +316,7 @@ __device__ __forceinline__ void conv_body(const ConvArgs& a, int cta, int ncta) 
                 const int task = wid + 8 * s;
                 if (task >= kTasks) break;
                 const int cv = task / 9, o = (task / 3) % 3, i = task % 3;
-                // G row y = core row y; IN row y = core row y (rows -1 .. 16 valid)
+                // G row y = core row y; IN row y = core row y (rows -1 .. kTH valid)
                 const float* G = cv ? &sD[o][4 - D_R0][0] : &sE[o][4 - E_R0][0];
                 const float* IN = cv ? &sX[i][4 - X_R0][0] : &sT[i][4 - T_R0][0];
                 float w0[3], w1[3];
@@ -385,6 +391,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_b(Batch<ConvArgs> b) {
 
 }  // namespace
 
+void conv_init_attributes() {
+    const int sm = kFrameFloats * (int)sizeof(float);
+    cudaFuncSetAttribute(k_conv<PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_conv<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_conv_b<PASS_FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
 int conv_tiles(int H, int W) { return ((H + kTH - 1) / kTH) * ((W + kTW - 1) / kTW); }
 
 ConvArgs conv_args(const Work& w, const float* params, const float* image, float grad_scale, float* xhat_out) {
@@ -409,12 +422,15 @@ ConvArgs conv_args(const Work& w, const float* params, const float* image, float
 void launch_conv(const Work& w, const float* params, const float* image, int pass, float grad_scale,
                  float* xhat_out, cudaStream_t s) {
     const ConvArgs a = conv_args(w, params, image, grad_scale, xhat_out);
+    constexpr size_t sm = kFrameFloats * sizeof(float);
     if (pass_bwd(pass))
-        launch_pdl(k_conv<PASS_FWD_BWD>, w.n_cta_conv, kThreads, 0, s, a);
+        launch_pdl(k_conv<PASS_FWD_BWD>, w.n_cta_conv, kThreads, sm, s, a);
     else
-        launch_pdl(k_conv<PASS_FWD>, w.n_cta_conv, kThreads, 0, s, a);
+        launch_pdl(k_conv<PASS_FWD>, w.n_cta_conv, kThreads, sm, s, a);
 }
 
-void launch_conv_b(const Batch<ConvArgs>& b, cudaStream_t s) { launch_pdl(k_conv_b<PASS_FWD_BWD>, b.total_ctas, kThreads, 0, s, b); }
+void launch_conv_b(const Batch<ConvArgs>& b, cudaStream_t s) {
+    launch_pdl(k_conv_b<PASS_FWD_BWD>, b.total_ctas, kThreads, kFrameFloats * sizeof(float), s, b);
+}
 
 }  // namespace cc

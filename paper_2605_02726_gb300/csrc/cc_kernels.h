@@ -67,7 +67,7 @@ __device__ __forceinline__ float relax_latent(const Hp& hp, const ProxyAt& p, fl
 
 constexpr int kArmThreads = 128;   // latents per ARM round
 constexpr int kSynThreads = 128;   // pixels per synthesis round
-constexpr int kConvTH = 16, kConvTW = 32;  // conv tile (pixels)
+constexpr int kConvTH = 22, kConvTW = 32;  // conv tile (pixels)
 constexpr int kUpThreads = 256;
 constexpr int kUpMaxCta = 1024;    // per-stage cap on CTAs of an upsampling-adjoint pass
 constexpr int kUpTX = 64;          // input columns of an upsampling-adjoint tile
@@ -459,6 +459,7 @@ int up_adj_ctas(int nch, int hs, int ws);
 void arm_init_attributes();
 void synth_init_attributes();
 void syn_init_attributes();
+void conv_init_attributes();
 
 // argument builders, CTA counts and multi-job launches (batched encode)
 RelaxArgs relax_args(const Work& w, const float* y, const int64_t* step_dev, int64_t step_host, const Hp& hp,

@@ -325,26 +325,42 @@ __device__ __forceinline__ void syn_bwd_body(const SynArgs& a, int cta, int ncta
         st[(V_Z + tq + 4) * kSld + gq] = zA1;
         st[(V_Z + tq + 4) * kSld + gq + 8] = zB1;
         __syncwarp();
+        // fragments by ldmatrix (rows of 16 bytes at an 80-byte stride: 16-byte aligned, and eight
+        // rows fall on disjoint banks): an A fragment is the matrices (rows 0-7, k 0-3), (8-15, 0-3),
+        // (0-7, 4-7), (8-15, 4-7); a pair of B fragments (8 rows each) is (first, k 0-3),
+        // (first, 4-7), (second, 0-3), (second, 4-7)
+        const int mi = lane >> 3, ri = lane & 7;
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
             const int k0 = ks * 8;
+            const float* arow = st + (ri + (mi & 1) * 8) * kSld + k0 + (mi >> 1) * 4;
+            const float* brow = st + ri * kSld + k0 + (mi & 1) * 4;
             auto afrag = [&](int row0) {
-                return make_a(st[(row0 + gq) * kSld + k0 + tq], st[(row0 + gq + 8) * kSld + k0 + tq],
-                              st[(row0 + gq) * kSld + k0 + tq + 4], st[(row0 + gq + 8) * kSld + k0 + tq + 4]);
-            };
-            auto bfrag = [&](int row0) {
+                uint32_t r[4];
+                ldsm_x4(r, arow + row0 * kSld);
                 AFrag f;
-                split2(st[(row0 + gq) * kSld + k0 + tq], f.h[0], f.l[0]);
-                split2(st[(row0 + gq) * kSld + k0 + tq + 4], f.h[1], f.l[1]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) split_u(r[q], f.h[q], f.l[q]);
                 return f;
             };
+            auto bpair = [&](int row0a, int row0b, AFrag& fa, AFrag& fb) {
+                uint32_t r[4];
+                ldsm_x4(r, brow + ((mi >> 1) ? row0b : row0a) * kSld);
+                split_u(r[0], fa.h[0], fa.l[0]);
+                split_u(r[1], fa.h[1], fa.l[1]);
+                split_u(r[2], fb.h[0], fb.l[0]);
+                split_u(r[3], fb.h[1], fb.l[1]);
+            };
             const AFrag U0 = afrag(0), U1 = afrag(16), U2 = afrag(32);
-            const AFrag VZ = bfrag(V_Z);
+            AFrag VZ, G[5];
+            bpair(V_Z, V_G, VZ, G[0]);
+            bpair(V_G + 8, V_G + 16, G[1], G[2]);
+            bpair(V_G + 24, V_G + 32, G[3], G[4]);
             mma3b(acc[0], U0, VZ);
             mma3b(acc[1], U1, VZ);
             mma3b(acc[2], U2, VZ);
 #pragma unroll
-            for (int n = 0; n < 5; ++n) mma3b(acc[3 + n], U2, bfrag(V_G + 8 * n));
+            for (int n = 0; n < 5; ++n) mma3b(acc[3 + n], U2, G[n]);
         }
         __syncwarp();
     }

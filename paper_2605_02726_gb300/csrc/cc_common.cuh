@@ -224,6 +224,22 @@ __device__ __forceinline__ float gelu_f(float a) {
     const float lt = gelu_lower_tail(a, ex);
     return a * (a < 0.f ? lt : 1.f - lt);
 }
+// gelu_f of two values in packed two-wide FP32 instructions: each component goes through exactly
+// the operations of gelu_f (the packed multiply and fused multiply-add round like the scalar
+// ones; the reciprocal and the exponential stay scalar calls), so the results are the same bits.
+__device__ __forceinline__ float2 gelu2_f(float2 a) {
+    const float2 x = __fmul2_rn(make_float2(fabsf(a.x), fabsf(a.y)), make_float2(0.70710678118654752f, 0.70710678118654752f));
+    const float2 d = __ffma2_rn(make_float2(0.3275911f, 0.3275911f), x, make_float2(1.f, 1.f));
+    const float2 s = make_float2(__fdividef(1.f, d.x), __fdividef(1.f, d.y));
+    float2 q = __ffma2_rn(make_float2(1.061405429f, 1.061405429f), s, make_float2(-1.453152027f, -1.453152027f));
+    q = __ffma2_rn(q, s, make_float2(1.421413741f, 1.421413741f));
+    q = __ffma2_rn(q, s, make_float2(-0.284496736f, -0.284496736f));
+    q = __ffma2_rn(q, s, make_float2(0.254829592f, 0.254829592f));
+    const float2 e = __fmul2_rn(make_float2(-x.x, -x.y), x);
+    const float2 ex = make_float2(__expf(e.x), __expf(e.y));
+    const float2 lt = __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), __fmul2_rn(q, s)), ex);
+    return __fmul2_rn(a, make_float2(a.x < 0.f ? lt.x : 1.f - lt.x, a.y < 0.f ? lt.y : 1.f - lt.y));
+}
 // gelu(a) and gelu'(a) together
 __device__ __forceinline__ void gelu_fg(float a, float& g, float& dg) {
     float ex;

@@ -105,17 +105,30 @@ __device__ __forceinline__ float dense_ch(const SynArgs& a, const Samp& s, int j
 // short and latency-bound, and a thread per pixel keeps the register count, hence the number of
 // resident warps, where the tensor-core form cannot).
 // ---------------------------------------------------------------------------------------------
-// per hidden unit o, 12 floats: W1[o][0..6], b1[o], W2[0..2][o], 0 (three 16-byte loads)
-constexpr int ss_unit = 0;   // [40][12]
+// Hidden-unit weights, two layouts of the same 480 floats.  PACKED: per pair of units (o, o + 1),
+// 24 floats interleaved so that every 16-byte load gives two (unit o, unit o + 1) register pairs for
+// the packed two-wide FMAs: W1[o][i], W1[o+1][i] for i = 0..6, b1[o], b1[o+1], then W2[0..2][o],
+// W2[0..2][o+1], 0, 0 (six 16-byte loads).  Otherwise per unit o, 12 floats: W1[o][0..6], b1[o],
+// W2[0..2][o], 0 (three 16-byte loads).
+constexpr int ss_unit = 0;   // [20][24] or [40][12]
 constexpr int ss_ws = 480;   // [3][8]  (7 used, 8th = b2 + bs)
 constexpr int ss_total = 504;
+static_assert(kSH % 2 == 0, "hidden units in pairs");
 
+template <bool PACKED>
 __device__ __forceinline__ void load_syn_weights(const float* P, float* sW) {
     for (int j = threadIdx.x; j < ss_total; j += blockDim.x) {
         float v;
-        if (j < ss_ws) {
+        if (j < ss_ws && !PACKED) {
             const int o = j / 12, i = j - o * 12;
             v = i < 7 ? P[po::syn_w1 + o * 7 + i] : i == 7 ? P[po::syn_b1 + o] : i < 11 ? P[po::syn_w2 + (i - 8) * kSH + o] : 0.f;
+        } else if (j < ss_ws) {
+            const int pr = j / 24, i = j - pr * 24;
+            const int o = 2 * pr + (i < 16 ? (i & 1) : (i - 16) / 3);
+            if (i < 14) v = P[po::syn_w1 + o * 7 + (i >> 1)];
+            else if (i < 16) v = P[po::syn_b1 + o];
+            else if (i < 22) v = P[po::syn_w2 + ((i - 16) % 3) * kSH + o];
+            else v = 0.f;
         } else {
             const int o = (j - ss_ws) >> 3, i = (j - ss_ws) & 7;
             v = i < 7 ? P[po::syn_ws + o * 7 + i] : P[po::syn_b2 + o] + P[po::syn_bs + o];
@@ -124,11 +137,15 @@ __device__ __forceinline__ void load_syn_weights(const float* P, float* sW) {
     }
 }
 
-template <int PASS>
+// PACKED: the hidden units' first layer and GELU as packed two-wide FP32 operations (the
+// single-job kernel, whose arguments stay in the parameter space); otherwise the same operations
+// one unit at a time (the multi-job kernel, whose arguments in shared memory leave too few
+// registers for the pairs).  Both give the same bits.
+template <int PASS, bool PACKED>
 __device__ __forceinline__ void syn_fwd_body(const SynArgs& a, int cta, int ncta) {
     __shared__ __align__(16) float sW[ss_total];
     __shared__ float sRaw[po::syn_block];  // the synthesis parameters, staged in one round trip
-    load_syn_weights(stage_params(a.params, po::syn_w1, po::syn_block, sRaw), sW);
+    load_syn_weights<PACKED>(stage_params(a.params, po::syn_w1, po::syn_block, sRaw), sW);
     const float tp[4] = {a.params[po::up], a.params[po::up + 1], a.params[po::up + 2], a.params[po::up + 3]};
     __syncthreads();
     const float rcpW = 1.f / (float)a.g.W;
@@ -148,24 +165,56 @@ __device__ __forceinline__ void syn_fwd_body(const SynArgs& a, int cta, int ncta
             t1 = fmaf(sW[ss_ws + 8 + i], z[i], t1);
             t2 = fmaf(sW[ss_ws + 16 + i], z[i], t2);
         }
+        // the hidden units: packed in pairs (each unit gets exactly the scalar operations, in the same
+        // order) or one at a time; the output layer scalar in unit order either way
+        if constexpr (PACKED) {
+            float2 zz[7];
+#pragma unroll
+            for (int i = 0; i < 7; ++i) zz[i] = make_float2(z[i], z[i]);
+#pragma unroll 1
+            for (int pr = 0; pr < kSH / 2; ++pr) {
+                const float4* q = reinterpret_cast<const float4*>(sW + ss_unit + pr * 24);
+                const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4], q5 = q[5];
+                float2 acc = make_float2(q3.z, q3.w);
+                acc = __ffma2_rn(make_float2(q0.x, q0.y), zz[0], acc);
+                acc = __ffma2_rn(make_float2(q0.z, q0.w), zz[1], acc);
+                acc = __ffma2_rn(make_float2(q1.x, q1.y), zz[2], acc);
+                acc = __ffma2_rn(make_float2(q1.z, q1.w), zz[3], acc);
+                acc = __ffma2_rn(make_float2(q2.x, q2.y), zz[4], acc);
+                acc = __ffma2_rn(make_float2(q2.z, q2.w), zz[5], acc);
+                acc = __ffma2_rn(make_float2(q3.x, q3.y), zz[6], acc);
+                if (PASS == PASS_FWD_STORE) {
+                    a.act[(int64_t)(2 * pr) * a.HW + p] = acc.x;
+                    a.act[(int64_t)(2 * pr + 1) * a.HW + p] = acc.y;
+                }
+                const float2 h = gelu2_f(acc);
+                t0 = fmaf(q4.x, h.x, t0);
+                t1 = fmaf(q4.y, h.x, t1);
+                t2 = fmaf(q4.z, h.x, t2);
+                t0 = fmaf(q4.w, h.y, t0);
+                t1 = fmaf(q5.x, h.y, t1);
+                t2 = fmaf(q5.y, h.y, t2);
+            }
+        } else {
 #pragma unroll 4
-        for (int o = 0; o < kSH; ++o) {
-            const float4 w0 = *reinterpret_cast<const float4*>(sW + ss_unit + o * 12);
-            const float4 w1 = *reinterpret_cast<const float4*>(sW + ss_unit + o * 12 + 4);
-            const float4 w2 = *reinterpret_cast<const float4*>(sW + ss_unit + o * 12 + 8);
-            float acc = w1.w;
-            acc = fmaf(w0.x, z[0], acc);
-            acc = fmaf(w0.y, z[1], acc);
-            acc = fmaf(w0.z, z[2], acc);
-            acc = fmaf(w0.w, z[3], acc);
-            acc = fmaf(w1.x, z[4], acc);
-            acc = fmaf(w1.y, z[5], acc);
-            acc = fmaf(w1.z, z[6], acc);
-            if (PASS == PASS_FWD_STORE) a.act[(int64_t)o * a.HW + p] = acc;
-            const float h = gelu_f(acc);
-            t0 = fmaf(w2.x, h, t0);
-            t1 = fmaf(w2.y, h, t1);
-            t2 = fmaf(w2.z, h, t2);
+            for (int o = 0; o < kSH; ++o) {
+                const float4 w0 = *reinterpret_cast<const float4*>(sW + ss_unit + o * 12);
+                const float4 w1 = *reinterpret_cast<const float4*>(sW + ss_unit + o * 12 + 4);
+                const float4 w2 = *reinterpret_cast<const float4*>(sW + ss_unit + o * 12 + 8);
+                float acc = w1.w;
+                acc = fmaf(w0.x, z[0], acc);
+                acc = fmaf(w0.y, z[1], acc);
+                acc = fmaf(w0.z, z[2], acc);
+                acc = fmaf(w0.w, z[3], acc);
+                acc = fmaf(w1.x, z[4], acc);
+                acc = fmaf(w1.y, z[5], acc);
+                acc = fmaf(w1.z, z[6], acc);
+                if (PASS == PASS_FWD_STORE) a.act[(int64_t)o * a.HW + p] = acc;
+                const float h = gelu_f(acc);
+                t0 = fmaf(w2.x, h, t0);
+                t1 = fmaf(w2.y, h, t1);
+                t2 = fmaf(w2.z, h, t2);
+            }
         }
         a.t[p] = t0;
         a.t[a.HW + p] = t1;
@@ -391,14 +440,14 @@ __device__ __forceinline__ void syn_bwd_body(const SynArgs& a, int cta, int ncta
 template <int PASS>
 __global__ void __launch_bounds__(kSynThreads, 8) k_syn_fwd(const __grid_constant__ SynArgs a) {
     pdl_enter();
-    syn_fwd_body<PASS>(a, blockIdx.x, gridDim.x);
+    syn_fwd_body<PASS, true>(a, blockIdx.x, gridDim.x);
 }
 template <int PASS>
 __global__ void __launch_bounds__(kSynThreads, 8) k_syn_fwd_b(Batch<SynArgs> b) {
     __shared__ SynArgs sa;
     const int j = batch_job(b.cta_begin, b.njobs);
     batch_fetch(b.args, j, sa);
-    syn_fwd_body<PASS>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
+    syn_fwd_body<PASS, false>(sa, blockIdx.x - b.cta_begin[j], b.cta_begin[j + 1] - b.cta_begin[j]);
 }
 template <int PASS>
 __global__ void __launch_bounds__(kSynThreads, 4) k_syn_bwd(const __grid_constant__ SynArgs a) {

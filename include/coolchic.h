@@ -323,9 +323,12 @@ int coolchic_decode_image(const cc_arch_t* arch, const int32_t* q, const float* 
 #define CC_KERNEL_SYN_BWD 1  /* synthesis adjoint               */
 #define CC_KERNEL_CONV 2     /* residual convs + distortion     */
 #define CC_KERNEL_SYN_FWD 3  /* synthesis forward               */
-#define CC_KERNEL_UP_FWD 4   /* upsampling stages 6..2 (one bracket around the five launches) */
+#define CC_KERNEL_UP_FWD 4   /* upsampling stages 3..2 (one bracket around their two launches;
+                                stages 6..4 run inside the entropy-model launch) */
 #define CC_KERNEL_UP_ADJ 5   /* upsampling adjoint stages 1..6 (one bracket around the six)  */
-#define CC_KERNEL_GATHER 6   /* latent-gradient gather + latent Adam                         */
+#define CC_KERNEL_GATHER 6   /* latent-gradient gather + latent Adam (in encoder iterations the
+                                same launch also reduces the parameter gradients, takes the
+                                parameters' Adam step and writes the loss record) */
 int coolchic_timing_enable(int32_t kernel_id, int32_t max_launches);
 int coolchic_timing_collect(double* total_ms, int64_t* launches);
 int coolchic_timing_disable(void);
